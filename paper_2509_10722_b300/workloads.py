@@ -1,0 +1,220 @@
+"""Seeded synthetic NUM instances (the only module shared by the oracle side and the CUDA side).
+
+This module draws random problem data and nothing else: it holds none of the method's
+arithmetic (no prox, no averaging, no residuals).  Every instance is a plain dict of numpy
+arrays in the layout the C ABI takes:
+
+    n, m          number of traffic streams and of links
+    route_ptr     int64[n+1]   CSC column pointer of the 0/1 link-route matrix R (Sec. II)
+    route_links   int32[nnz]   link ids of each route, stream-major; no duplicate within a route
+    c             float64[m]   link capacities, > 0
+    utype         uint8[n]     0 = w log x utility, 1 = w x utility
+    w             float64[n]   utility weights, > 0
+    lo, hi        float64[n]   box of each stream rate
+
+The five named workloads follow the instance recipes stated for this build (uniform routes
+without replacement, Zipf-skewed link choice for the congested case); the paper itself only
+says its matrices are random with about ten links per route (Sec. V-B) and that congestion
+makes a few links carry a large share of the streams (Sec. V-C).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+LOG = 0
+LINEAR = 1
+
+
+def _dedupe_routes(rng, route_ptr, links, draw, max_rounds=10_000):
+    """Redraw every link id that repeats an earlier id of the same route until none repeats.
+
+    Redrawing a repeated id from the same distribution is rejection sampling, so a route of
+    length L drawn this way is a sample of L distinct links (without replacement).
+    """
+    n = route_ptr.size - 1
+    lengths = np.diff(route_ptr)
+    nnz = links.size
+    if nnz == 0:
+        return links
+    maxlen = int(lengths.max())
+    if maxlen <= 64:
+        route_of = np.repeat(np.arange(n, dtype=np.int64), lengths)
+        pos = np.arange(nnz, dtype=np.int64) - route_ptr[:-1][route_of]
+        for _ in range(max_rounds):
+            bad = np.zeros(nnz, dtype=bool)
+            for d in range(1, maxlen):
+                eq = links[d:] == links[:-d]
+                eq &= pos[d:] >= d
+                bad[d:] |= eq
+            idx = np.flatnonzero(bad)
+            if idx.size == 0:
+                return links
+            links[idx] = draw(idx.size)
+        raise RuntimeError("could not draw distinct links for every route")
+    route_of = np.repeat(np.arange(n, dtype=np.int64), lengths)
+    for _ in range(max_rounds):
+        order = np.lexsort((np.arange(nnz), links, route_of))
+        sl = links[order]
+        sr = route_of[order]
+        dup = (sl[1:] == sl[:-1]) & (sr[1:] == sr[:-1])
+        idx = order[1:][dup]
+        if idx.size == 0:
+            return links
+        links[idx] = draw(idx.size)
+    raise RuntimeError("could not draw distinct links for every route")
+
+
+def _zipf_sampler(rng, m, s):
+    """Truncated Zipf(s) over ranks 1..m by inverse CDF, ranks mapped to link ids by a seeded
+    random permutation (so the hot links are spread over the id range)."""
+    ranks = np.arange(1, m + 1, dtype=np.float64)
+    pmf = ranks ** (-s)
+    cdf = np.cumsum(pmf)
+    cdf /= cdf[-1]
+    perm = rng.permutation(m).astype(np.int32)
+
+    def draw(k):
+        u = rng.random(k)
+        r = np.searchsorted(cdf, u, side="right")
+        np.minimum(r, m - 1, out=r)
+        return perm[r]
+
+    return draw
+
+
+def random_instance(n, m, len_lo, len_hi, *, seed=0, link_dist="uniform", zipf_s=1.1,
+                    c_lo=1.0, c_hi=10.0, c_scale=1.0, frac_log=0.5, w_dist="uniform",
+                    w_lo=0.5, w_hi=2.0, box=(0.0, 20.0), degrade=None):
+    """Draw one NUM instance.
+
+    len_lo..len_hi    route length, uniform over the integers in that range (capped at m)
+    link_dist         "uniform" (links uniform without replacement) or "zipf"
+    frac_log          fraction of streams with log utility (exact count, random positions)
+    w_dist            "uniform" (U[w_lo, w_hi]) or "lognormal" (LogNormal(0, 0.5))
+    box               (lo, hi) applied to every stream, or a callable(rng, n) -> (lo, hi) arrays
+    degrade           None or (lo, hi): capacities multiplied by a per-link U[lo, hi] factor
+    """
+    if n < 1 or m < 1:
+        raise ValueError("n and m must be positive")
+    rng = np.random.default_rng(seed)
+    len_hi = min(len_hi, m)
+    len_lo = max(1, min(len_lo, len_hi))
+    lengths = rng.integers(len_lo, len_hi + 1, size=n, dtype=np.int64)
+    route_ptr = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(lengths, out=route_ptr[1:])
+    nnz = int(route_ptr[-1])
+    if link_dist == "uniform":
+        def draw(k):
+            return rng.integers(0, m, size=k, dtype=np.int64).astype(np.int32)
+    elif link_dist == "zipf":
+        draw = _zipf_sampler(rng, m, zipf_s)
+    else:
+        raise ValueError(link_dist)
+    links = draw(nnz).astype(np.int32)
+    links = _dedupe_routes(rng, route_ptr, links, draw)
+    c = rng.uniform(c_lo, c_hi, size=m) * c_scale
+    if degrade is not None:
+        c = c * rng.uniform(degrade[0], degrade[1], size=m)
+    n_log = int(round(frac_log * n))
+    utype = np.full(n, LINEAR, dtype=np.uint8)
+    utype[rng.permutation(n)[:n_log]] = LOG
+    if w_dist == "uniform":
+        w = rng.uniform(w_lo, w_hi, size=n)
+    elif w_dist == "lognormal":
+        w = rng.lognormal(0.0, 0.5, size=n)
+    else:
+        raise ValueError(w_dist)
+    if callable(box):
+        lo, hi = box(rng, n)
+        lo = np.asarray(lo, dtype=np.float64)
+        hi = np.asarray(hi, dtype=np.float64)
+    else:
+        lo = np.full(n, float(box[0]))
+        hi = np.full(n, float(box[1]))
+    return dict(n=int(n), m=int(m), route_ptr=route_ptr, route_links=links, c=c,
+                utype=utype, w=w, lo=lo, hi=hi)
+
+
+# ---------------------------------------------------------------------------------------------
+# The named workloads.  Sizes, distributions and boxes are the ones the instance recipes state;
+# C4 (batched) and C5 (differentiation) are listed for completeness of the recipe table.
+
+WORKLOADS = {
+    # small FP64 parity case: 2,000 iterations
+    "c1": dict(n=1_000, m=500, len_lo=2, len_hi=6, frac_log=0.5, box=(0.0, 20.0), seed=0),
+    # headline: n = 1e7 streams, m = 1e6 links, about 5.5e7 nonzeros
+    "c2": dict(n=10_000_000, m=1_000_000, len_lo=1, len_hi=10, frac_log=0.7,
+               box=(0.0, 50.0), seed=0),
+    # congested, skewed: Zipf(1.1) link choice, capacities scaled by 0.1, all log utilities
+    "c3": dict(n=20_000_000, m=2_000_000, len_lo=2, len_hi=12, link_dist="zipf",
+               zipf_s=1.1, c_scale=0.1, frac_log=1.0, w_dist="lognormal",
+               box=(0.0, 10.0), seed=0),
+    # differentiation case (forward solve only is used here)
+    "c5": dict(n=1_000_000, m=100_000, len_lo=2, len_hi=8, frac_log=1.0,
+               box=(0.0, 20.0), seed=0),
+}
+
+WORKLOAD_ITERS = {"c1": 2000}
+
+
+def workload(name, seed=None, scale=None):
+    """Instance for a named workload.  `scale` (0 < scale <= 1) shrinks n and m together,
+    keeping route lengths and distributions, for the CPU-sized stand-ins of a large case."""
+    spec = dict(WORKLOADS[name])
+    if seed is not None:
+        spec["seed"] = seed
+    if scale is not None:
+        spec["n"] = max(1, int(round(spec["n"] * scale)))
+        spec["m"] = max(1, int(round(spec["m"] * scale)))
+    n = spec.pop("n")
+    m = spec.pop("m")
+    lo = spec.pop("len_lo")
+    hi = spec.pop("len_hi")
+    return random_instance(n, m, lo, hi, **spec)
+
+
+def batched_instances(count=256, seed=0):
+    """Batched-solve recipe: `count` independent instances, n log-uniform in [1e3, 1e5],
+    m = n/10, routes of 2..8 uniform links, capacities U[1,10] times a per-link U[0.3,1]
+    degradation factor, 70% log utilities, box [0, 20]."""
+    rng = np.random.default_rng(seed)
+    ns = np.exp(rng.uniform(np.log(1e3), np.log(1e5), size=count)).astype(np.int64)
+    seeds = rng.integers(0, 2**31 - 1, size=count)
+    out = []
+    for n, s in zip(ns, seeds):
+        m = max(8, int(n) // 10)
+        out.append(random_instance(int(n), m, 2, 8, seed=int(s), frac_log=0.7,
+                                   box=(0.0, 20.0), degrade=(0.3, 1.0)))
+    return out
+
+
+def four_stream_example():
+    """The four-stream, three-link network of the paper's small example (Sec. III-A):
+    R = [[1,0,0,0],[0,1,1,0],[0,1,0,1]].  The paper gives only the structure; capacities 1,
+    weights 1 and log utilities are this fixture's choice."""
+    route_ptr = np.array([0, 1, 3, 4, 5], dtype=np.int64)
+    route_links = np.array([0, 1, 2, 1, 2], dtype=np.int32)
+    n, m = 4, 3
+    return dict(n=n, m=m, route_ptr=route_ptr, route_links=route_links,
+                c=np.ones(m), utype=np.zeros(n, dtype=np.uint8), w=np.ones(n),
+                lo=np.zeros(n), hi=np.full(n, 1e3))
+
+
+def instance_bytes(inst):
+    """Bytes the C ABI copies host-to-device for one instance."""
+    return sum(int(inst[k].nbytes) for k in ("route_ptr", "route_links", "c", "utype", "w",
+                                            "lo", "hi"))
+
+
+def csr_of(inst):
+    """Row-major (link-major) copy of R: (row_ptr int64[m+1], col_idx int32[nnz]) with each
+    row's stream ids ascending.  Pure index bookkeeping used to check the device transpose."""
+    n, m = inst["n"], inst["m"]
+    lengths = np.diff(inst["route_ptr"])
+    stream_of = np.repeat(np.arange(n, dtype=np.int32), lengths)
+    order = np.argsort(inst["route_links"], kind="stable")
+    col_idx = stream_of[order]
+    counts = np.bincount(inst["route_links"], minlength=m)
+    row_ptr = np.zeros(m + 1, dtype=np.int64)
+    np.cumsum(counts, out=row_ptr[1:])
+    return row_ptr, col_idx.astype(np.int32)
