@@ -1,0 +1,449 @@
+#!/usr/bin/env python
+"""Benchmark of the PMP solver: iterations/s and time to the 1e-4 residual tolerance on the
+n = 1e7 streams, m = 1e6 links instance, FP32 fused path vs the plain FP64 GPU path.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One step = one whole solve from inputs already resident in HBM: num_create_device (input
+validation and the device CSR build), num_solve to eps_abs = 1e-4 (Sec. III-F), and
+num_get_device (x, prices, FP64 objective).  `value` = iterations of the timed steps per
+second of device time (CUDA events on the solver's stream).  Prints one JSON line.
+
+--impl reference times the FP64 CPU oracle (a literal per-terminal ADMM, single thread) on
+the same instance, as the slow reference arm.  With N > 1 (torchrun) every rank solves an
+independent instance (replicas; no collective in the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import hashlib
+import io
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2509_10722_b300 import workloads as W  # noqa: E402
+
+METRIC = "PMP iters/s & time-to-1e-4 KKT residual, n=1e7 m=1e6, vs FP64 plain path"
+WORKLOAD_TEXT = {
+    "c2": ("n=1e7 streams, m=1e6 links, route length U{1..10} over uniform links without "
+           "replacement (nnz~5.5e7), c~U[1,10], 70% log / 30% linear, w~U[0.5,2], box [0,50], "
+           "eps_abs=1e-4 (||r||,||s|| < eps_abs*sqrt(nnz+m)), rho0=1, alpha=1.6, mu=2, "
+           "gamma=1.1, rho period 50"),
+    "c3": ("n=2e7 streams, m=2e6 links, route length U{2..12}, Zipf(1.1) link choice, "
+           "c~0.1*U[1,10], all log, w~LogNormal(0,0.5), box [0,10], eps_abs=1e-4"),
+}
+PRECISION = {"fp32": 0, "fp64": 1, "plain": 2}
+KERNEL_NAMES = {0: ["stream (SpMV-transpose + prox)", "link (SpMV + link update + finalize)"],
+                2: ["plain SpMV-transpose", "plain stream prox", "plain SpMV", "plain link update",
+                    "plain reduce 1", "plain reduce 2", "plain reduce 3", "plain finalize"]}
+
+
+def parse():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="c2", choices=sorted(WORKLOAD_TEXT))
+    ap.add_argument("--scale", type=float, default=None, help="shrink n and m (testing only)")
+    ap.add_argument("--eps", type=float, default=1e-4)
+    ap.add_argument("--max-iters", type=int, default=50_000)
+    ap.add_argument("--tile", type=int, default=0, help="tile_items (0 = automatic)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-iters", type=int, default=3)
+    ap.add_argument("--ref-iters", type=int, default=1, help="oracle iterations per reference step")
+    return ap.parse_args()
+
+
+# ---- distributed plumbing (replicas) -------------------------------------------------------------
+
+class Dist:
+    def __init__(self):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.pg = None
+
+    def init(self, backend):
+        if self.world > 1:
+            import torch.distributed as dist
+            dist.init_process_group(backend)
+            self.pg = dist
+
+    def barrier(self):
+        if self.pg:
+            self.pg.barrier()
+
+    def max(self, v):
+        return self._reduce(v, "max")
+
+    def sum(self, v):
+        return self._reduce(v, "sum")
+
+    def _reduce(self, v, op):
+        if not self.pg:
+            return v
+        import torch
+        dev = "cuda" if self.pg.get_backend() == "nccl" else "cpu"
+        t = torch.tensor([float(v)], dtype=torch.float64, device=dev)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX if op == "max" else self.pg.ReduceOp.SUM)
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            self.pg.destroy_process_group()
+
+
+# ---- clocks during the timed region ---------------------------------------------------------------
+
+CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+class ClockSampler:
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={CLOCK_QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = list(csv.reader(io.StringIO(open(self.path).read())))
+        os.unlink(self.path)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, r[5:9]):
+                if val.strip().lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---- helpers --------------------------------------------------------------------------------------
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "of measured (MEASURED_PEAKS.json hbm_gbs, copy bandwidth)"
+    return 6400.0, "of fallback (6.4 TB/s)"
+
+
+def traffic_record(kernel_key):
+    """DRAM bytes per launch from a committed ncu capture, if it was taken on the current
+    kernel source (profiles/traffic.json holds the source hash it was taken on)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    rec = json.load(open(path)).get(kernel_key)
+    if not rec:
+        return None
+    src = os.path.join(ROOT, "paper_2509_10722_b300", "csrc", "fused.cu")
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    return rec if rec.get("source_sha") == h else None
+
+
+def to_device(inst, torch):
+    return {k: torch.as_tensor(np.ascontiguousarray(inst[k])).cuda()
+            for k in ("route_ptr", "route_links", "c", "utype", "w", "lo", "hi")}
+
+
+def pinned_copy(inst, torch):
+    out = {}
+    for k in ("route_ptr", "route_links", "c", "utype", "w", "lo", "hi"):
+        a = np.ascontiguousarray(inst[k])
+        t = torch.empty(a.shape, dtype=torch.from_numpy(a[:0]).dtype, pin_memory=True)
+        t.numpy()[...] = a
+        out[k] = t.numpy()
+    return out
+
+
+class Solver:
+    """One whole solve per call, on a fixed torch stream, inputs resident on the device."""
+
+    def __init__(self, capi, torch, dev_inst, n, m, precision, eps, max_iters, stream, tile=0):
+        self.capi, self.torch = capi, torch
+        self.d = dev_inst
+        self.n, self.m = n, m
+        self.eps, self.max_iters = eps, max_iters
+        self.stream = stream
+        self.alloc = capi.torch_allocator()
+        import ctypes
+        self.params = capi.num_default_params(precision=precision, profile=1, tile_items=tile,
+                                              allocator=ctypes.pointer(self.alloc))
+        self.x = torch.empty(n, dtype=torch.float64, device="cuda")
+        self.p = torch.empty(m, dtype=torch.float64, device="cuda")
+        self.kernel_ms = None
+        self.kernel_runs = None
+        self.bytes = None
+
+    def step(self):
+        c, d = self.capi, self.d
+        h = c.num_create_device(self.n, self.m, d["route_ptr"], d["route_links"], d["c"],
+                                d["utype"], d["w"], d["lo"], d["hi"], self.params,
+                                self.stream.cuda_stream)
+        try:
+            status, iters = c.num_solve(h, self.max_iters, self.eps)
+            info = c.num_get_device(h, self.x, self.p)
+            ms, runs = c.num_get_kernel_times(h)
+            if self.kernel_ms is None:
+                self.kernel_ms, self.kernel_runs = np.zeros_like(ms), np.zeros_like(runs)
+                self.bytes = c.num_iteration_bytes(h)
+            self.kernel_ms += ms
+            self.kernel_runs += runs
+        finally:
+            c.num_destroy(h)
+        return status, iters, info
+
+    def reset_kernel_times(self):
+        self.kernel_ms = None
+        self.kernel_runs = None
+
+
+def timed(solver, torch, steps):
+    """Run `steps` solves between CUDA events on the solver's stream."""
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    iters, infos = 0, []
+    e0.record(solver.stream)
+    for _ in range(steps):
+        status, it, info = solver.step()
+        iters += it
+        infos.append((status, it, info))
+    e1.record(solver.stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1), iters, infos
+
+
+# ---- arms --------------------------------------------------------------------------------------------
+
+def run_reference(args, dist):
+    """The FP64 CPU oracle as the reference arm (rank 0 only)."""
+    if dist.rank != 0:
+        return
+    import oracle
+    inst = W.workload(args.workload, scale=args.scale)
+    k = max(args.ref_iters, 1)
+    for _ in range(args.warmup):
+        oracle.solve(inst, k, eps_abs=0.0)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.solve(inst, k, eps_abs=0.0)
+    dt = time.perf_counter() - t0
+    value = args.steps * k / dt
+    sample = (f"{k} oracle iteration(s) per step (its own setup included) on the full "
+              f"{args.workload} instance, single thread")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "iterations/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{args.workload}: {WORKLOAD_TEXT[args.workload]}",
+                       "scale": args.scale, "parallelism": "cpu, 1 thread"},
+            "cpu_baseline": {"value": value, "unit": "iterations/s", "cores": 1,
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "iterations/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(args, inst):
+    """Oracle iterations/s on the same instance: (t(k) - t(1)) / (k - 1) per iteration."""
+    import oracle
+    k = max(args.cpu_iters, 2)
+    t0 = time.perf_counter()
+    oracle.solve(inst, 1, eps_abs=0.0)
+    t1 = time.perf_counter()
+    oracle.solve(inst, k, eps_abs=0.0)
+    t2 = time.perf_counter()
+    per_it = ((t2 - t1) - (t1 - t0)) / (k - 1)
+    return {"value": 1.0 / per_it, "unit": "iterations/s", "cores": 1, "kind": "oracle",
+            "sample": f"{k - 1} oracle iterations on the full instance (difference of a "
+                      f"{k}-iteration and a 1-iteration run, single thread)"}
+
+
+def run_ours(args, dist):
+    import torch
+    dist.init("nccl")
+    torch.cuda.set_device(dist.local)
+    from paper_2509_10722_b300 import capi
+    inst = W.workload(args.workload, seed=dist.rank if dist.world > 1 else None, scale=args.scale)
+    n, m, nnz = inst["n"], inst["m"], int(inst["route_ptr"][-1])
+    dev = to_device(inst, torch)
+    stream = torch.cuda.Stream()
+    fp32 = Solver(capi, torch, dev, n, m, PRECISION["fp32"], args.eps, args.max_iters, stream,
+                  args.tile)
+    for _ in range(args.warmup):
+        fp32.step()
+    fp32.reset_kernel_times()
+    torch.cuda.synchronize()
+    dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = capi.num_kernel_launches()
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    ms, iters, infos = timed(fp32, torch, args.steps)
+    clocks = sampler.stop()
+    launches = capi.num_kernel_launches() - launches0
+    torch.cuda.synchronize()
+    dist.barrier()
+    ms_max = dist.max(ms)
+    iters_all = dist.sum(iters)
+    value = iters_all / (ms_max / 1e3)
+    statuses = [s for s, _, _ in infos]
+    it_per_solve = [it for _, it, _ in infos]
+    info = infos[-1][2]
+    x32 = fp32.x.double().cpu().numpy()
+    p32 = fp32.p.double().cpu().numpy()
+
+    # per-kernel device times measured by events inside the timed solves
+    kms, kruns = fp32.kernel_ms, fp32.kernel_runs
+    per_launch_ms = kms / np.maximum(kruns, 1)
+    dom = int(np.argmax(kms))
+    bytes_per_launch = fp32.bytes[dom]
+    achieved = bytes_per_launch / (per_launch_ms[dom] / 1e3) / 1e9
+    peak, peak_note = measured_peaks()
+    kernel_key = ["k_stream", "k_link"][dom]
+    trec = traffic_record(f"{args.workload}:{kernel_key}")
+    iter_bytes = float(sum(fp32.bytes))
+    iter_ms = float(np.sum(per_launch_ms))
+    roofline = {"bound": "hbm", "kernel": KERNEL_NAMES[0][dom], "achieved": achieved,
+                "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_note": peak_note,
+                "traffic": None if trec is None else trec["dram_bytes_per_launch"],
+                "algorithmic_bytes_per_launch": bytes_per_launch,
+                "launch_ms": float(per_launch_ms[dom]),
+                "share": float(kms[dom] / kms.sum()),
+                "iteration": {"bytes": iter_bytes, "ms": iter_ms,
+                              "achieved_gbs": iter_bytes / (iter_ms / 1e3) / 1e9,
+                              "frac": iter_bytes / (iter_ms / 1e3) / 1e9 / peak,
+                              "frac_of_8tbs": iter_bytes / (iter_ms / 1e3) / 1e9 / 8000.0},
+                "kernels": {KERNEL_NAMES[0][q]: {"ms_per_launch": float(per_launch_ms[q]),
+                                                 "launches": int(kruns[q]),
+                                                 "bytes_per_launch": float(fp32.bytes[q]),
+                                                 "gbs": float(fp32.bytes[q] / (per_launch_ms[q] / 1e3) / 1e9)}
+                            for q in range(len(kms))}}
+
+    line = {"metric": METRIC, "value": value, "unit": "iterations/s", "n_gpus": dist.world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": f"{args.workload}: {WORKLOAD_TEXT[args.workload]}",
+                       "scale": args.scale, "n": n, "m": m, "nnz": nnz,
+                       "step": "num_create_device + num_solve(eps_abs=1e-4) + num_get_device",
+                       "l2": "no flush: every step moves ~0.8 GB per iteration, far more than "
+                             "the 126 MB L2",
+                       "parallelism": "single GPU" if dist.world == 1 else f"{dist.world} replicas",
+                       "precision": "FP32 iterates, FP64 residuals / stopping test / rho"},
+            "time_to_tol_s": ms_max / args.steps / 1e3,
+            "iters_to_tol": it_per_solve[-1], "converged": all(s == 0 for s in statuses),
+            "final_residuals": {"primal": info["primal"], "dual": info["dual"],
+                                "eps_tol": info["eps_tol"]},
+            "objective": info["objective"],
+            "roofline": roofline, "gpu_launches": int(launches), "clocks": clocks}
+
+    if not args.no_fp64:
+        plain = Solver(capi, torch, dev, n, m, PRECISION["plain"], args.eps, args.max_iters,
+                       stream)
+        plain.step()
+        plain.reset_kernel_times()
+        pms, pit, pinfos = timed(plain, torch, 1)
+        x64 = plain.x.cpu().numpy()
+        p64 = plain.p.cpu().numpy()
+        pk = plain.kernel_ms / np.maximum(plain.kernel_runs, 1)
+        line["fp64_plain"] = {
+            "iters_per_s": pit / (pms / 1e3), "time_to_tol_s": pms / 1e3, "iters_to_tol": pit,
+            "converged": pinfos[0][0] == 0, "objective": pinfos[0][2]["objective"],
+            "iteration_ms": float(np.sum(pk)),
+            "kernels_ms_per_launch": {KERNEL_NAMES[2][q]: float(pk[q]) for q in range(len(pk))}}
+        line["speedup_vs_fp64_plain"] = {
+            "iters_per_s": value / dist.world / (pit / (pms / 1e3)),
+            "time_to_tol": (pms / 1e3) / (ms_max / args.steps / 1e3)}
+        o32, o64 = info["objective"], pinfos[0][2]["objective"]
+        line["parity_vs_fp64_plain"] = {
+            "objective_rel": abs(o32 - o64) / abs(o64),
+            "x_rel": float(np.linalg.norm(x32 - x64) / np.linalg.norm(x64)),
+            "prices_rel": float(np.linalg.norm(p32 - p64) / np.linalg.norm(p64))}
+        del plain
+
+    if not args.no_e2e:
+        host = pinned_copy(inst, torch)
+        e2e_params = capi.num_default_params(precision=0)
+        xh = np.empty(n)
+        ph = np.empty(m)
+        t_e2e, it_e2e = 0.0, 0
+        for rep in range(1 + args.steps):
+            t0 = time.perf_counter()
+            h = capi.num_create(n, m, host["route_ptr"], host["route_links"], host["c"],
+                                host["utype"], host["w"], host["lo"], host["hi"], e2e_params,
+                                stream.cuda_stream)
+            st, it = capi.num_solve(h, args.max_iters, args.eps)
+            xh, ph, _ = capi.num_get(h, n, m)
+            capi.num_destroy(h)
+            dt = time.perf_counter() - t0
+            if rep > 0:
+                t_e2e += dt
+                it_e2e += it
+        line["e2e"] = {"value": dist.sum(it_e2e) / dist.max(t_e2e), "unit": "iterations/s",
+                       "h2d_bytes_per_step": W.instance_bytes(inst),
+                       "d2h_bytes_per_step": 8 * (n + m) + 8 * 8,
+                       "time_to_tol_s": t_e2e / args.steps,
+                       "path": "num_create (pinned host arrays) + num_solve + num_get (host) + "
+                               "num_destroy, wall clock"}
+
+    if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args, inst)
+    if dist.rank == 0:
+        print(json.dumps(line), flush=True)
+    dist.close()
+
+
+def main():
+    args = parse()
+    dist = Dist()
+    if args.impl == "reference":
+        run_reference(args, dist)
+        return
+    run_ours(args, dist)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,219 @@
+/*
+ * num_pmp.h -- C ABI of the B300 (sm_103a) proximal message passing (PMP) solver for
+ * network utility maximization.
+ *
+ * Problem (Sec. II, Eq. vanilla_num):   maximize  sum_j U_j(x_j)
+ *                                       subject to R x <= c,  lo_j <= x_j <= hi_j,
+ * with the 0/1 link-route matrix R (R_lj = 1 iff stream j uses link l), capacities c > 0,
+ * and U_j(x) = w_j log x (NUM_LOG) or w_j x (NUM_LINEAR), w_j > 0.  The box is the
+ * "indicator of a convex set" of Sec. II; lo = 0 gives the paper's x >= 0.
+ *
+ * Method: the ADMM form of Sec. III-D (prox device updates, link averages, scaled price
+ * updates) with the residuals and stopping test of Sec. III-F and the residual balancing
+ * (Eq. rho-update, Eq. dual-rescale) and over-relaxation of Sec. III-G.  The library runs
+ * it on one GPU in hand-written CUDA kernels; the per-terminal state of the paper is kept
+ * in the exactly equivalent per-stream / per-link form (Z_j = sum of the link-side copies
+ * over stream j's terminals; one price y_l = rho u_l per link).
+ *
+ * Conventions for every function below:
+ *   - return value: NUM_OK (0) on success, NUM_NOT_CONVERGED (1) from num_solve when the
+ *     iteration limit came first (the state is valid), or a negative NUM_ERR_* code;
+ *     num_last_error() then holds a one-line message for the calling thread;
+ *   - "host" pointers are ordinary CPU memory; "device" pointers are CUDA global memory of
+ *     the device that was current when the handle was created;
+ *   - the caller owns every array it passes; the library copies what it keeps during
+ *     num_create* and never retains a caller pointer;
+ *   - one handle must not be used from two threads at once; separate handles are
+ *     independent.  All work of a handle is ordered on the CUDA stream given at creation.
+ */
+#ifndef NUM_PMP_H
+#define NUM_PMP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define NUM_API __attribute__((visibility("default")))
+#else
+#define NUM_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------------------------ */
+#define NUM_OK 0
+#define NUM_NOT_CONVERGED 1
+#define NUM_ERR_INVALID (-1) /* bad argument or malformed instance (see num_create) */
+#define NUM_ERR_OOM (-2)     /* a device allocation failed */
+#define NUM_ERR_CUDA (-3)    /* a CUDA runtime call failed; num_last_error() names it */
+#define NUM_ERR_NUMERIC (-4) /* a residual became non-finite; iteration stopped */
+#define NUM_ERR_STATE (-5)   /* call not valid for this handle's state */
+
+/* ---- utility types (Sec. III-B) ------------------------------------------------------------ */
+#define NUM_LOG 0    /* U(x) = w log x, the log-utility stream */
+#define NUM_LINEAR 1 /* U(x) = w x, the linear-utility stream */
+
+/* ---- kernel path / precision --------------------------------------------------------------- */
+#define NUM_FUSED_FP32 0 /* two fused kernels per iteration; FP32 iterates, FP64 residuals,
+                            FP64 stopping test and rho */
+#define NUM_FUSED_FP64 1 /* the same fused kernels with FP64 iterates */
+#define NUM_PLAIN_FP64 2 /* unfused baseline: one kernel per step (SpMV, elementwise prox,
+                            SpMV-transpose, reductions), all FP64 */
+
+/* Optional device allocator.  alloc returns device memory of `bytes` bytes usable on
+ * `stream` (NULL on failure, which num_create reports as NUM_ERR_OOM); release frees it. */
+typedef struct {
+    void* (*alloc)(void* ctx, size_t bytes, void* stream);
+    void (*release)(void* ctx, void* ptr, size_t bytes, void* stream);
+    void* ctx;
+} num_allocator;
+
+/* Solver parameters; num_default_params() fills the paper's values.
+ *   rho0        initial penalty rho (the paper does not state it; default 1.0)
+ *   alpha       over-relaxation parameter, Sec. III-G (default 1.6)
+ *   mu, gamma   residual-balancing threshold and factor, Eq. rho-update (2.0, 1.1)
+ *   eps_abs     absolute tolerance; the run stops when ||r||_2 and ||s||_2 are both below
+ *               eps_abs * sqrt(J), J = nnz(R) + m terminals, Sec. III-F (default 1e-4)
+ *   rho_period  iterations between rho updates (default 50; 0 = never update)
+ *   precision   NUM_FUSED_FP32 (default), NUM_FUSED_FP64 or NUM_PLAIN_FP64
+ *   check_every iterations per CUDA-graph replay between two host reads of the stop flag
+ *               (default 50); iterations after the stop inside a replay do nothing
+ *   tile_items  items (nonzeros + rows) per tile of the fused kernels; 0 = automatic,
+ *               otherwise a power of two in [256, 8192] (small values exercise row splitting)
+ *   history     length of the on-device ring buffer of (||r||, ||s||, rho) per iteration
+ *               (default 4096; 0 = none)
+ *   use_graph   1 (default): replay captured CUDA graphs; 0: plain launches
+ *   profile     1: record a CUDA event on the handle's stream after every kernel of every
+ *               iteration (inside the replayed graphs) and accumulate per-kernel device
+ *               times, read with num_get_kernel_times; 0 (default): no events
+ *   allocator   NULL (default): cudaMalloc / cudaFree */
+typedef struct {
+    double rho0;
+    double alpha;
+    double mu;
+    double gamma;
+    double eps_abs;
+    int32_t rho_period;
+    int32_t precision;
+    int32_t check_every;
+    int32_t tile_items;
+    int32_t history;
+    int32_t use_graph;
+    int32_t profile;
+    const num_allocator* allocator;
+} num_params;
+
+typedef struct num_problem num_problem; /* opaque; owns all of its device memory */
+
+/* Fill *p with the defaults listed above.  Never fails. */
+NUM_API void num_default_params(num_params* p);
+
+/* Create a solver handle for one NUM instance, from HOST arrays.
+ *   n, m         number of traffic streams and of links, both >= 1
+ *   route_ptr    int64[n+1], route_ptr[0] = 0, nondecreasing: stream j uses the links
+ *                route_links[route_ptr[j] .. route_ptr[j+1]-1] (R in CSC form, Sec. II)
+ *   route_links  int32[nnz], nnz = route_ptr[n] < 2^31 - m; link ids in [0, m), no link
+ *                twice in one route, every route nonempty (a stream has >= 1 terminal)
+ *   c            double[m], capacities, finite and > 0
+ *   utype        uint8[n], NUM_LOG or NUM_LINEAR
+ *   w            double[n], weights, finite and > 0
+ *   lo, hi       double[n] box of each rate, finite, lo <= hi, hi > 0 for log streams;
+ *                lo may be NULL (all zero)
+ *   p            parameters (NULL = defaults)
+ *   cuda_stream  cudaStream_t to order all work on (NULL = the legacy default stream)
+ * Scalar and pointer checks happen on the host before any CUDA call (NUM_ERR_INVALID);
+ * the per-element checks run on the device and are reported as NUM_ERR_INVALID too.
+ * Copies the arrays host-to-device, builds the link-major (CSR) copy of R on the device,
+ * and zeroes the iteration state (x = z = u = 0, rho = rho0).  Synchronizes the stream.
+ * On success *out owns the handle (free it with num_destroy); on failure *out = NULL. */
+NUM_API int num_create(num_problem** out, int64_t n, int64_t m, const int64_t* route_ptr,
+               const int32_t* route_links, const double* c, const uint8_t* utype,
+               const double* w, const double* lo, const double* hi, const num_params* p,
+               void* cuda_stream);
+
+/* As num_create, with every array argument a DEVICE pointer (same layout, same rules). */
+NUM_API int num_create_device(num_problem** out, int64_t n, int64_t m, const int64_t* route_ptr,
+                      const int32_t* route_links, const double* c, const uint8_t* utype,
+                      const double* w, const double* lo, const double* hi,
+                      const num_params* p, void* cuda_stream);
+
+/* Force the rho decision of the first `count` update points (host array, copied):
+ * decisions[i] = +1 (rho *= gamma), 0 (keep) or -1 (rho /= gamma) at iteration
+ * (i+1) * rho_period; later update points follow Eq. rho-update again.  count = 0 clears
+ * the schedule.  Used to compare runs of different precision along one trajectory. */
+NUM_API int num_set_rho_schedule(num_problem* h, const int8_t* decisions, int64_t count);
+
+/* Run at most max_iters (>= 0) further PMP iterations, stopping at the first iteration
+ * whose residuals pass the test of Sec. III-F with tolerance eps_abs:
+ *   eps_abs > 0   use it;   eps_abs < 0   use the handle's parameter;
+ *   eps_abs == 0  never stop on the test (run exactly max_iters iterations).
+ * *iters_done (may be NULL) receives the iterations run by this call.  Returns NUM_OK when
+ * the test passed, NUM_NOT_CONVERGED when max_iters came first, NUM_ERR_NUMERIC on a
+ * non-finite residual.  Continues from the current state; synchronizes the stream. */
+NUM_API int num_solve(num_problem* h, int64_t max_iters, double eps_abs, int64_t* iters_done);
+
+/* Copy the current solution to HOST buffers (each may be NULL):
+ *   x       double[n]  stream rates
+ *   prices  double[m]  link prices lambda = rho u = y (Sec. III-D: u = y / rho)
+ *   info    double[NUM_INFO_LEN], see NUM_INFO_* (objective sum_j U_j(x_j) in FP64) */
+NUM_API int num_get(const num_problem* h, double* x, double* prices, double* info);
+
+/* As num_get with x and prices DEVICE pointers (info stays a host pointer). */
+NUM_API int num_get_device(const num_problem* h, double* x, double* prices, double* info);
+
+#define NUM_INFO_PRIMAL 0    /* ||r||_2 of the last iteration */
+#define NUM_INFO_DUAL 1      /* ||s||_2 of the last iteration */
+#define NUM_INFO_EPS_TOL 2   /* eps_abs * sqrt(J) of the last solve */
+#define NUM_INFO_RHO 3       /* current rho */
+#define NUM_INFO_OBJECTIVE 4 /* sum_j U_j(x_j) at the current x, FP64 */
+#define NUM_INFO_ITERS 5     /* iterations run since creation / reset */
+#define NUM_INFO_STATUS 6    /* 0 running, 1 converged, 2 iteration limit, 3 non-finite */
+#define NUM_INFO_J 7         /* number of terminals nnz + m */
+#define NUM_INFO_LEN 8
+
+/* Copy up to max_rows rows (||r||, ||s||, rho) of the residual history, oldest first, into
+ * the HOST array hist[3 * max_rows]; *rows receives the count (<= the history length). */
+NUM_API int num_get_history(const num_problem* h, double* hist, int64_t max_rows, int64_t* rows);
+
+/* Copy the device-built link-major form of R to HOST arrays: row_ptr int64[m+1] and
+ * col_idx int32[nnz] (each row's stream ids ascending).  For checking the device build. */
+NUM_API int num_get_operator(const num_problem* h, int64_t* row_ptr, int32_t* col_idx);
+
+/* Zero the iteration state and history (x = z = u = 0, rho = rho0, iteration 0). */
+NUM_API int num_reset(num_problem* h);
+
+/* Algorithmic bytes of one iteration, for roofline accounting: what the two fused kernels
+ * must move (every index array once, every state array read and written once, each
+ * gathered vector once).  out[0] = stream kernel, out[1] = link kernel (host doubles). */
+NUM_API int num_iteration_bytes(const num_problem* h, double* out);
+
+/* Per-kernel device time of the iterations run so far (profile = 1 only).  Kernel q of an
+ * iteration (fused paths: 0 = stream kernel, 1 = link kernel; plain path: 0 SpMV-transpose,
+ * 1 stream prox, 2 SpMV, 3 link update, 4-6 reductions, 7 finalize): ms[q] = total
+ * milliseconds between the event before and the event after it, launches[q] = how many
+ * of its launches did work (launches after the stop flag was set are not counted).
+ * Fills min(max_kernels, kernels per iteration) entries of the HOST arrays; *nkernels
+ * receives the number of kernels per iteration. */
+NUM_API int num_get_kernel_times(const num_problem* h, double* ms, int64_t* launches,
+                                 int32_t max_kernels, int32_t* nkernels);
+
+/* Number of kernel launches this library has made in this process so far (every kernel
+ * node of a replayed graph counts as one launch). */
+NUM_API int64_t num_kernel_launches(void);
+
+/* Free every resource of the handle.  NULL is ignored. */
+NUM_API void num_destroy(num_problem* h);
+
+/* Static text for a status code. */
+NUM_API const char* num_strerror(int code);
+
+/* Message of the last failing call on this thread ("" if none). */
+NUM_API const char* num_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NUM_PMP_H */

@@ -1,0 +1,344 @@
+"""Thin Python binding of the C ABI in include/num_pmp.h (argument marshalling only).
+
+Every function here has the name of the C entry point it calls and does no arithmetic of
+its own: arrays are checked for dtype / length and passed by pointer, status codes become
+`NumError` exceptions.  The shared library is loaded from the package's `lib/` folder; if
+it is missing the import of this module fails loudly (there is no fallback path).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "lib", "libnum_pmp.so")
+
+NUM_OK = 0
+NUM_NOT_CONVERGED = 1
+NUM_ERR_INVALID = -1
+NUM_ERR_OOM = -2
+NUM_ERR_CUDA = -3
+NUM_ERR_NUMERIC = -4
+NUM_ERR_STATE = -5
+
+NUM_LOG = 0
+NUM_LINEAR = 1
+
+NUM_FUSED_FP32 = 0
+NUM_FUSED_FP64 = 1
+NUM_PLAIN_FP64 = 2
+
+INFO = dict(primal=0, dual=1, eps_tol=2, rho=3, objective=4, iters=5, status=6, J=7)
+NUM_INFO_LEN = 8
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+RELEASE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
+                              ctypes.c_void_p)
+
+
+class num_allocator(ctypes.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("release", RELEASE_FN), ("ctx", ctypes.c_void_p)]
+
+
+class num_params(ctypes.Structure):
+    _fields_ = [("rho0", ctypes.c_double), ("alpha", ctypes.c_double), ("mu", ctypes.c_double),
+                ("gamma", ctypes.c_double), ("eps_abs", ctypes.c_double),
+                ("rho_period", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("check_every", ctypes.c_int32), ("tile_items", ctypes.c_int32),
+                ("history", ctypes.c_int32), ("use_graph", ctypes.c_int32),
+                ("profile", ctypes.c_int32), ("allocator", ctypes.POINTER(num_allocator))]
+
+
+class NumError(RuntimeError):
+    def __init__(self, code, message):
+        super().__init__(f"{num_strerror(code)} ({code}): {message}")
+        self.code = code
+
+
+def _load():
+    if not os.path.exists(_LIB_PATH):
+        raise ImportError(f"{_LIB_PATH} is missing: build it with "
+                          "`python -m paper_2509_10722_b300.build` (no CPU fallback exists)")
+    lib = ctypes.CDLL(_LIB_PATH)
+    P, i64, i32, d = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double
+    pp = ctypes.POINTER(num_params)
+    sig = {
+        "num_default_params": (None, [pp]),
+        "num_create": (ctypes.c_int, [ctypes.POINTER(P), i64, i64, P, P, P, P, P, P, P, pp, P]),
+        "num_create_device": (ctypes.c_int, [ctypes.POINTER(P), i64, i64, P, P, P, P, P, P, P,
+                                             pp, P]),
+        "num_set_rho_schedule": (ctypes.c_int, [P, P, i64]),
+        "num_solve": (ctypes.c_int, [P, i64, d, ctypes.POINTER(i64)]),
+        "num_get": (ctypes.c_int, [P, P, P, P]),
+        "num_get_device": (ctypes.c_int, [P, P, P, P]),
+        "num_get_history": (ctypes.c_int, [P, P, i64, ctypes.POINTER(i64)]),
+        "num_get_operator": (ctypes.c_int, [P, P, P]),
+        "num_reset": (ctypes.c_int, [P]),
+        "num_iteration_bytes": (ctypes.c_int, [P, P]),
+        "num_get_kernel_times": (ctypes.c_int, [P, P, P, i32, ctypes.POINTER(i32)]),
+        "num_kernel_launches": (ctypes.c_int64, []),
+        "num_destroy": (None, [P]),
+        "num_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+        "num_last_error": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+_lib = _load()
+EXPORTED = ("num_default_params", "num_create", "num_create_device", "num_set_rho_schedule",
+            "num_solve", "num_get", "num_get_device", "num_get_history", "num_get_operator",
+            "num_reset", "num_iteration_bytes", "num_get_kernel_times", "num_kernel_launches",
+            "num_destroy", "num_strerror", "num_last_error")
+
+
+def library():
+    """The loaded ctypes library (for symbol checks)."""
+    return _lib
+
+
+def library_path():
+    return _LIB_PATH
+
+
+def num_strerror(code):
+    return _lib.num_strerror(int(code)).decode()
+
+
+def num_last_error():
+    return _lib.num_last_error().decode()
+
+
+def _check(rc):
+    if rc < 0:
+        raise NumError(rc, num_last_error())
+    return rc
+
+
+def num_default_params(**overrides):
+    p = num_params()
+    _lib.num_default_params(ctypes.byref(p))
+    for k, v in overrides.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+def _host(a, dtype, n, name):
+    a = np.ascontiguousarray(a, dtype=dtype)
+    if a.shape != (n,):
+        raise ValueError(f"{name} must have shape ({n},), got {a.shape}")
+    return a
+
+
+def _hptr(a):
+    return None if a is None else ctypes.c_void_p(a.ctypes.data)
+
+
+def num_create(n, m, route_ptr, route_links, c, utype, w, lo, hi, params=None, stream=None):
+    """Create a handle from host arrays (numpy); returns the handle (a c_void_p)."""
+    n, m = int(n), int(m)
+    rp = _host(route_ptr, np.int64, n + 1, "route_ptr")
+    nnz = int(rp[-1]) if rp[0] == 0 and rp[-1] >= 0 else 0
+    rl = np.ascontiguousarray(route_links, dtype=np.int32)
+    if rl.size < nnz:
+        raise ValueError("route_links shorter than route_ptr[n]")
+    args = [rp, rl, _host(c, np.float64, m, "c"), _host(utype, np.uint8, n, "utype"),
+            _host(w, np.float64, n, "w"),
+            None if lo is None else _host(lo, np.float64, n, "lo"), _host(hi, np.float64, n, "hi")]
+    h = ctypes.c_void_p()
+    keep = params
+    _check(_lib.num_create(ctypes.byref(h), n, m, *[_hptr(a) for a in args],
+                           None if params is None else ctypes.byref(params),
+                           ctypes.c_void_p(stream) if stream else None))
+    del keep
+    return h
+
+
+def _dptr(t, dtype_name, n, name):
+    import torch
+    want = getattr(torch, dtype_name)
+    if t is None:
+        return None
+    if not t.is_cuda or t.dtype != want or t.numel() != n or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous CUDA {dtype_name} tensor of {n} elements")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def num_create_device(n, m, route_ptr, route_links, c, utype, w, lo, hi, params=None,
+                      stream=None):
+    """Create a handle from device arrays (torch CUDA tensors, same layout)."""
+    n, m = int(n), int(m)
+    nnz = int(route_links.numel())
+    ptrs = [_dptr(route_ptr, "int64", n + 1, "route_ptr"),
+            _dptr(route_links, "int32", nnz, "route_links"), _dptr(c, "float64", m, "c"),
+            _dptr(utype, "uint8", n, "utype"), _dptr(w, "float64", n, "w"),
+            _dptr(lo, "float64", n, "lo"), _dptr(hi, "float64", n, "hi")]
+    h = ctypes.c_void_p()
+    _check(_lib.num_create_device(ctypes.byref(h), n, m, *ptrs,
+                                  None if params is None else ctypes.byref(params),
+                                  ctypes.c_void_p(stream) if stream else None))
+    return h
+
+
+def num_set_rho_schedule(h, decisions):
+    d = np.ascontiguousarray(decisions, dtype=np.int8)
+    _check(_lib.num_set_rho_schedule(h, _hptr(d) if d.size else None, d.size))
+
+
+def num_solve(h, max_iters, eps_abs=-1.0):
+    """Returns (status, iterations run): status NUM_OK or NUM_NOT_CONVERGED."""
+    it = ctypes.c_int64(0)
+    rc = _check(_lib.num_solve(h, int(max_iters), float(eps_abs), ctypes.byref(it)))
+    return rc, int(it.value)
+
+
+def num_get(h, n, m, x=True, prices=True):
+    """Host copies: returns (x[n] or None, prices[m] or None, info dict)."""
+    xa = np.empty(n) if x else None
+    pa = np.empty(m) if prices else None
+    info = np.zeros(NUM_INFO_LEN)
+    _check(_lib.num_get(h, _hptr(xa), _hptr(pa), _hptr(info)))
+    return xa, pa, {k: float(info[i]) for k, i in INFO.items()}
+
+
+def num_get_device(h, x=None, prices=None):
+    """Write x / prices into float64 CUDA tensors (either may be None); returns info dict."""
+    info = np.zeros(NUM_INFO_LEN)
+    xp = None if x is None else _dptr(x, "float64", x.numel(), "x")
+    pp = None if prices is None else _dptr(prices, "float64", prices.numel(), "prices")
+    _check(_lib.num_get_device(h, xp, pp, _hptr(info)))
+    return {k: float(info[i]) for k, i in INFO.items()}
+
+
+def num_get_history(h, max_rows):
+    buf = np.zeros((max(int(max_rows), 0), 3))
+    rows = ctypes.c_int64(0)
+    _check(_lib.num_get_history(h, _hptr(buf) if max_rows else None, int(max_rows),
+                                ctypes.byref(rows)))
+    return buf[:rows.value]
+
+
+def num_get_operator(h, m, nnz):
+    rp = np.zeros(m + 1, dtype=np.int64)
+    ci = np.zeros(nnz, dtype=np.int32)
+    _check(_lib.num_get_operator(h, _hptr(rp), _hptr(ci)))
+    return rp, ci
+
+
+def num_reset(h):
+    _check(_lib.num_reset(h))
+
+
+def num_iteration_bytes(h):
+    out = np.zeros(2)
+    _check(_lib.num_iteration_bytes(h, _hptr(out)))
+    return float(out[0]), float(out[1])
+
+
+def num_get_kernel_times(h, max_kernels=8):
+    """Per-kernel (total ms, launches that did work) of the profiled iterations."""
+    ms = np.zeros(max_kernels)
+    cnt = np.zeros(max_kernels, dtype=np.int64)
+    nk = ctypes.c_int32(0)
+    _check(_lib.num_get_kernel_times(h, _hptr(ms), _hptr(cnt), max_kernels, ctypes.byref(nk)))
+    k = min(nk.value, max_kernels)
+    return ms[:k], cnt[:k]
+
+
+def num_kernel_launches():
+    return int(_lib.num_kernel_launches())
+
+
+def num_destroy(h):
+    _lib.num_destroy(h)
+
+
+def torch_allocator():
+    """A num_allocator that takes device memory from PyTorch's caching allocator (the
+    returned object must stay alive as long as the handles that use it)."""
+    import torch
+
+    def _alloc(ctx, nbytes, stream):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), stream=stream or 0)
+        except Exception:
+            return None
+
+    def _release(ctx, ptr, nbytes, stream):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    a = num_allocator(ALLOC_FN(_alloc), RELEASE_FN(_release), None)
+    return a
+
+
+class Problem:
+    """Owner of one handle: `Problem(inst, **params)` with an instance dict as made by
+    `workloads.py`; `device=True` copies the instance to torch CUDA tensors first and uses
+    num_create_device."""
+
+    def __init__(self, inst, device=False, stream=None, use_torch_allocator=False, **params):
+        self.n, self.m = int(inst["n"]), int(inst["m"])
+        self.nnz = int(np.asarray(inst["route_ptr"])[-1])
+        self._alloc = torch_allocator() if use_torch_allocator else None
+        if self._alloc is not None:
+            params["allocator"] = ctypes.pointer(self._alloc)
+        self.params = num_default_params(**params)
+        self.h = None
+        if device:
+            import torch
+            dev = {k: torch.as_tensor(np.ascontiguousarray(inst[k])).cuda()
+                   for k in ("route_ptr", "route_links", "c", "utype", "w", "lo", "hi")}
+            self.h = num_create_device(self.n, self.m, dev["route_ptr"], dev["route_links"],
+                                       dev["c"], dev["utype"], dev["w"], dev["lo"], dev["hi"],
+                                       self.params, stream)
+        else:
+            self.h = num_create(self.n, self.m, inst["route_ptr"], inst["route_links"],
+                                inst["c"], inst["utype"], inst["w"], inst["lo"], inst["hi"],
+                                self.params, stream)
+
+    def solve(self, max_iters, eps_abs=-1.0):
+        return num_solve(self.h, max_iters, eps_abs)
+
+    def get(self, x=True, prices=True):
+        return num_get(self.h, self.n, self.m, x, prices)
+
+    def history(self, max_rows=None):
+        return num_get_history(self.h, self.params.history if max_rows is None else max_rows)
+
+    def operator(self):
+        return num_get_operator(self.h, self.m, self.nnz)
+
+    def set_rho_schedule(self, decisions):
+        num_set_rho_schedule(self.h, decisions)
+
+    def reset(self):
+        num_reset(self.h)
+
+    def iteration_bytes(self):
+        return num_iteration_bytes(self.h)
+
+    def kernel_times(self):
+        return num_get_kernel_times(self.h)
+
+    def close(self):
+        if self.h is not None:
+            num_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

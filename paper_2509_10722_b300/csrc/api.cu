@@ -1,0 +1,825 @@
+// C ABI of the PMP solver (declared in include/num_pmp.h): handle lifetime, device memory,
+// input validation, the CUDA-graph iteration loop and result export.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "num_pmp.h"
+#include "pmp_internal.cuh"
+
+using pmp::Ctl;
+using pmp::View;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string& msg) {
+    g_last_error = msg;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+    return fail(NUM_ERR_CUDA, std::string(what) + ": " + cudaGetErrorName(e) + " (" +
+                                  cudaGetErrorString(e) + ")");
+}
+
+constexpr int kMaxGrid = 8192;
+constexpr int kExportBlocksMax = 1024;
+
+std::atomic<long long> g_launches{0};
+
+}  // namespace
+
+namespace pmp {
+void note_launches(long long count) { g_launches.fetch_add(count, std::memory_order_relaxed); }
+long long launches() { return g_launches.load(std::memory_order_relaxed); }
+}  // namespace pmp
+
+struct num_problem {
+    int64_t n = 0, m = 0, nnz = 0;
+    int Js = 0, Jl = 0;
+    num_params prm{};
+    num_allocator alloc{};
+    bool custom_alloc = false;
+    cudaStream_t user_stream = nullptr;
+    cudaStream_t stream = nullptr;  // where the work goes
+    bool own_stream = false;
+    cudaEvent_t legacy_ev = nullptr;
+    int device = 0;
+    int prec = 0;
+    std::vector<std::pair<void*, size_t>> blocks;
+
+    int *col_ptr = nullptr, *row_idx = nullptr, *row_ptr = nullptr, *col_idx = nullptr;
+    int2 *tiles_s = nullptr, *tiles_l = nullptr;
+    int ntiles_s = 0, ntiles_l = 0, tile_s = 0, tile_l = 0, grid_s = 0, grid_l = 0;
+    void *wt = nullptr, *lo = nullptr, *hi = nullptr, *c = nullptr;
+    void *x = nullptr, *Z = nullptr, *pby = nullptr, *zs = nullptr, *Rx = nullptr, *ps = nullptr;
+    void *carry_s = nullptr, *carry_l = nullptr;
+    int *arrive_s = nullptr, *arrive_l = nullptr;
+    double *part_s = nullptr, *part_l = nullptr;
+    int plain_nb = 0;
+    void *A = nullptr, *B = nullptr, *tS = nullptr, *tR = nullptr, *tL = nullptr, *RxN = nullptr,
+         *pbar = nullptr, *y = nullptr;
+    Ctl* ctl = nullptr;
+    Ctl* ctl_host = nullptr;  // pinned
+    double* hist = nullptr;
+    signed char* sched = nullptr;
+    int sched_len = 0;
+    double* x64 = nullptr;
+    double* y64 = nullptr;
+    double* part_exp = nullptr;
+    int exp_blocks = 0;
+    int box_uniform = 0;
+    double lo_u = 0.0, hi_u = 0.0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    double last_eps_tol = 0.0;
+    // profiling: evs[0] before the first kernel of a batch of iterations, then one event
+    // after every kernel; per-kernel totals
+    std::vector<cudaEvent_t> evs;
+    double kernel_ms[pmp::kPlainKernelsPerIter] = {};
+    long long kernel_runs[pmp::kPlainKernelsPerIter] = {};
+    int kpi = 0;  // kernels per iteration
+};
+
+namespace {
+
+void* dev_alloc(num_problem* h, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    void* p = nullptr;
+    if (h->custom_alloc) {
+        p = h->alloc.alloc(h->alloc.ctx, bytes, (void*)h->user_stream);
+    } else {
+        if (cudaMalloc(&p, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            p = nullptr;
+        }
+    }
+    if (p) h->blocks.emplace_back(p, bytes);
+    return p;
+}
+
+void dev_free(num_problem* h, void* p) {
+    if (!p) return;
+    for (size_t i = 0; i < h->blocks.size(); ++i) {
+        if (h->blocks[i].first == p) {
+            if (h->custom_alloc)
+                h->alloc.release(h->alloc.ctx, p, h->blocks[i].second, (void*)h->stream);
+            else
+                cudaFree(p);
+            h->blocks.erase(h->blocks.begin() + i);
+            return;
+        }
+    }
+}
+
+void destroy_handle(num_problem* h) {
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
+    if (h->graph) cudaGraphDestroy(h->graph);
+    while (!h->blocks.empty()) dev_free(h, h->blocks.back().first);
+    if (h->ctl_host) cudaFreeHost(h->ctl_host);
+    for (cudaEvent_t ev : h->evs) cudaEventDestroy(ev);
+    if (h->legacy_ev) cudaEventDestroy(h->legacy_ev);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    delete h;
+}
+
+// Work submitted by the caller to the legacy default stream before this call must finish
+// before the handle's own stream runs (the handle's stream is a non-blocking one then).
+cudaError_t order_after_legacy(num_problem* h) {
+    if (!h->own_stream) return cudaSuccess;
+    cudaError_t e = cudaEventRecord(h->legacy_ev, cudaStreamLegacy);
+    if (e != cudaSuccess) return e;
+    return cudaStreamWaitEvent(h->stream, h->legacy_ev, 0);
+}
+
+template <typename T>
+View<T> make_view(const num_problem* h) {
+    View<T> v;
+    std::memset(&v, 0, sizeof(v));
+    v.n = (int)h->n;
+    v.m = (int)h->m;
+    v.nnz = (int)h->nnz;
+    v.Js = h->Js;
+    v.Jl = h->Jl;
+    v.col_ptr = h->col_ptr;
+    v.row_idx = h->row_idx;
+    v.row_ptr = h->row_ptr;
+    v.col_idx = h->col_idx;
+    v.tiles_s = h->tiles_s;
+    v.tiles_l = h->tiles_l;
+    v.ntiles_s = h->ntiles_s;
+    v.ntiles_l = h->ntiles_l;
+    v.tile_s = h->tile_s;
+    v.tile_l = h->tile_l;
+    v.wt = (const T*)h->wt;
+    v.lo = (const T*)h->lo;
+    v.hi = (const T*)h->hi;
+    v.lo_u = (T)h->lo_u;
+    v.hi_u = (T)h->hi_u;
+    v.box_uniform = h->box_uniform;
+    v.c = (const T*)h->c;
+    v.x = (T*)h->x;
+    v.Z = (T*)h->Z;
+    v.pby = (typename View<T>::T2*)h->pby;
+    v.zs = (T*)h->zs;
+    v.Rx = (T*)h->Rx;
+    v.ps = (T*)h->ps;
+    v.carry_s = (typename View<T>::T2*)h->carry_s;
+    v.carry_l = (T*)h->carry_l;
+    v.arrive_s = h->arrive_s;
+    v.arrive_l = h->arrive_l;
+    v.part_s = h->part_s;
+    v.part_l = h->part_l;
+    v.grid_s = h->grid_s;
+    v.grid_l = h->grid_l;
+    v.ctl = h->ctl;
+    v.hist = h->hist;
+    v.sched = h->sched;
+    v.A = (T*)h->A;
+    v.B = (T*)h->B;
+    v.tS = (T*)h->tS;
+    v.tR = (T*)h->tR;
+    v.tL = (T*)h->tL;
+    v.RxN = (T*)h->RxN;
+    v.pbar = (T*)h->pbar;
+    v.y = (T*)h->y;
+    return v;
+}
+
+// Enqueue `count` iterations (count <= check_every when profiling).  Not counted as
+// launches here: the caller counts what actually executes.
+cudaError_t run_iterations(num_problem* h, int count) {
+    const bool prof = h->prm.profile != 0;
+    if (prof) {
+        cudaError_t e = cudaEventRecord(h->evs[0], h->stream);
+        if (e != cudaSuccess) return e;
+    }
+    for (int i = 0; i < count; ++i) {
+        cudaEvent_t* ev = prof ? h->evs.data() + 1 + (size_t)i * h->kpi : nullptr;
+        cudaError_t e;
+        if (h->prec == NUM_FUSED_FP32)
+            e = pmp::fused_iteration<float>(make_view<float>(h), h->stream, ev);
+        else if (h->prec == NUM_FUSED_FP64)
+            e = pmp::fused_iteration<double>(make_view<double>(h), h->stream, ev);
+        else
+            e = pmp::plain_iteration(make_view<double>(h), h->plain_nb, h->stream, ev);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+// After a batch of iterations completed (stream synchronized): add the per-kernel times of
+// the first `ran` iterations of the batch (the later ones exited at the stop flag).
+cudaError_t accumulate_kernel_times(num_problem* h, long long ran) {
+    for (long long i = 0; i < ran; ++i) {
+        for (int q = 0; q < h->kpi; ++q) {
+            const size_t cur = 1 + (size_t)i * h->kpi + q;
+            float ms = 0.f;
+            cudaError_t e = cudaEventElapsedTime(&ms, h->evs[cur - 1], h->evs[cur]);
+            if (e != cudaSuccess) return e;
+            h->kernel_ms[q] += ms;
+            h->kernel_runs[q] += 1;
+        }
+    }
+    return cudaSuccess;
+}
+
+cudaError_t zero_state(num_problem* h) {
+    const size_t ts = h->prec == NUM_FUSED_FP32 ? 4 : 8;
+    cudaStream_t st = h->stream;
+    cudaError_t e = cudaSuccess;
+    auto z = [&](void* p, size_t bytes) {
+        if (p && e == cudaSuccess) e = cudaMemsetAsync(p, 0, bytes, st);
+    };
+    z(h->x, ts * h->n);
+    z(h->Z, ts * h->n);
+    z(h->pby, 2 * ts * h->m);
+    z(h->zs, ts * h->m);
+    z(h->Rx, ts * h->m);
+    z(h->ps, ts * h->m);
+    z(h->pbar, ts * h->m);
+    z(h->y, ts * h->m);
+    z(h->arrive_s, sizeof(int) * (size_t)h->ntiles_s);
+    z(h->arrive_l, sizeof(int) * (size_t)h->ntiles_l);
+    if (h->hist && h->prm.history > 0) z(h->hist, sizeof(double) * 3 * (size_t)h->prm.history);
+    if (e != cudaSuccess) return e;
+    e = pmp::ctl_reset(h->ctl, h->prm.rho0, h->prm.alpha, h->prm.mu, h->prm.gamma,
+                       h->prm.rho_period, h->prm.history, st);
+    if (e != cudaSuccess) return e;
+    if (h->sched_len > 0) e = pmp::ctl_set_schedule_len(h->ctl, h->sched_len, st);
+    return e;
+}
+
+bool is_pow2_tile(int t) { return t >= 256 && t <= 8192 && (t & (t - 1)) == 0; }
+
+int check_params(const num_params& p) {
+    if (!(p.rho0 > 0.0) || !std::isfinite(p.rho0))
+        return fail(NUM_ERR_INVALID, "rho0 must be finite and > 0");
+    if (!(p.alpha > 0.0 && p.alpha < 2.0)) return fail(NUM_ERR_INVALID, "alpha must be in (0, 2)");
+    if (!(p.mu >= 1.0) || !std::isfinite(p.mu)) return fail(NUM_ERR_INVALID, "mu must be >= 1");
+    if (!(p.gamma >= 1.0) || !std::isfinite(p.gamma))
+        return fail(NUM_ERR_INVALID, "gamma must be >= 1");
+    if (std::isnan(p.eps_abs)) return fail(NUM_ERR_INVALID, "eps_abs is NaN");
+    if (p.rho_period < 0) return fail(NUM_ERR_INVALID, "rho_period must be >= 0");
+    if (p.precision < 0 || p.precision > 2) return fail(NUM_ERR_INVALID, "unknown precision");
+    if (p.check_every < 1) return fail(NUM_ERR_INVALID, "check_every must be >= 1");
+    if (p.tile_items != 0 && !is_pow2_tile(p.tile_items))
+        return fail(NUM_ERR_INVALID, "tile_items must be 0 or a power of two in [256, 8192]");
+    if (p.history < 0) return fail(NUM_ERR_INVALID, "history must be >= 0");
+    if (p.profile != 0 && p.profile != 1) return fail(NUM_ERR_INVALID, "profile must be 0 or 1");
+    if (p.allocator && (!p.allocator->alloc || !p.allocator->release))
+        return fail(NUM_ERR_INVALID, "allocator needs alloc and release");
+    return NUM_OK;
+}
+
+std::string describe_bits(int bits) {
+    std::string s;
+    auto add = [&](int b, const char* t) {
+        if (bits & b) s += (s.empty() ? "" : "; ") + std::string(t);
+    };
+    add(pmp::VB_ROUTE, "route_ptr must start at 0 and increase (every route nonempty)");
+    add(pmp::VB_LINK_ID, "a link id is outside [0, m)");
+    add(pmp::VB_DUPLICATE, "a link appears twice in one route");
+    add(pmp::VB_CAPACITY, "a capacity is not finite and > 0");
+    add(pmp::VB_WEIGHT, "a weight is not finite and > 0");
+    add(pmp::VB_UTYPE, "a utility type is not NUM_LOG or NUM_LINEAR");
+    add(pmp::VB_BOX, "a box is not finite with lo <= hi (and hi > 0 for log utility)");
+    return s;
+}
+
+int create_impl(num_problem** out, int64_t n, int64_t m, const int64_t* route_ptr,
+                const int32_t* route_links, const double* c, const uint8_t* utype,
+                const double* w, const double* lo, const double* hi, const num_params* p,
+                void* cuda_stream, bool on_device) {
+    g_last_error.clear();
+    if (!out) return fail(NUM_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    if (!route_ptr || !route_links || !c || !utype || !w || !hi)
+        return fail(NUM_ERR_INVALID, "a required array is NULL");
+    if (n < 1 || m < 1) return fail(NUM_ERR_INVALID, "n and m must be >= 1");
+    if (n > INT32_MAX - 1 || m > INT32_MAX - 1)
+        return fail(NUM_ERR_INVALID, "n and m must be < 2^31 - 1");
+    num_params prm;
+    if (p)
+        prm = *p;
+    else
+        num_default_params(&prm);
+    int rc = check_params(prm);
+    if (rc != NUM_OK) return rc;
+
+    int64_t p0 = 0, nnz = 0;
+    if (on_device) {
+        cudaError_t e = cudaMemcpy(&p0, route_ptr, sizeof(int64_t), cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(&nnz, route_ptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(e, "reading route_ptr");
+    } else {
+        p0 = route_ptr[0];
+        nnz = route_ptr[n];
+    }
+    if (p0 != 0) return fail(NUM_ERR_INVALID, "route_ptr[0] must be 0");
+    if (nnz < n) return fail(NUM_ERR_INVALID, "route_ptr[n] < n: some route is empty");
+    if (nnz + (n > m ? n : m) > (int64_t)INT32_MAX - 1)
+        return fail(NUM_ERR_INVALID, "nnz + max(n, m) must be < 2^31 - 1");
+
+    num_problem* h = new (std::nothrow) num_problem();
+    if (!h) return fail(NUM_ERR_OOM, "host allocation failed");
+    h->n = n;
+    h->m = m;
+    h->nnz = nnz;
+    h->Js = (int)(nnz + n);
+    h->Jl = (int)(nnz + m);
+    h->prm = prm;
+    h->prec = prm.precision;
+    h->user_stream = (cudaStream_t)cuda_stream;
+    if (prm.allocator) {
+        h->alloc = *prm.allocator;
+        h->custom_alloc = true;
+    }
+    h->prm.allocator = nullptr;
+
+    const bool fp32 = h->prec == NUM_FUSED_FP32;
+    const bool plain = h->prec == NUM_PLAIN_FP64;
+    const size_t ts = fp32 ? 4 : 8;
+    const size_t N = (size_t)n, M = (size_t)m, NNZ = (size_t)nnz;
+    h->tile_s = prm.tile_items ? prm.tile_items : pmp::fused_tile_items_stream(fp32 ? 0 : 1);
+    h->tile_l = prm.tile_items ? prm.tile_items : pmp::fused_tile_items_link(fp32 ? 0 : 1);
+    h->ntiles_s = (int)((h->Js + (int64_t)h->tile_s - 1) / h->tile_s);
+    h->ntiles_l = (int)((h->Jl + (int64_t)h->tile_l - 1) / h->tile_l);
+    h->plain_nb = pmp::plain_partial_blocks((int)n, (int)m);
+    h->exp_blocks = pmp::export_partial_blocks((int)n);
+
+    // ---- device memory: the handle's arrays, then the transient build buffers ----
+    bool ok = true;
+    auto A = [&](size_t bytes) -> void* {
+        if (!ok) return nullptr;
+        void* q = dev_alloc(h, bytes);
+        if (!q) ok = false;
+        return q;
+    };
+    h->col_ptr = (int*)A(4 * (N + 1));
+    h->row_idx = (int*)A(4 * NNZ);
+    h->row_ptr = (int*)A(4 * (M + 1));
+    h->col_idx = (int*)A(4 * NNZ);
+    h->wt = A(ts * N);
+    h->lo = A(ts * N);
+    h->hi = A(ts * N);
+    h->c = A(ts * M);
+    h->x = A(ts * N);
+    h->Z = A(ts * N);
+    h->zs = A(ts * M);
+    h->Rx = A(ts * M);
+    h->ps = A(ts * M);
+    if (plain) {
+        h->pbar = A(ts * M);
+        h->y = A(ts * M);
+        h->A = A(ts * N);
+        h->B = A(ts * N);
+        h->tS = A(ts * N);
+        h->tR = A(ts * M);
+        h->tL = A(ts * M);
+        h->RxN = A(ts * M);
+    } else {
+        h->pby = A(2 * ts * M);
+        h->tiles_s = (int2*)A(sizeof(int2) * (size_t)h->ntiles_s);
+        h->tiles_l = (int2*)A(sizeof(int2) * (size_t)h->ntiles_l);
+        h->carry_s = A(2 * ts * 2 * (size_t)h->ntiles_s);
+        h->carry_l = A(ts * 2 * (size_t)h->ntiles_l);
+        h->arrive_s = (int*)A(sizeof(int) * (size_t)h->ntiles_s);
+        h->arrive_l = (int*)A(sizeof(int) * (size_t)h->ntiles_l);
+    }
+    const size_t npart = (size_t)(kMaxGrid > h->plain_nb ? kMaxGrid : h->plain_nb);
+    h->part_s = (double*)A(sizeof(double) * npart);
+    h->part_l = (double*)A(sizeof(double) * 2 * npart);
+    h->ctl = (Ctl*)A(sizeof(Ctl));
+    h->hist = (double*)A(sizeof(double) * 3 * (size_t)(prm.history > 0 ? prm.history : 1));
+    h->x64 = (double*)A(8 * N);
+    h->y64 = (double*)A(8 * M);
+    h->part_exp = (double*)A(sizeof(double) * kExportBlocksMax);
+    // transient
+    int64_t* d_rp = nullptr;
+    int* d_rl = nullptr;
+    double *d_c = nullptr, *d_w = nullptr, *d_lo = nullptr, *d_hi = nullptr;
+    uint8_t* d_ut = nullptr;
+    if (!on_device) {
+        d_rp = (int64_t*)A(8 * (N + 1));
+        d_rl = (int*)A(4 * NNZ);
+        d_c = (double*)A(8 * M);
+        d_w = (double*)A(8 * N);
+        d_lo = lo ? (double*)A(8 * N) : nullptr;
+        d_hi = (double*)A(8 * N);
+        d_ut = (uint8_t*)A(N);
+    }
+    int* d_err = (int*)A(sizeof(int) * 2);
+    unsigned long long* d_box = (unsigned long long*)A(sizeof(unsigned long long) * 4);
+    pmp::Scratch s{};
+    s.keys_a = (int*)A(4 * NNZ);
+    s.vals_a = (int*)A(4 * NNZ);
+    s.keys_b = (int*)A(4 * NNZ);
+    s.vals_b = (int*)A(4 * NNZ);
+    s.hist_len = pmp::radix_hist_len((int)nnz);
+    s.scan_tmp_len = pmp::scan_tmp_len(s.hist_len);
+    s.hist = (int*)A(4 * s.hist_len);
+    s.scan_tmp = (int*)A(4 * s.scan_tmp_len);
+    if (!ok) {
+        destroy_handle(h);
+        return fail(NUM_ERR_OOM, "device allocation failed");
+    }
+
+    // ---- from here on: CUDA work ----
+    cudaError_t e;
+#define CK(call, what)                          \
+    do {                                        \
+        e = (call);                             \
+        if (e != cudaSuccess) {                 \
+            destroy_handle(h);                  \
+            return cuda_fail(e, what);          \
+        }                                       \
+    } while (0)
+    CK(cudaGetDevice(&h->device), "cudaGetDevice");
+    if (h->user_stream == nullptr) {
+        CK(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking), "cudaStreamCreate");
+        h->own_stream = true;
+        CK(cudaEventCreateWithFlags(&h->legacy_ev, cudaEventDisableTiming), "cudaEventCreate");
+    } else {
+        h->stream = h->user_stream;
+    }
+    CK(cudaHostAlloc((void**)&h->ctl_host, sizeof(Ctl), cudaHostAllocDefault), "cudaHostAlloc");
+    h->kpi = plain ? pmp::kPlainKernelsPerIter : pmp::kFusedKernelsPerIter;
+    if (prm.profile) {
+        h->evs.resize(1 + (size_t)prm.check_every * h->kpi, nullptr);
+        for (auto& ev : h->evs) CK(cudaEventCreate(&ev), "cudaEventCreate");
+    }
+    CK(order_after_legacy(h), "ordering after the default stream");
+    cudaStream_t st = h->stream;
+    if (!on_device) {
+        CK(cudaMemcpyAsync(d_rp, route_ptr, 8 * (N + 1), cudaMemcpyHostToDevice, st), "copy route_ptr");
+        CK(cudaMemcpyAsync(d_rl, route_links, 4 * NNZ, cudaMemcpyHostToDevice, st), "copy route_links");
+        CK(cudaMemcpyAsync(d_c, c, 8 * M, cudaMemcpyHostToDevice, st), "copy c");
+        CK(cudaMemcpyAsync(d_w, w, 8 * N, cudaMemcpyHostToDevice, st), "copy w");
+        if (lo) CK(cudaMemcpyAsync(d_lo, lo, 8 * N, cudaMemcpyHostToDevice, st), "copy lo");
+        CK(cudaMemcpyAsync(d_hi, hi, 8 * N, cudaMemcpyHostToDevice, st), "copy hi");
+        CK(cudaMemcpyAsync(d_ut, utype, N, cudaMemcpyHostToDevice, st), "copy utype");
+        route_ptr = d_rp;
+        route_links = d_rl;
+        c = d_c;
+        w = d_w;
+        lo = d_lo;
+        hi = d_hi;
+        utype = d_ut;
+    }
+    CK(cudaMemsetAsync(d_err, 0, sizeof(int) * 2, st), "memset");
+    CK(pmp::validate_inputs((int)n, (int)m, route_ptr, route_links, c, utype, w, lo, hi, d_err,
+                            d_box, st),
+       "validating the inputs");
+    int err_bits = 0;
+    unsigned long long box[4];
+    CK(cudaMemcpyAsync(&err_bits, d_err, sizeof(int), cudaMemcpyDeviceToHost, st), "read flags");
+    CK(cudaMemcpyAsync(box, d_box, sizeof(box), cudaMemcpyDeviceToHost, st), "read box");
+    CK(cudaStreamSynchronize(st), "validation");
+    if (err_bits) {
+        destroy_handle(h);
+        return fail(NUM_ERR_INVALID, describe_bits(err_bits));
+    }
+    CK(pmp::build_operator((int)n, (int)m, (int)nnz, route_ptr, route_links, h->col_ptr,
+                           h->row_idx, h->row_ptr, h->col_idx, s, d_err, st),
+       "building the operator");
+    CK(cudaMemcpyAsync(&err_bits, d_err, sizeof(int), cudaMemcpyDeviceToHost, st), "read flags");
+    CK(cudaStreamSynchronize(st), "operator build");
+    if (err_bits) {
+        destroy_handle(h);
+        return fail(NUM_ERR_INVALID, describe_bits(err_bits));
+    }
+    const double lmin = pmp::ordered_key_to_double(box[0]), lmax = pmp::ordered_key_to_double(box[1]);
+    const double hmin = pmp::ordered_key_to_double(box[2]), hmax = pmp::ordered_key_to_double(box[3]);
+    h->box_uniform = (lmin == lmax && hmin == hmax) ? 1 : 0;
+    h->lo_u = lmin;
+    h->hi_u = hmin;
+    if (fp32)
+        CK(pmp::convert_params<float>((int)n, (int)m, c, utype, w, lo, hi, (float*)h->c,
+                                      (float*)h->wt, (float*)h->lo, (float*)h->hi, st),
+           "converting parameters");
+    else
+        CK(pmp::convert_params<double>((int)n, (int)m, c, utype, w, lo, hi, (double*)h->c,
+                                       (double*)h->wt, (double*)h->lo, (double*)h->hi, st),
+           "converting parameters");
+    if (!plain) {
+        CK(pmp::build_tiles(h->col_ptr, (int)n, h->Js, h->tile_s, h->ntiles_s, h->tiles_s, st),
+           "stream tiles");
+        CK(pmp::build_tiles(h->row_ptr, (int)m, h->Jl, h->tile_l, h->ntiles_l, h->tiles_l, st),
+           "link tiles");
+        CK(pmp::fused_grids(fp32 ? 0 : 1, h->tile_s, h->tile_l, h->ntiles_s, h->ntiles_l,
+                            &h->grid_s, &h->grid_l),
+           "sizing the fused grids");
+    }
+    CK(zero_state(h), "zeroing the state");
+    CK(cudaStreamSynchronize(st), "setup");
+    // release the transient buffers
+    for (void* q : {(void*)d_rp, (void*)d_rl, (void*)d_c, (void*)d_w, (void*)d_lo, (void*)d_hi,
+                    (void*)d_ut, (void*)d_err, (void*)d_box, (void*)s.keys_a, (void*)s.vals_a,
+                    (void*)s.keys_b, (void*)s.vals_b, (void*)s.hist, (void*)s.scan_tmp})
+        dev_free(h, q);
+#undef CK
+    *out = h;
+    return NUM_OK;
+}
+
+int finish_cuda(cudaError_t e, const char* what) {
+    if (e != cudaSuccess) return cuda_fail(e, what);
+    return NUM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void num_default_params(num_params* p) {
+    if (!p) return;
+    p->rho0 = 1.0;
+    p->alpha = 1.6;
+    p->mu = 2.0;
+    p->gamma = 1.1;
+    p->eps_abs = 1e-4;
+    p->rho_period = 50;
+    p->precision = NUM_FUSED_FP32;
+    p->check_every = 50;
+    p->tile_items = 0;
+    p->history = 4096;
+    p->use_graph = 1;
+    p->profile = 0;
+    p->allocator = nullptr;
+}
+
+int num_create(num_problem** out, int64_t n, int64_t m, const int64_t* route_ptr,
+               const int32_t* route_links, const double* c, const uint8_t* utype,
+               const double* w, const double* lo, const double* hi, const num_params* p,
+               void* cuda_stream) {
+    return create_impl(out, n, m, route_ptr, route_links, c, utype, w, lo, hi, p, cuda_stream,
+                       false);
+}
+
+int num_create_device(num_problem** out, int64_t n, int64_t m, const int64_t* route_ptr,
+                      const int32_t* route_links, const double* c, const uint8_t* utype,
+                      const double* w, const double* lo, const double* hi,
+                      const num_params* p, void* cuda_stream) {
+    return create_impl(out, n, m, route_ptr, route_links, c, utype, w, lo, hi, p, cuda_stream,
+                       true);
+}
+
+int num_set_rho_schedule(num_problem* h, const int8_t* decisions, int64_t count) {
+    g_last_error.clear();
+    if (!h) return fail(NUM_ERR_INVALID, "handle is NULL");
+    if (count < 0 || count > INT32_MAX || (count > 0 && !decisions))
+        return fail(NUM_ERR_INVALID, "bad schedule");
+    for (int64_t i = 0; i < count; ++i)
+        if (decisions[i] < -1 || decisions[i] > 1)
+            return fail(NUM_ERR_INVALID, "schedule entries must be -1, 0 or +1");
+    cudaError_t e = order_after_legacy(h);
+    if (e != cudaSuccess) return cuda_fail(e, "ordering");
+    if (h->sched) {
+        cudaStreamSynchronize(h->stream);
+        dev_free(h, h->sched);
+        h->sched = nullptr;
+    }
+    h->sched_len = 0;
+    if (count > 0) {
+        h->sched = (signed char*)dev_alloc(h, (size_t)count);
+        if (!h->sched) return fail(NUM_ERR_OOM, "device allocation failed");
+        e = cudaMemcpyAsync(h->sched, decisions, (size_t)count, cudaMemcpyHostToDevice, h->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "copy schedule");
+        h->sched_len = (int)count;
+    }
+    // graphs captured the old schedule pointer
+    if (h->graph_exec) {
+        cudaGraphExecDestroy(h->graph_exec);
+        h->graph_exec = nullptr;
+    }
+    if (h->graph) {
+        cudaGraphDestroy(h->graph);
+        h->graph = nullptr;
+    }
+    e = pmp::ctl_set_schedule_len(h->ctl, h->sched_len, h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "schedule");
+    return finish_cuda(cudaStreamSynchronize(h->stream), "schedule");
+}
+
+int num_solve(num_problem* h, int64_t max_iters, double eps_abs, int64_t* iters_done) {
+    g_last_error.clear();
+    if (iters_done) *iters_done = 0;
+    if (!h) return fail(NUM_ERR_INVALID, "handle is NULL");
+    if (max_iters < 0) return fail(NUM_ERR_INVALID, "max_iters must be >= 0");
+    if (std::isnan(eps_abs)) return fail(NUM_ERR_INVALID, "eps_abs is NaN");
+    cudaStream_t st = h->stream;
+    cudaError_t e = order_after_legacy(h);
+    if (e != cudaSuccess) return cuda_fail(e, "ordering");
+    e = cudaMemcpyAsync(h->ctl_host, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "reading the control block");
+    const long long k0 = h->ctl_host->k;
+    if (max_iters == 0) return NUM_NOT_CONVERGED;
+    const double eps = eps_abs > 0.0 ? eps_abs : (eps_abs < 0.0 ? h->prm.eps_abs : 0.0);
+    const double eps_tol = eps > 0.0 ? eps * std::sqrt((double)(h->nnz + h->m)) : 0.0;
+    h->last_eps_tol = eps_tol;
+    e = pmp::ctl_arm(h->ctl, k0 + max_iters, eps_tol, st);
+    if (e != cudaSuccess) return cuda_fail(e, "arming the control block");
+    const int K = h->prm.check_every;
+    if (h->prm.use_graph && !h->graph_exec) {
+        e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
+        cudaError_t e2 = run_iterations(h, K);
+        e = cudaStreamEndCapture(st, &h->graph);
+        if (e2 != cudaSuccess) return cuda_fail(e2, "capturing the iteration graph");
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+        e = cudaGraphInstantiate(&h->graph_exec, h->graph, 0);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+    }
+    const long long max_launches = (max_iters + K - 1) / K + 1;
+    for (long long it = 0;; ++it) {
+        if (it >= max_launches) return fail(NUM_ERR_STATE, "the iteration limit was not honoured");
+        const long long k_before = h->ctl_host->k;
+        if (h->prm.use_graph)
+            e = cudaGraphLaunch(h->graph_exec, st);
+        else
+            e = run_iterations(h, K);
+        if (e != cudaSuccess) return cuda_fail(e, "launching iterations");
+        pmp::note_launches((long long)K * h->kpi);
+        e = cudaMemcpyAsync(h->ctl_host, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_fail(e, "iterations");
+        if (h->prm.profile) {
+            e = accumulate_kernel_times(h, h->ctl_host->k - k_before);
+            if (e != cudaSuccess) return cuda_fail(e, "reading kernel times");
+        }
+        if (h->ctl_host->stop != pmp::RUNNING) break;
+    }
+    if (iters_done) *iters_done = h->ctl_host->k - k0;
+    switch (h->ctl_host->stop) {
+        case pmp::CONVERGED: return NUM_OK;
+        case pmp::LIMIT: return NUM_NOT_CONVERGED;
+        default: return fail(NUM_ERR_NUMERIC, "a residual became non-finite");
+    }
+}
+
+static int get_impl(const num_problem* hc, double* x, double* prices, double* info, bool dev) {
+    g_last_error.clear();
+    if (!hc) return fail(NUM_ERR_INVALID, "handle is NULL");
+    num_problem* h = const_cast<num_problem*>(hc);
+    cudaStream_t st = h->stream;
+    cudaError_t e = order_after_legacy(h);
+    if (e != cudaSuccess) return cuda_fail(e, "ordering");
+    double* xo = dev ? x : (x ? h->x64 : nullptr);
+    double* yo = dev ? prices : (prices ? h->y64 : nullptr);
+    if (h->prec == NUM_FUSED_FP32)
+        e = pmp::export_solution<float>(make_view<float>(h), xo, yo, h->part_exp, h->exp_blocks, st);
+    else
+        e = pmp::export_solution<double>(make_view<double>(h), xo, yo, h->part_exp,
+                                         h->exp_blocks, st);
+    if (e != cudaSuccess) return cuda_fail(e, "exporting the solution");
+    if (!dev) {
+        if (x) e = cudaMemcpyAsync(x, h->x64, 8 * (size_t)h->n, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess && prices)
+            e = cudaMemcpyAsync(prices, h->y64, 8 * (size_t)h->m, cudaMemcpyDeviceToHost, st);
+        if (e != cudaSuccess) return cuda_fail(e, "copying the solution");
+    }
+    e = cudaMemcpyAsync(h->ctl_host, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "reading the results");
+    if (info) {
+        const Ctl& c = *h->ctl_host;
+        info[NUM_INFO_PRIMAL] = c.rnorm;
+        info[NUM_INFO_DUAL] = c.snorm;
+        info[NUM_INFO_EPS_TOL] = h->last_eps_tol;
+        info[NUM_INFO_RHO] = c.rho;
+        info[NUM_INFO_OBJECTIVE] = c.objective;
+        info[NUM_INFO_ITERS] = (double)c.k;
+        info[NUM_INFO_STATUS] = (double)c.stop;
+        info[NUM_INFO_J] = (double)(h->nnz + h->m);
+    }
+    return NUM_OK;
+}
+
+int num_get(const num_problem* h, double* x, double* prices, double* info) {
+    return get_impl(h, x, prices, info, false);
+}
+
+int num_get_device(const num_problem* h, double* x, double* prices, double* info) {
+    return get_impl(h, x, prices, info, true);
+}
+
+int num_get_history(const num_problem* hc, double* hist, int64_t max_rows, int64_t* rows) {
+    g_last_error.clear();
+    if (rows) *rows = 0;
+    if (!hc) return fail(NUM_ERR_INVALID, "handle is NULL");
+    if (max_rows < 0 || (max_rows > 0 && !hist)) return fail(NUM_ERR_INVALID, "bad buffer");
+    num_problem* h = const_cast<num_problem*>(hc);
+    const int H = h->prm.history;
+    std::vector<double> ring((size_t)3 * (H > 0 ? H : 1));
+    cudaError_t e = order_after_legacy(h);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h->ctl_host, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess && H > 0)
+        e = cudaMemcpyAsync(ring.data(), h->hist, sizeof(double) * 3 * (size_t)H,
+                            cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "reading the history");
+    const long long k = h->ctl_host->k;
+    long long have = H > 0 ? (k < H ? k : H) : 0;
+    if (have > max_rows) have = max_rows;
+    for (long long i = 0; i < have; ++i) {
+        const long long it = k - have + i;  // 0-based iteration index
+        const double* src = ring.data() + 3 * (it % H);
+        hist[3 * i] = src[0];
+        hist[3 * i + 1] = src[1];
+        hist[3 * i + 2] = src[2];
+    }
+    if (rows) *rows = have;
+    return NUM_OK;
+}
+
+int num_get_operator(const num_problem* hc, int64_t* row_ptr, int32_t* col_idx) {
+    g_last_error.clear();
+    if (!hc || !row_ptr || !col_idx) return fail(NUM_ERR_INVALID, "NULL argument");
+    num_problem* h = const_cast<num_problem*>(hc);
+    std::vector<int> rp((size_t)h->m + 1);
+    cudaError_t e = order_after_legacy(h);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(rp.data(), h->row_ptr, 4 * rp.size(), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(col_idx, h->col_idx, 4 * (size_t)h->nnz, cudaMemcpyDeviceToHost,
+                            h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "reading the operator");
+    for (size_t i = 0; i < rp.size(); ++i) row_ptr[i] = rp[i];
+    return NUM_OK;
+}
+
+int num_reset(num_problem* h) {
+    g_last_error.clear();
+    if (!h) return fail(NUM_ERR_INVALID, "handle is NULL");
+    cudaError_t e = order_after_legacy(h);
+    if (e == cudaSuccess) e = zero_state(h);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    return finish_cuda(e, "reset");
+}
+
+int num_iteration_bytes(const num_problem* h, double* out) {
+    g_last_error.clear();
+    if (!h || !out) return fail(NUM_ERR_INVALID, "NULL argument");
+    const double ts = h->prec == NUM_FUSED_FP32 ? 4.0 : 8.0;
+    const double n = (double)h->n, m = (double)h->m, nnz = (double)h->nnz;
+    const double box = h->box_uniform ? 0.0 : 2.0 * ts * n;
+    // stream kernel: col_ptr, route entries, x and Z read + written, weights, box,
+    // the (pbar, y) vector gathered once
+    out[0] = 4.0 * (n + 1) + 4.0 * nnz + ts * (4.0 * n + n) + box + 2.0 * ts * m;
+    // link kernel: row_ptr, link entries, x gathered once, link state read
+    // (pbar, y, zs, Rx, ps, c) and written (pbar, y, zs, Rx, ps)
+    out[1] = 4.0 * (m + 1) + 4.0 * nnz + ts * n + ts * 11.0 * m;
+    return NUM_OK;
+}
+
+int num_get_kernel_times(const num_problem* h, double* ms, int64_t* launches,
+                         int32_t max_kernels, int32_t* nkernels) {
+    g_last_error.clear();
+    if (!h) return fail(NUM_ERR_INVALID, "handle is NULL");
+    if (max_kernels < 0 || (max_kernels > 0 && (!ms || !launches)))
+        return fail(NUM_ERR_INVALID, "bad buffers");
+    if (nkernels) *nkernels = h->kpi;
+    for (int q = 0; q < h->kpi && q < max_kernels; ++q) {
+        ms[q] = h->kernel_ms[q];
+        launches[q] = h->kernel_runs[q];
+    }
+    return NUM_OK;
+}
+
+int64_t num_kernel_launches(void) { return pmp::launches(); }
+
+void num_destroy(num_problem* h) { destroy_handle(h); }
+
+const char* num_strerror(int code) {
+    switch (code) {
+        case NUM_OK: return "ok";
+        case NUM_NOT_CONVERGED: return "iteration limit reached before the stopping test passed";
+        case NUM_ERR_INVALID: return "invalid argument or instance";
+        case NUM_ERR_OOM: return "device allocation failed";
+        case NUM_ERR_CUDA: return "CUDA runtime error";
+        case NUM_ERR_NUMERIC: return "non-finite residual";
+        case NUM_ERR_STATE: return "call not valid in this state";
+        default: return "unknown status code";
+    }
+}
+
+const char* num_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

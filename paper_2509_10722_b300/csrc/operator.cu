@@ -1,0 +1,488 @@
+// Setup of one NUM instance on the device: input validation, the link-major (CSR) copy of
+// the 0/1 link-route matrix R of Sec. II built from its routes (CSC) by a stable radix sort,
+// the tile tables of the fused kernels, parameter conversion, and the small control and
+// export kernels.  None of this runs per iteration.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cmath>
+#include <cstring>
+
+#include "pmp_device.cuh"
+#include "pmp_internal.cuh"
+
+namespace pmp {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+inline int blocks_for(long long count, int per_block = kThreads, int cap = 1 << 20) {
+    long long b = (count + per_block - 1) / per_block;
+    if (b < 1) b = 1;
+    if (b > cap) b = cap;
+    return (int)b;
+}
+
+// order-preserving map of a double onto unsigned 64-bit keys (for atomic min / max)
+__device__ __forceinline__ unsigned long long ordered_key(double v) {
+    unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    return (b & 0x8000000000000000ull) ? ~b : (b | 0x8000000000000000ull);
+}
+
+__global__ void k_validate_streams(int n, const int64_t* __restrict__ route_ptr,
+                                   const uint8_t* __restrict__ utype,
+                                   const double* __restrict__ w, const double* __restrict__ lo,
+                                   const double* __restrict__ hi, int* err,
+                                   unsigned long long* box) {
+    int bits = 0;
+    unsigned long long lo_min = ~0ull, lo_max = 0ull, hi_min = ~0ull, hi_max = 0ull;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+        const int64_t p0 = route_ptr[j], p1 = route_ptr[j + 1];
+        if (p1 <= p0 || (j == 0 && p0 != 0)) bits |= VB_ROUTE;
+        const double wj = w[j];
+        if (!(wj > 0.0) || !isfinite(wj)) bits |= VB_WEIGHT;
+        const uint8_t t = utype[j];
+        if (t > 1) bits |= VB_UTYPE;
+        const double l = lo ? lo[j] : 0.0, h = hi[j];
+        if (!isfinite(l) || !isfinite(h) || l > h || (t == 0 && !(h > 0.0))) bits |= VB_BOX;
+        const unsigned long long kl = ordered_key(l), kh = ordered_key(h);
+        lo_min = kl < lo_min ? kl : lo_min;
+        lo_max = kl > lo_max ? kl : lo_max;
+        hi_min = kh < hi_min ? kh : hi_min;
+        hi_max = kh > hi_max ? kh : hi_max;
+    }
+    if (bits) atomicOr(err, bits);
+    atomicMin(box + 0, lo_min);
+    atomicMax(box + 1, lo_max);
+    atomicMin(box + 2, hi_min);
+    atomicMax(box + 3, hi_max);
+}
+
+__global__ void k_validate_links(int m, long long nnz, const int* __restrict__ route_links,
+                                 const double* __restrict__ c, int* err) {
+    int bits = 0;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nnz; e += stride) {
+        const int l = route_links[e];
+        if (l < 0 || l >= m) bits |= VB_LINK_ID;
+    }
+    for (long long l = blockIdx.x * (long long)blockDim.x + threadIdx.x; l < m; l += stride) {
+        const double cl = c[l];
+        if (!(cl > 0.0) || !isfinite(cl)) bits |= VB_CAPACITY;
+    }
+    if (bits) atomicOr(err, bits);
+}
+
+__global__ void k_init_box(unsigned long long* box) {
+    box[0] = ~0ull;
+    box[1] = 0ull;
+    box[2] = ~0ull;
+    box[3] = 0ull;
+}
+
+// CSC pointer to int32, and the stream id of every route entry (the sort's payload)
+__global__ void k_expand_routes(int n, const int64_t* __restrict__ route_ptr, int* col_ptr,
+                                int* stream_of) {
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j <= n; j += gridDim.x * blockDim.x) {
+        const int p0 = (int)route_ptr[j];
+        col_ptr[j] = p0;
+        if (j < n) {
+            const int p1 = (int)route_ptr[j + 1];
+            for (int e = p0; e < p1; ++e) stream_of[e] = j;
+        }
+    }
+}
+
+// ---- stable LSD radix sort of (link id, stream id) pairs by link id ----------------------------
+constexpr int kRadixBits = 8;
+constexpr int kRadix = 1 << kRadixBits;
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 16;
+constexpr int kSortTile = kSortThreads * kSortItems;
+
+__global__ void __launch_bounds__(kSortThreads)
+k_radix_hist(const int* __restrict__ keys, int count, int shift, int* hist, int nblocks) {
+    __shared__ int cnt[kRadix];
+    cnt[threadIdx.x] = 0;
+    __syncthreads();
+    const int base = blockIdx.x * kSortTile;
+#pragma unroll 4
+    for (int k = 0; k < kSortItems; ++k) {
+        const int e = base + k * kSortThreads + threadIdx.x;
+        if (e < count) atomicAdd(&cnt[(keys[e] >> shift) & (kRadix - 1)], 1);
+    }
+    __syncthreads();
+    hist[(size_t)threadIdx.x * nblocks + blockIdx.x] = cnt[threadIdx.x];
+}
+
+// Scatter with the offsets of an exclusive scan of the digit-major histogram.  Within a
+// block, keys are ranked in their original order (rounds of 256 in order; inside a round,
+// warps in order and lanes in order), which makes every pass stable.
+__global__ void __launch_bounds__(kSortThreads)
+k_radix_scatter(const int* __restrict__ keys_in, const int* __restrict__ vals_in, int count,
+                int shift, const int* __restrict__ offs, int nblocks, int* keys_out,
+                int* vals_out) {
+    constexpr int kWarps = kSortThreads / 32;
+    __shared__ int run[kRadix];
+    __shared__ int wcnt[kWarps][kRadix];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    run[tid] = offs[(size_t)tid * nblocks + blockIdx.x];
+    const unsigned lt_mask = (1u << lane) - 1u;
+    const int base = blockIdx.x * kSortTile;
+    for (int k = 0; k < kSortItems; ++k) {
+        for (int i = tid; i < kWarps * kRadix; i += kSortThreads) (&wcnt[0][0])[i] = 0;
+        __syncthreads();
+        const int e = base + k * kSortThreads + tid;
+        const bool valid = e < count;
+        const int key = valid ? keys_in[e] : 0;
+        const int d = valid ? ((key >> shift) & (kRadix - 1)) : kRadix;  // kRadix: no digit
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        const int rank = __popc(peers & lt_mask);
+        if (valid && rank == 0) wcnt[warp][d] = __popc(peers);
+        __syncthreads();
+        int total = 0;
+        for (int w = 0; w < kWarps; ++w) {  // exclusive prefix over warps of digit `tid`
+            const int cw = wcnt[w][tid];
+            wcnt[w][tid] = total;
+            total += cw;
+        }
+        __syncthreads();
+        if (valid) {
+            const int pos = run[d] + wcnt[warp][d] + rank;
+            keys_out[pos] = key;
+            vals_out[pos] = vals_in[e];
+        }
+        __syncthreads();
+        run[tid] += total;
+    }
+}
+
+// ---- exclusive scan of int32 (values and total < 2^31) ----------------------------------------
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 16;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+__global__ void __launch_bounds__(kScanThreads)
+k_scan_tiles(const int* in, int* out, size_t len, int* tile_sums) {  // in may equal out
+    __shared__ int wsum[kScanThreads / 32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const size_t base = (size_t)blockIdx.x * kScanTile + (size_t)tid * kScanItems;
+    int v[kScanItems];
+    int s = 0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        v[i] = (base + i < len) ? in[base + i] : 0;
+        s += v[i];
+    }
+    int incl = s;  // inclusive scan of the thread sums
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    int wbase = 0;
+    for (int w = 0; w < warp; ++w) wbase += wsum[w];
+    int run = wbase + incl - s;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        if (base + i < len) out[base + i] = run;
+        run += v[i];
+    }
+    if (tid == kScanThreads - 1 && tile_sums) tile_sums[blockIdx.x] = wbase + incl;
+}
+
+__global__ void k_scan_add(int* out, size_t len, const int* __restrict__ tile_offs) {
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < len; i += stride)
+        out[i] += tile_offs[i / kScanTile];
+}
+
+cudaError_t scan_exclusive(const int* in, int* out, size_t len, int* tmp, cudaStream_t st) {
+    const size_t tiles = (len + kScanTile - 1) / kScanTile;
+    if (tiles <= 1) {
+        k_scan_tiles<<<1, kScanThreads, 0, st>>>(in, out, len, nullptr);
+        note_launches(1);
+        return cudaGetLastError();
+    }
+    int* sums = tmp;
+    int* sums_scanned = tmp + tiles;
+    k_scan_tiles<<<(unsigned)tiles, kScanThreads, 0, st>>>(in, out, len, sums);
+    note_launches(1);
+    cudaError_t e = scan_exclusive(sums, sums_scanned, tiles, tmp + 2 * tiles, st);
+    if (e != cudaSuccess) return e;
+    k_scan_add<<<blocks_for((long long)len, kThreads, 65535), kThreads, 0, st>>>(out, len,
+                                                                                 sums_scanned);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+// row_ptr from link ids sorted ascending: row_ptr[l] = first position with key >= l
+__global__ void k_row_ptr(const int* __restrict__ keys, int nnz, int m, int* row_ptr) {
+    const int stride = gridDim.x * blockDim.x;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e <= nnz; e += stride) {
+        const int prev = e == 0 ? -1 : keys[e - 1];
+        const int cur = e == nnz ? m : keys[e];
+        for (int l = prev + 1; l <= cur; ++l) row_ptr[l] = e;
+    }
+}
+
+// a duplicate link in one route shows up as two equal (link, stream) pairs side by side
+__global__ void k_find_duplicates(const int* __restrict__ keys, const int* __restrict__ vals,
+                                  int nnz, int* err) {
+    const int stride = gridDim.x * blockDim.x;
+    bool dup = false;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x + 1; e < nnz; e += stride)
+        dup |= (keys[e] == keys[e - 1]) && (vals[e] == vals[e - 1]);
+    if (dup) atomicOr(err, VB_DUPLICATE);
+}
+
+// row containing item j of the item space where row r holds items
+// [ptr[r] + r, ptr[r+1] + r] (its entries, then one row-end item)
+__device__ __forceinline__ int row_of_item(const int* ptr, int nrows, int j) {
+    int lo = 0, hi = nrows - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (ptr[mid] + mid <= j)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void k_tiles(const int* __restrict__ ptr, int nrows, int J, int tile, int ntiles,
+                        int2* tiles) {
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ntiles; t += gridDim.x * blockDim.x) {
+        const long long j0 = (long long)t * tile;
+        const long long j1 = j0 + tile < J ? j0 + tile : J;
+        tiles[t] = make_int2(row_of_item(ptr, nrows, (int)j0), row_of_item(ptr, nrows, (int)(j1 - 1)));
+    }
+}
+
+template <typename T>
+__global__ void k_convert(int n, int m, const double* __restrict__ c,
+                          const uint8_t* __restrict__ utype, const double* __restrict__ w,
+                          const double* __restrict__ lo, const double* __restrict__ hi, T* c_t,
+                          T* wt_t, T* lo_t, T* hi_t) {
+    const int stride = gridDim.x * blockDim.x;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
+        const T wj = (T)w[j];
+        wt_t[j] = utype[j] == 0 ? wj : -wj;
+        if (lo_t) lo_t[j] = lo ? (T)lo[j] : T(0);
+        if (hi_t) hi_t[j] = (T)hi[j];
+    }
+    for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < m; l += stride) c_t[l] = (T)c[l];
+}
+
+__global__ void k_ctl_arm(Ctl* ctl, long long k_limit, double eps_tol) {
+    ctl->k_limit = k_limit;
+    ctl->eps_tol = eps_tol;
+    ctl->stop = RUNNING;
+}
+
+__global__ void k_ctl_reset(Ctl* ctl, double rho0, double alpha, double mu, double gamma,
+                            int period, int hist_len) {
+    Ctl c;
+    memset(&c, 0, sizeof(c));
+    c.rho = rho0;
+    c.alpha = alpha;
+    c.mu = mu;
+    c.gamma = gamma;
+    c.period = period;
+    c.hist_len = hist_len;
+    *ctl = c;
+}
+
+__global__ void k_ctl_sched(Ctl* ctl, int len) { ctl->sched_len = len; }
+
+// ---- solution export ------------------------------------------------------------------------
+constexpr int kExportThreads = 256;
+
+template <typename T>
+__global__ void __launch_bounds__(kExportThreads)
+k_export(View<T> v, double* x_out, double* y_out, double* part) {
+    __shared__ double red[kExportThreads / 32];
+    double obj = 0.0;
+    const int stride = gridDim.x * blockDim.x;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < v.n; j += stride) {
+        const double xj = (double)v.x[j];
+        const double wt = (double)v.wt[j];
+        if (x_out) x_out[j] = xj;
+        obj += wt > 0.0 ? wt * log(xj) : -wt * xj;  // U_j(x_j), Sec. II
+    }
+    if (y_out) {
+        for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < v.m; l += stride)
+            y_out[l] = v.y ? (double)v.y[l] : (double)v.pby[l].y;
+    }
+    const double s = block_sum(obj, red);
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = s;
+        __threadfence();
+        const unsigned t = atomicAdd(&v.ctl->ticket2, 1u);
+        red[0] = (t == gridDim.x - 1) ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    if (red[0] != 0.0) {  // last block: FP64 sum of the block partials in block order
+        __syncthreads();
+        __threadfence();
+        const double tot = block_sum_global(part, gridDim.x, 1, red);
+        if (threadIdx.x == 0) {
+            v.ctl->objective = tot;
+            v.ctl->ticket2 = 0;
+        }
+    }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------------
+
+size_t radix_hist_len(int nnz) {
+    const size_t nblocks = ((size_t)nnz + kSortTile - 1) / kSortTile;
+    return (nblocks < 1 ? 1 : nblocks) * kRadix;
+}
+
+size_t scan_tmp_len(size_t len) {
+    size_t total = 0;
+    size_t tiles = (len + kScanTile - 1) / kScanTile;
+    while (tiles > 1) {
+        total += 2 * tiles;
+        tiles = (tiles + kScanTile - 1) / kScanTile;
+    }
+    return total + 2;
+}
+
+double ordered_key_to_double(unsigned long long k) {
+    unsigned long long b = (k & 0x8000000000000000ull) ? (k & ~0x8000000000000000ull) : ~k;
+    double d;
+    std::memcpy(&d, &b, sizeof d);
+    return d;
+}
+
+cudaError_t validate_inputs(int n, int m, const int64_t* route_ptr, const int* route_links,
+                            const double* c, const uint8_t* utype, const double* w,
+                            const double* lo, const double* hi, int* err_bits,
+                            unsigned long long* box_minmax, cudaStream_t st) {
+    k_init_box<<<1, 1, 0, st>>>(box_minmax);
+    note_launches(1);
+    k_validate_streams<<<blocks_for(n, kThreads, 4096), kThreads, 0, st>>>(
+        n, route_ptr, utype, w, lo, hi, err_bits, box_minmax);
+    note_launches(1);
+    int64_t nnz_host = 0;
+    cudaError_t e = cudaMemcpyAsync(&nnz_host, route_ptr + n, sizeof(int64_t),
+                                    cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return e;
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return e;
+    k_validate_links<<<blocks_for(nnz_host > m ? nnz_host : m, kThreads, 8192), kThreads, 0, st>>>(
+        m, (long long)nnz_host, route_links, c, err_bits);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t build_operator(int n, int m, int nnz, const int64_t* route_ptr,
+                           const int* route_links, int* col_ptr, int* row_idx, int* row_ptr,
+                           int* col_idx, const Scratch& s, int* err_bits, cudaStream_t st) {
+    cudaError_t e;
+    k_expand_routes<<<blocks_for(n + 1, kThreads, 65535), kThreads, 0, st>>>(n, route_ptr, col_ptr,
+                                                                              s.vals_a);
+    note_launches(1);
+    if ((e = cudaMemcpyAsync(row_idx, route_links, sizeof(int) * (size_t)nnz,
+                             cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
+        return e;
+    if ((e = cudaMemcpyAsync(s.keys_a, route_links, sizeof(int) * (size_t)nnz,
+                             cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
+        return e;
+    int bits = 0;
+    while (bits < 31 && (1ll << bits) < (long long)m) ++bits;
+    const int passes = (bits + kRadixBits - 1) / kRadixBits;
+    int *ki = s.keys_a, *vi = s.vals_a, *ko = s.keys_b, *vo = s.vals_b;
+    const int nblocks = nnz > 0 ? (nnz + kSortTile - 1) / kSortTile : 0;
+    for (int p = 0; p < passes && nblocks > 0; ++p) {
+        const int shift = p * kRadixBits;
+        k_radix_hist<<<nblocks, kSortThreads, 0, st>>>(ki, nnz, shift, s.hist, nblocks);
+        note_launches(1);
+        if ((e = scan_exclusive(s.hist, s.hist, (size_t)nblocks * kRadix, s.scan_tmp, st)) !=
+            cudaSuccess)
+            return e;
+        k_radix_scatter<<<nblocks, kSortThreads, 0, st>>>(ki, vi, nnz, shift, s.hist, nblocks, ko,
+                                                          vo);
+        note_launches(1);
+        int* t;
+        t = ki; ki = ko; ko = t;
+        t = vi; vi = vo; vo = t;
+    }
+    if ((e = cudaMemcpyAsync(col_idx, vi, sizeof(int) * (size_t)nnz, cudaMemcpyDeviceToDevice,
+                             st)) != cudaSuccess)
+        return e;
+    k_row_ptr<<<blocks_for((long long)nnz + 1, kThreads, 65535), kThreads, 0, st>>>(ki, nnz, m,
+                                                                                    row_ptr);
+    note_launches(1);
+    if (nnz > 1)
+        k_find_duplicates<<<blocks_for(nnz, kThreads, 8192), kThreads, 0, st>>>(ki, vi, nnz,
+                                                                                err_bits);
+        note_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t build_tiles(const int* ptr, int nrows, int J, int tile, int ntiles, int2* tiles,
+                        cudaStream_t st) {
+    k_tiles<<<blocks_for(ntiles, kThreads, 65535), kThreads, 0, st>>>(ptr, nrows, J, tile, ntiles,
+                                                                      tiles);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t convert_params(int n, int m, const double* c, const uint8_t* utype,
+                           const double* w, const double* lo, const double* hi, T* c_t,
+                           T* wt_t, T* lo_t, T* hi_t, cudaStream_t st) {
+    k_convert<T><<<blocks_for(n > m ? n : m, kThreads, 65535), kThreads, 0, st>>>(
+        n, m, c, utype, w, lo, hi, c_t, wt_t, lo_t, hi_t);
+    note_launches(1);
+    return cudaGetLastError();
+}
+template cudaError_t convert_params<float>(int, int, const double*, const uint8_t*,
+                                           const double*, const double*, const double*, float*,
+                                           float*, float*, float*, cudaStream_t);
+template cudaError_t convert_params<double>(int, int, const double*, const uint8_t*,
+                                            const double*, const double*, const double*,
+                                            double*, double*, double*, double*, cudaStream_t);
+
+int export_partial_blocks(int n) { return blocks_for(n, kExportThreads, 1024); }
+
+template <typename T>
+cudaError_t export_solution(const View<T>& v, double* x_out, double* y_out, double* part,
+                            int part_blocks, cudaStream_t st) {
+    k_export<T><<<part_blocks, kExportThreads, 0, st>>>(v, x_out, y_out, part);
+    note_launches(1);
+    return cudaGetLastError();
+}
+template cudaError_t export_solution<float>(const View<float>&, double*, double*, double*, int,
+                                            cudaStream_t);
+template cudaError_t export_solution<double>(const View<double>&, double*, double*, double*,
+                                             int, cudaStream_t);
+
+cudaError_t ctl_arm(Ctl* ctl, long long k_limit, double eps_tol, cudaStream_t st) {
+    k_ctl_arm<<<1, 1, 0, st>>>(ctl, k_limit, eps_tol);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t ctl_reset(Ctl* ctl, double rho0, double alpha, double mu, double gamma, int period,
+                      int hist_len, cudaStream_t st) {
+    k_ctl_reset<<<1, 1, 0, st>>>(ctl, rho0, alpha, mu, gamma, period, hist_len);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t ctl_set_schedule_len(Ctl* ctl, int len, cudaStream_t st) {
+    k_ctl_sched<<<1, 1, 0, st>>>(ctl, len);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+}  // namespace pmp

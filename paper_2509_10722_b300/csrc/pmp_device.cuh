@@ -1,0 +1,117 @@
+// Inline device helpers shared by the kernels of the PMP solver (header-only so that each
+// translation unit gets its own copy without relocatable device code).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "pmp_internal.cuh"
+
+namespace pmp {
+
+// ---- small vector arithmetic on the gathered types --------------------------------------------
+__device__ __forceinline__ float vzero(float) { return 0.f; }
+__device__ __forceinline__ double vzero(double) { return 0.0; }
+__device__ __forceinline__ float2 vzero(float2) { return make_float2(0.f, 0.f); }
+__device__ __forceinline__ double2 vzero(double2) { return make_double2(0.0, 0.0); }
+__device__ __forceinline__ float vadd(float a, float b) { return a + b; }
+__device__ __forceinline__ double vadd(double a, double b) { return a + b; }
+__device__ __forceinline__ float2 vadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 vadd(double2 a, double2 b) {
+    return make_double2(a.x + b.x, a.y + b.y);
+}
+
+// ---- reductions --------------------------------------------------------------------------------
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Sum of v over the block, valid in thread 0.  Fixed order (deterministic).  `red` holds
+// at least blockDim.x / 32 doubles.  Contains __syncthreads.
+__device__ __forceinline__ double block_sum(double v, double* red) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    v = warp_sum(v);
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < nw; ++i) s += red[i];
+    return s;
+}
+
+// Sum over the block of a[0..count) of a global array (strided per thread, then a block
+// reduction), bypassing L1 so values written by other blocks of the same launch are seen.
+__device__ __forceinline__ double block_sum_global(const double* a, int count, int stride,
+                                                   double* red) {
+    double s = 0.0;
+    for (int i = threadIdx.x; i < count; i += blockDim.x) s += __ldcg(a + (size_t)i * stride);
+    return block_sum(s, red);
+}
+
+// ---- the end-of-iteration step -----------------------------------------------------------------
+// Given the complete sums r2 = ||r||^2 and s2 = ||s||^2 / rho^2 of this iteration: the
+// residual norms of Sec. III-F, the stopping test ||r|| < eps_tol and ||s|| < eps_tol,
+// and every `period` iterations the residual balancing of Eq. rho-update (or the forced
+// schedule); the dual rescale of Eq. dual-rescale is implicit because prices are stored
+// unscaled (y = rho u).  Single thread.
+__device__ __forceinline__ void finalize_iteration(Ctl* ctl, double r2, double s2,
+                                                   double* hist, const signed char* sched) {
+    const double rho = ctl->rho;
+    const long long k = ctl->k + 1;
+    const double rn = sqrt(r2 > 0.0 ? r2 : 0.0);
+    const double sn = rho * sqrt(s2 > 0.0 ? s2 : 0.0);
+    ctl->rnorm = rn;
+    ctl->snorm = sn;
+    ctl->k = k;
+    if (ctl->hist_len > 0) {
+        double* h = hist + 3 * ((k - 1) % ctl->hist_len);
+        h[0] = rn;
+        h[1] = sn;
+        h[2] = rho;
+    }
+    int stop = RUNNING;
+    if (!isfinite(rn) || !isfinite(sn)) {
+        stop = NONFINITE;
+    } else if (ctl->eps_tol > 0.0 && rn < ctl->eps_tol && sn < ctl->eps_tol) {
+        stop = CONVERGED;
+    } else {
+        if (ctl->period > 0 && k % ctl->period == 0) {
+            int dec;
+            if (ctl->n_updates < ctl->sched_len)
+                dec = sched[ctl->n_updates];
+            else
+                dec = rn > ctl->mu * sn ? 1 : (sn > ctl->mu * rn ? -1 : 0);
+            ctl->n_updates += 1;
+            if (dec > 0)
+                ctl->rho = rho * ctl->gamma;
+            else if (dec < 0)
+                ctl->rho = rho / ctl->gamma;
+        }
+        if (k >= ctl->k_limit) stop = LIMIT;
+    }
+    ctl->stop = stop;
+}
+
+// ---- proximal operators of Sec. III-E in the iteration precision --------------------------------
+// Stream prox: the minimizer over [lo, hi] of -U(x) + (rho/2) sum_t (x - zeta_t)^2, which
+// depends on zeta only through S = sum_t zeta_t.  wt > 0: U = wt log x, the positive root
+// of rho L x^2 - rho S x - wt = 0 (evaluated without cancellation for S < 0); wt < 0:
+// U = |wt| x, x = (S + |wt| / rho) / L.  inv_rho = 1 / rho.
+template <typename T>
+__device__ __forceinline__ T stream_prox(T S, T L, T wt, T inv_rho, T lo, T hi) {
+    T xn;
+    if (wt > T(0)) {
+        const T wr = wt * inv_rho;
+        const T D = S * S + T(4) * wr * L;
+        const T sq = sqrt(D);
+        xn = S >= T(0) ? (S + sq) / (T(2) * L) : (T(2) * wr) / (sq - S);
+    } else {
+        xn = (S - wt * inv_rho) / L;
+    }
+    xn = xn < lo ? lo : xn;  // comparisons (not fmin/fmax) so that a NaN propagates
+    return xn > hi ? hi : xn;
+}
+
+}  // namespace pmp

@@ -1,0 +1,171 @@
+// Internal declarations shared by the CUDA translation units of the PMP solver.
+//
+// State layout (the exact per-stream / per-link form of the per-terminal ADMM of
+// Sec. III-D..G; see the derivation in fused.cu):
+//   streams (n):  x_j rate, Z_j = sum of the link-side copies z over stream j's terminals,
+//                 wt_j = +w_j (log utility) or -w_j (linear utility), box lo_j / hi_j
+//   links   (m):  (pbar_l, y_l) interleaved (link average and price y = rho u),
+//                 zs_l (slack terminal's z), Rx_l and ps_l of the previous iteration, c_l
+// The operator R is kept twice, as 32-bit index arrays without values: CSC (routes,
+// stream-major) for the stream kernel and CSR (link-major, stream ids ascending in a row)
+// for the link kernel.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace pmp {
+
+// Iteration control block, one per handle, in device memory.  Written by the finalize step
+// at the end of every iteration and read by every kernel at entry (stop flag, rho).
+struct Ctl {
+    double rho;        // penalty used by the next iteration
+    double rnorm;      // ||r||_2 of the last iteration
+    double snorm;      // ||s||_2 of the last iteration
+    double eps_tol;    // stop when both norms are below it; <= 0 disables the test
+    double alpha, mu, gamma;
+    double objective;  // sum U_j(x_j), written by the objective reduction
+    long long k;       // iterations done since creation / reset
+    long long k_limit; // the run stops when k reaches it
+    long long n_updates;  // rho update points passed
+    int stop;          // 0 running, 1 converged, 2 iteration limit, 3 non-finite residual
+    int period;        // rho update period (0 = never)
+    int sched_len;     // entries of the forced rho schedule
+    int hist_len;      // entries of the residual ring buffer
+    unsigned int ticket;  // last-block-done counter of the link kernel
+    unsigned int ticket2; // last-block-done counter of the reductions
+};
+
+enum Stop { RUNNING = 0, CONVERGED = 1, LIMIT = 2, NONFINITE = 3 };
+
+template <typename T> struct Pair;
+template <> struct Pair<float> { using type = float2; };
+template <> struct Pair<double> { using type = double2; };
+
+// Everything a fused or plain kernel needs, passed by value.
+template <typename T>
+struct View {
+    using T2 = typename Pair<T>::type;
+    int n, m, nnz;
+    int Js, Jl;                 // item counts of the two tiled spaces: nnz + n, nnz + m
+    const int* col_ptr;         // CSC [n+1]
+    const int* row_idx;         // CSC [nnz] link of each route entry
+    const int* row_ptr;         // CSR [m+1]
+    const int* col_idx;         // CSR [nnz] stream of each link entry
+    const int2* tiles_s;        // stream-kernel tiles: (first row, last row)
+    const int2* tiles_l;        // link-kernel tiles
+    int ntiles_s, ntiles_l, tile_s, tile_l;
+    const T* wt;                // signed weights
+    const T* lo;                // per-stream box (unused when box_uniform)
+    const T* hi;
+    T lo_u, hi_u;
+    int box_uniform;
+    const T* c;
+    T* x;
+    T* Z;
+    T2* pby;                    // (pbar, y)
+    T* zs;
+    T* Rx;
+    T* ps;
+    T2* carry_s;                // split-row partial sums, 2 per tile
+    T* carry_l;
+    int* arrive_s;              // split-row arrival counters, 1 per tile
+    int* arrive_l;
+    double* part_s;             // per-block residual partials of the stream kernel [grid_s]
+    double* part_l;             // ... of the link kernel [2 * grid_l]
+    int grid_s, grid_l;
+    Ctl* ctl;
+    double* hist;
+    const signed char* sched;
+    // plain FP64 path only
+    T* A;                       // sum of pbar over each route
+    T* B;                       // sum of y over each route
+    T* tS;                      // per-stream dual-residual term
+    T* tR;                      // per-link primal-residual term
+    T* tL;                      // per-link dual-residual term
+    T* RxN;                     // this iteration's R x
+    T* pbar;                    // split arrays of the plain path
+    T* y;
+};
+
+// ---- launchers (fused.cu) -------------------------------------------------------------------
+// Tile sizes used by the fused kernels for each precision and kernel.
+int fused_tile_items_stream(int precision);
+int fused_tile_items_link(int precision);
+size_t fused_smem_stream(int precision, int tile);
+size_t fused_smem_link(int precision, int tile);
+// Pick persistent grid sizes (<= ntiles) from the occupancy of each kernel.
+cudaError_t fused_grids(int precision, int tile_s, int tile_l, int ntiles_s, int ntiles_l,
+                        int* grid_s, int* grid_l);
+// One iteration on stream st.  If evs is not NULL, evs[q] is recorded on st right after
+// the q-th kernel of the iteration (for per-kernel timing).
+template <typename T>
+cudaError_t fused_iteration(const View<T>& v, cudaStream_t st, cudaEvent_t* evs);
+cudaError_t plain_iteration(const View<double>& v, int plain_blocks, cudaStream_t st,
+                            cudaEvent_t* evs);
+constexpr int kFusedKernelsPerIter = 2;
+constexpr int kPlainKernelsPerIter = 8;
+
+// Process-wide count of kernel launches made by this library (graph replays count every
+// kernel node they run).
+void note_launches(long long count);
+long long launches();
+int plain_partial_blocks(int n, int m);
+
+// ---- operator and state (operator.cu) -------------------------------------------------------
+// Error bits of the device-side validation.
+enum ValidationBits {
+    VB_ROUTE = 1,     // route_ptr not increasing (an empty route) or not starting at 0
+    VB_LINK_ID = 2,   // link id outside [0, m)
+    VB_DUPLICATE = 4, // a link twice in one route
+    VB_CAPACITY = 8,  // c not finite or <= 0
+    VB_WEIGHT = 16,   // w not finite or <= 0
+    VB_UTYPE = 32,    // utility type not 0 or 1
+    VB_BOX = 64,      // lo / hi not finite, lo > hi, or hi <= 0 for a log stream
+};
+
+struct Scratch {  // transient buffers of the operator build, caller-allocated
+    int* keys_a; int* vals_a; int* keys_b; int* vals_b;
+    int* hist;     // radix histogram / scan buffer
+    int* scan_tmp; // block sums of the scans
+    size_t hist_len, scan_tmp_len;
+};
+
+size_t radix_hist_len(int nnz);
+size_t scan_tmp_len(size_t len);
+
+// Validate the inputs; *err_bits (device int) accumulates ValidationBits; box_minmax
+// (device unsigned long long[4]) receives order-preserving keys of min lo, max lo, min hi,
+// max hi.
+cudaError_t validate_inputs(int n, int m, const int64_t* route_ptr, const int* route_links,
+                            const double* c, const uint8_t* utype, const double* w,
+                            const double* lo, const double* hi, int* err_bits,
+                            unsigned long long* box_minmax, cudaStream_t st);
+// Build the CSC int32 pointer, and the CSR (row_ptr, col_idx) by a stable device radix sort.
+// Also flags duplicates (VB_DUPLICATE) into err_bits.
+cudaError_t build_operator(int n, int m, int nnz, const int64_t* route_ptr,
+                           const int* route_links, int* col_ptr, int* row_idx, int* row_ptr,
+                           int* col_idx, const Scratch& s, int* err_bits, cudaStream_t st);
+// (first row, last row) of every tile of `tile` items over the item space of a pointer
+// array with one extra item per row (J = ptr[nrows] + nrows).
+cudaError_t build_tiles(const int* ptr, int nrows, int J, int tile, int ntiles, int2* tiles,
+                        cudaStream_t st);
+// Convert parameters to the iteration precision.
+template <typename T>
+cudaError_t convert_params(int n, int m, const double* c, const uint8_t* utype,
+                           const double* w, const double* lo, const double* hi, T* c_t,
+                           T* wt_t, T* lo_t, T* hi_t, cudaStream_t st);
+double ordered_key_to_double(unsigned long long k);
+// x (T) -> double copies; objective partials and its FP64 reduction into ctl->objective.
+template <typename T>
+cudaError_t export_solution(const View<T>& v, double* x_out, double* y_out, double* part,
+                            int part_blocks, cudaStream_t st);
+int export_partial_blocks(int n);
+
+// Small control kernels.
+cudaError_t ctl_arm(Ctl* ctl, long long k_limit, double eps_tol, cudaStream_t st);
+cudaError_t ctl_reset(Ctl* ctl, double rho0, double alpha, double mu, double gamma, int period,
+                      int hist_len, cudaStream_t st);
+cudaError_t ctl_set_schedule_len(Ctl* ctl, int len, cudaStream_t st);
+
+}  // namespace pmp

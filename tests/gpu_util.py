@@ -1,0 +1,46 @@
+"""Helpers of the GPU tests: run the CUDA path through the C ABI, run the oracle, compare."""
+from __future__ import annotations
+
+import numpy as np
+
+import oracle
+
+PREC = {"fp32": 0, "fp64": 1, "plain": 2}
+
+
+def run_gpu(inst, iters, precision="fp64", eps=0.0, schedule=None, device=False, **params):
+    from paper_2509_10722_b300 import capi
+    params.setdefault("history", max(int(iters), 1))
+    with capi.Problem(inst, device=device, precision=PREC[precision], **params) as p:
+        if schedule is not None:
+            p.set_rho_schedule(schedule)
+        status, done = p.solve(iters, eps)
+        x, lam, info = p.get()
+        hist = p.history()
+    return dict(x=x, lam=lam, info=info, hist=hist, status=status, iters=done)
+
+
+def rel(a, b):
+    a = np.asarray(a, float)
+    b = np.asarray(b, float)
+    nb = np.linalg.norm(b)
+    return float(np.linalg.norm(a - b) / (nb if nb > 0 else 1.0))
+
+
+def max_abs_rel(a, b, floor):
+    """max |a - b| / max(|b|, floor * max|b|): elementwise error with a floor."""
+    a = np.asarray(a, float)
+    b = np.asarray(b, float)
+    scale = np.maximum(np.abs(b), floor * max(np.max(np.abs(b)), 1e-300))
+    return float(np.max(np.abs(a - b) / scale))
+
+
+def compare(gpu, ref, tol, floor=1e-3):
+    """Relative-norm and floored elementwise errors of x and prices; returns a dict."""
+    return dict(x=rel(gpu["x"], ref["x"]), lam=rel(gpu["lam"], ref["lam"]),
+                x_el=max_abs_rel(gpu["x"], ref["x"], floor),
+                lam_el=max_abs_rel(gpu["lam"], ref["lam"], floor), tol=tol)
+
+
+def oracle_run(inst, iters, eps=0.0, **kw):
+    return oracle.solve(inst, iters, eps_abs=eps, **kw)

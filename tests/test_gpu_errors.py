@@ -1,0 +1,71 @@
+"""Malformed instances are rejected by the device-side validation (NUM_ERR_INVALID with a
+message naming the defect), from host and from device arrays; a handle stays usable."""
+import numpy as np
+import pytest
+
+from paper_2509_10722_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def _base():
+    return W.random_instance(50, 20, 1, 5, seed=3)
+
+
+def _mutations():
+    def dup(i):
+        i["route_links"][1] = i["route_links"][0]  # route 0 has >= 2 links? force it below
+    yield "duplicate", "twice", lambda i: i["route_links"].__setitem__(
+        slice(int(i["route_ptr"][_long(i)]) + 1, int(i["route_ptr"][_long(i)]) + 2),
+        i["route_links"][int(i["route_ptr"][_long(i)])])
+    yield "link_id_high", "outside", lambda i: i["route_links"].__setitem__(3, 20)
+    yield "link_id_negative", "outside", lambda i: i["route_links"].__setitem__(5, -1)
+    yield "capacity_zero", "capacity", lambda i: i["c"].__setitem__(4, 0.0)
+    yield "capacity_nan", "capacity", lambda i: i["c"].__setitem__(4, np.nan)
+    yield "weight_negative", "weight", lambda i: i["w"].__setitem__(7, -1.0)
+    yield "weight_inf", "weight", lambda i: i["w"].__setitem__(7, np.inf)
+    yield "utype", "utility type", lambda i: i["utype"].__setitem__(2, 3)
+    yield "box_inverted", "box", lambda i: (i["lo"].__setitem__(9, 5.0), i["hi"].__setitem__(9, 1.0))
+    yield "box_nan", "box", lambda i: i["hi"].__setitem__(9, np.nan)
+    yield "log_hi_zero", "box", lambda i: (i["utype"].__setitem__(11, 0), i["hi"].__setitem__(11, 0.0),
+                                           i["lo"].__setitem__(11, 0.0))
+
+
+def _long(inst):
+    return int(np.flatnonzero(np.diff(inst["route_ptr"]) >= 2)[0])
+
+
+MUT = list(_mutations())
+
+
+@pytest.mark.parametrize("name,msg,mut", MUT, ids=[m[0] for m in MUT])
+@pytest.mark.parametrize("device", [False, True])
+def test_invalid_instance(name, msg, mut, device):
+    from paper_2509_10722_b300 import capi
+    inst = _base()
+    mut(inst)
+    with pytest.raises(capi.NumError) as ei:
+        capi.Problem(inst, device=device)
+    assert ei.value.code == capi.NUM_ERR_INVALID
+    assert msg in str(ei.value)
+
+
+def test_valid_after_rejection():
+    from paper_2509_10722_b300 import capi
+    bad = _base()
+    bad["c"][0] = -1.0
+    with pytest.raises(capi.NumError):
+        capi.Problem(bad)
+    with capi.Problem(_base()) as p:
+        status, done = p.solve(20, 0.0)
+        assert (status, done) == (1, 20)
+
+
+def test_bad_solve_arguments():
+    from paper_2509_10722_b300 import capi
+    with capi.Problem(_base()) as p:
+        with pytest.raises(capi.NumError):
+            p.solve(-1)
+        with pytest.raises(capi.NumError):
+            p.set_rho_schedule([0, 2, 0])
+        assert p.solve(0, 0.0) == (1, 0)

@@ -1,0 +1,189 @@
+"""CUDA path against the FP64 oracle, element by element, through the C ABI.
+
+Tolerances: the FP64 paths (fused and plain) within 1e-10 relative (2-norm) of the oracle
+after the same iteration count with their own rho decisions; the FP32 fused path within
+1e-4 relative after the same iteration count on the oracle's rho schedule.  Integer work
+(the device-built CSR) is compared bit for bit.
+"""
+import numpy as np
+import pytest
+
+from gpu_util import compare, oracle_run, rel, run_gpu
+from paper_2509_10722_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-10
+FP32_TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def c1():
+    return W.workload("c1")
+
+
+@pytest.fixture(scope="module")
+def c1_oracle(c1):
+    return {k: oracle_run(c1, k) for k in (1, 7, 50, 51, 300, 2000)}
+
+
+def _check_hist(gh, oh, rtol):
+    assert gh.shape == oh.shape
+    scale = np.max(np.abs(oh[:, :2]))
+    assert np.allclose(gh[:, :2], oh[:, :2], rtol=rtol, atol=rtol * 1e-3 * scale)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "plain"])
+@pytest.mark.parametrize("iters", [1, 7, 50, 51, 300, 2000])
+def test_c1_fp64_paths_match_oracle(c1, c1_oracle, precision, iters):
+    ref = c1_oracle[iters]
+    g = run_gpu(c1, iters, precision)
+    assert g["iters"] == iters
+    e = compare(g, ref, FP64_TOL)
+    assert e["x"] <= FP64_TOL and e["lam"] <= FP64_TOL, e
+    assert e["x_el"] <= 1e-9 and e["lam_el"] <= 1e-9, e
+    _check_hist(g["hist"], ref["hist"], 1e-9)
+    assert np.array_equal(g["hist"][:, 2], ref["hist"][:, 2])  # identical rho decisions
+
+
+@pytest.mark.parametrize("iters", [50, 300, 2000])
+def test_c1_fp32_matches_oracle_on_its_rho_schedule(c1, c1_oracle, iters):
+    ref = c1_oracle[iters]
+    g = run_gpu(c1, iters, "fp32", schedule=ref["decisions"])
+    e = compare(g, ref, FP32_TOL)
+    assert e["x"] <= FP32_TOL and e["lam"] <= FP32_TOL, e
+    assert np.array_equal(g["hist"][:, 2], ref["hist"][:, 2])
+
+
+def test_c1_fp32_own_decisions_converge_to_the_oracle_solution(c1):
+    ref = oracle_run(c1, 100_000, eps=1e-7)
+    g = run_gpu(c1, 100_000, "fp32", eps=1e-4)
+    assert g["status"] == 0
+    from oracle import kkt
+    u_ref = kkt.utility(c1, ref["x"])
+    assert abs(g["info"]["objective"] - u_ref) <= 1e-5 * abs(u_ref) * 10
+    # tolerance 1e-4 leaves x within the accuracy the residuals allow
+    assert rel(g["x"], ref["x"]) < 5e-3
+
+
+@pytest.mark.parametrize("precision", ["fp64", "plain", "fp32"])
+def test_stopping_iteration_matches_oracle(c1, precision):
+    eps = 1e-6 if precision != "fp32" else 1e-4
+    ref = oracle_run(c1, 100_000, eps=eps)
+    sched = ref["decisions"] if precision == "fp32" else None
+    g = run_gpu(c1, 100_000, precision, eps=eps, schedule=sched)
+    assert g["status"] == 0 and ref["converged"]
+    if precision == "fp32":
+        assert abs(g["iters"] - ref["iters"]) <= 2
+    else:
+        assert g["iters"] == ref["iters"]
+    assert g["info"]["primal"] < g["info"]["eps_tol"] and g["info"]["dual"] < g["info"]["eps_tol"]
+
+
+# ---- ragged shapes, tile splitting, skew, degenerate rows ------------------------------------
+
+def _cases():
+    yield "one_stream_one_link", W.random_instance(1, 1, 1, 1, seed=1), {}
+    yield "tiny", W.random_instance(37, 11, 1, 6, seed=2), {}
+    yield "links_without_streams", W.random_instance(40, 400, 1, 3, seed=3), {}
+    yield "split_rows_small_tiles", W.random_instance(5000, 300, 1, 8, seed=4), dict(tile_items=256)
+    yield "zipf_hot_rows_many_tiles", W.random_instance(
+        20000, 500, 2, 12, seed=5, link_dist="zipf", frac_log=1.0, c_scale=0.1,
+        w_dist="lognormal", box=(0.0, 10.0)), dict(tile_items=256)
+    yield "zipf_default_tiles", W.random_instance(
+        60000, 2000, 2, 12, seed=6, link_dist="zipf", frac_log=1.0, c_scale=0.1,
+        w_dist="lognormal", box=(0.0, 10.0)), {}
+    yield "long_routes", W.random_instance(300, 200, 60, 150, seed=7), dict(tile_items=512)
+    yield "ragged_tail", W.random_instance(4097, 1025, 1, 10, seed=8), dict(tile_items=1024)
+    yield "all_linear", W.random_instance(2000, 300, 1, 6, seed=9, frac_log=0.0), {}
+
+    def box(rng, n):
+        lo = rng.uniform(0.0, 0.5, n)
+        return lo, lo + rng.uniform(0.1, 3.0, n)
+    yield "per_stream_box", W.random_instance(3000, 200, 1, 6, seed=10, box=box), {}
+
+
+CASES = list(_cases())
+
+
+@pytest.mark.parametrize("name,inst,params", CASES, ids=[c[0] for c in CASES])
+@pytest.mark.parametrize("precision", ["fp64", "plain"])
+def test_shapes_fp64_match_oracle(name, inst, params, precision):
+    iters = 200
+    ref = oracle_run(inst, iters)
+    g = run_gpu(inst, iters, precision, **params)
+    e = compare(g, ref, FP64_TOL)
+    assert e["x"] <= FP64_TOL and e["lam"] <= FP64_TOL, e
+    assert e["x_el"] <= 1e-9 and e["lam_el"] <= 1e-9, e
+
+
+@pytest.mark.parametrize("name,inst,params", CASES, ids=[c[0] for c in CASES])
+def test_shapes_fp32_match_oracle(name, inst, params):
+    iters = 200
+    ref = oracle_run(inst, iters)
+    g = run_gpu(inst, iters, "fp32", schedule=ref["decisions"], **params)
+    e = compare(g, ref, FP32_TOL)
+    assert e["x"] <= FP32_TOL and e["lam"] <= FP32_TOL, e
+
+
+@pytest.mark.parametrize("name,inst,params", CASES[:6], ids=[c[0] for c in CASES[:6]])
+def test_operator_is_bit_exact(name, inst, params):
+    from paper_2509_10722_b300 import capi
+    with capi.Problem(inst, **params) as p:
+        rp, ci = p.operator()
+    rp_ref, ci_ref = W.csr_of(inst)
+    assert np.array_equal(rp, rp_ref) and np.array_equal(ci, ci_ref)
+
+
+# ---- determinism, graph vs launches, device inputs ----------------------------------------------
+
+def test_runs_are_bit_identical(c1):
+    a = run_gpu(c1, 500, "fp32")
+    b = run_gpu(c1, 500, "fp32")
+    c = run_gpu(c1, 500, "fp32", use_graph=0)
+    d = run_gpu(c1, 500, "fp32", check_every=7)
+    for other in (b, c, d):
+        assert np.array_equal(a["x"], other["x"]) and np.array_equal(a["lam"], other["lam"])
+
+
+def test_device_inputs_equal_host_inputs(c1):
+    a = run_gpu(c1, 300, "fp32")
+    b = run_gpu(c1, 300, "fp32", device=True)
+    assert np.array_equal(a["x"], b["x"]) and np.array_equal(a["lam"], b["lam"])
+
+
+def test_torch_allocator(c1):
+    a = run_gpu(c1, 100, "fp64")
+    b = run_gpu(c1, 100, "fp64", use_torch_allocator=True)
+    assert np.array_equal(a["x"], b["x"])
+
+
+def test_continue_and_reset(c1):
+    from paper_2509_10722_b300 import capi
+    whole = run_gpu(c1, 300, "fp64")
+    with capi.Problem(c1, precision=1) as p:
+        assert p.solve(120, 0.0) == (1, 120)
+        assert p.solve(180, 0.0) == (1, 180)
+        x, lam, info = p.get()
+        assert info["iters"] == 300
+        assert np.array_equal(x, whole["x"]) and np.array_equal(lam, whole["lam"])
+        p.reset()
+        p.solve(300, 0.0)
+        x2, lam2, _ = p.get()
+        assert np.array_equal(x2, whole["x"])
+
+
+def test_objective_matches_fp64_utility(c1):
+    from oracle import kkt
+    g = run_gpu(c1, 400, "fp64")
+    assert abs(g["info"]["objective"] - kkt.utility(c1, g["x"])) <= 1e-12 * abs(
+        kkt.utility(c1, g["x"]))
+
+
+# ---- the paper's example and closed forms through the GPU path --------------------------------
+
+def test_four_stream_example_fp32():
+    inst = W.four_stream_example()
+    g = run_gpu(inst, 10_000, "fp32", eps=1e-5)
+    assert np.allclose(g["x"], [1.0, 1 / 3, 2 / 3, 2 / 3], rtol=1e-4)
+    assert np.allclose(g["lam"], [1.0, 1.5, 1.5], rtol=1e-4)
