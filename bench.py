@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--eps", type=float, default=1e-4)
     ap.add_argument("--max-iters", type=int, default=50_000)
     ap.add_argument("--tile", type=int, default=0, help="tile_items (0 = automatic)")
+    ap.add_argument("--schedule", choices=["rows", "tiles"], default="rows",
+                    help="kernel schedule of the fused FP32 path")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -201,7 +203,8 @@ def pinned_copy(inst, torch):
 class Solver:
     """One whole solve per call, on a fixed torch stream, inputs resident on the device."""
 
-    def __init__(self, capi, torch, dev_inst, n, m, precision, eps, max_iters, stream, tile=0):
+    def __init__(self, capi, torch, dev_inst, n, m, precision, eps, max_iters, stream, tile=0,
+                 schedule=0):
         self.capi, self.torch = capi, torch
         self.d = dev_inst
         self.n, self.m = n, m
@@ -210,6 +213,7 @@ class Solver:
         self.alloc = capi.torch_allocator()
         import ctypes
         self.params = capi.num_default_params(precision=precision, profile=1, tile_items=tile,
+                                              schedule=schedule,
                                               allocator=ctypes.pointer(self.alloc))
         self.x = torch.empty(n, dtype=torch.float64, device="cuda")
         self.p = torch.empty(m, dtype=torch.float64, device="cuda")
@@ -310,8 +314,9 @@ def run_ours(args, dist):
     n, m, nnz = inst["n"], inst["m"], int(inst["route_ptr"][-1])
     dev = to_device(inst, torch)
     stream = torch.cuda.Stream()
+    sched = {"rows": capi.NUM_SCHEDULE_ROWS, "tiles": capi.NUM_SCHEDULE_TILES}[args.schedule]
     fp32 = Solver(capi, torch, dev, n, m, PRECISION["fp32"], args.eps, args.max_iters, stream,
-                  args.tile)
+                  args.tile, sched)
     for _ in range(args.warmup):
         fp32.step()
     fp32.reset_kernel_times()
@@ -372,7 +377,8 @@ def run_ours(args, dist):
                        "l2": "no flush: every step moves ~0.8 GB per iteration, far more than "
                              "the 126 MB L2",
                        "parallelism": "single GPU" if dist.world == 1 else f"{dist.world} replicas",
-                       "precision": "FP32 iterates, FP64 residuals / stopping test / rho"},
+                       "precision": "FP32 iterates, FP64 residuals / stopping test / rho",
+                       "schedule": args.schedule},
             "time_to_tol_s": ms_max / args.steps / 1e3,
             "iters_to_tol": it_per_solve[-1], "converged": all(s == 0 for s in statuses),
             "final_residuals": {"primal": info["primal"], "dual": info["dual"],
@@ -406,7 +412,7 @@ def run_ours(args, dist):
 
     if not args.no_e2e:
         host = pinned_copy(inst, torch)
-        e2e_params = capi.num_default_params(precision=0)
+        e2e_params = capi.num_default_params(precision=0, schedule=sched)
         xh = np.empty(n)
         ph = np.empty(m)
         t_e2e, it_e2e = 0.0, 0

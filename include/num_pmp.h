@@ -62,6 +62,10 @@ extern "C" {
 #define NUM_PLAIN_FP64 2 /* unfused baseline: one kernel per step (SpMV, elementwise prox,
                             SpMV-transpose, reductions), all FP64 */
 
+/* ---- kernel schedule of the fused paths ---------------------------------------------------- */
+#define NUM_SCHEDULE_ROWS 1  /* row-parallel kernels (the default) */
+#define NUM_SCHEDULE_TILES 2 /* merge-path tiles */
+
 /* Optional device allocator.  alloc returns device memory of `bytes` bytes usable on
  * `stream` (NULL on failure, which num_create reports as NUM_ERR_OOM); release frees it. */
 typedef struct {
@@ -80,11 +84,14 @@ typedef struct {
  *   precision   NUM_FUSED_FP32 (default), NUM_FUSED_FP64 or NUM_PLAIN_FP64
  *   check_every iterations per CUDA-graph replay between two host reads of the stop flag
  *               (default 50); iterations after the stop inside a replay do nothing
- *   tile_items  items (nonzeros + rows) per tile of the fused kernels; 0 = automatic,
+ *   tile_items  items (nonzeros + rows) per tile of the merge-path kernels; 0 = automatic,
  *               otherwise a power of two in [256, 8192] (small values exercise row splitting)
  *   history     length of the on-device ring buffer of (||r||, ||s||, rho) per iteration
  *               (default 4096; 0 = none)
  *   use_graph   1 (default): replay captured CUDA graphs; 0: plain launches
+ *   schedule    0 (default) or NUM_SCHEDULE_ROWS: row-parallel fused kernels (a warp per
+ *               32 streams, a warp per link, links above 2048 streams cut into chunks);
+ *               NUM_SCHEDULE_TILES: merge-path tiles of tile_items items (any skew)
  *   profile     1: record a CUDA event on the handle's stream after every kernel of every
  *               iteration (inside the replayed graphs) and accumulate per-kernel device
  *               times, read with num_get_kernel_times; 0 (default): no events
@@ -101,6 +108,7 @@ typedef struct {
     int32_t tile_items;
     int32_t history;
     int32_t use_graph;
+    int32_t schedule;
     int32_t profile;
     const num_allocator* allocator;
 } num_params;

@@ -61,6 +61,10 @@ struct num_problem {
     int *col_ptr = nullptr, *row_idx = nullptr, *row_ptr = nullptr, *col_idx = nullptr;
     int2 *tiles_s = nullptr, *tiles_l = nullptr;
     int ntiles_s = 0, ntiles_l = 0, tile_s = 0, tile_l = 0, grid_s = 0, grid_l = 0;
+    int sched_kind = NUM_SCHEDULE_ROWS;  // fused paths: row kernels or merge-path tiles
+    int4* chunks = nullptr;              // row kernels: chunks of the long links
+    int nchunks = 0;
+    int narrive_l = 0;                   // entries of arrive_l
     void *wt = nullptr, *lo = nullptr, *hi = nullptr, *c = nullptr;
     void *x = nullptr, *Z = nullptr, *pby = nullptr, *zs = nullptr, *Rx = nullptr, *ps = nullptr;
     void *carry_s = nullptr, *carry_l = nullptr;
@@ -184,6 +188,8 @@ View<T> make_view(const num_problem* h) {
     v.part_l = h->part_l;
     v.grid_s = h->grid_s;
     v.grid_l = h->grid_l;
+    v.chunks = h->chunks;
+    v.nchunks = h->nchunks;
     v.ctl = h->ctl;
     v.hist = h->hist;
     v.sched = h->sched;
@@ -203,16 +209,19 @@ View<T> make_view(const num_problem* h) {
 cudaError_t run_iterations(num_problem* h, int count) {
     const bool prof = h->prm.profile != 0;
     if (prof) {
-        cudaError_t e = cudaEventRecord(h->evs[0], h->stream);
+        cudaError_t e = cudaEventRecordWithFlags(h->evs[0], h->stream, cudaEventRecordExternal);
         if (e != cudaSuccess) return e;
     }
     for (int i = 0; i < count; ++i) {
         cudaEvent_t* ev = prof ? h->evs.data() + 1 + (size_t)i * h->kpi : nullptr;
         cudaError_t e;
+        const bool rows = h->sched_kind == NUM_SCHEDULE_ROWS;
         if (h->prec == NUM_FUSED_FP32)
-            e = pmp::fused_iteration<float>(make_view<float>(h), h->stream, ev);
+            e = rows ? pmp::rows_iteration<float>(make_view<float>(h), h->stream, ev)
+                     : pmp::fused_iteration<float>(make_view<float>(h), h->stream, ev);
         else if (h->prec == NUM_FUSED_FP64)
-            e = pmp::fused_iteration<double>(make_view<double>(h), h->stream, ev);
+            e = rows ? pmp::rows_iteration<double>(make_view<double>(h), h->stream, ev)
+                     : pmp::fused_iteration<double>(make_view<double>(h), h->stream, ev);
         else
             e = pmp::plain_iteration(make_view<double>(h), h->plain_nb, h->stream, ev);
         if (e != cudaSuccess) return e;
@@ -252,7 +261,7 @@ cudaError_t zero_state(num_problem* h) {
     z(h->pbar, ts * h->m);
     z(h->y, ts * h->m);
     z(h->arrive_s, sizeof(int) * (size_t)h->ntiles_s);
-    z(h->arrive_l, sizeof(int) * (size_t)h->ntiles_l);
+    z(h->arrive_l, sizeof(int) * (size_t)h->narrive_l);
     if (h->hist && h->prm.history > 0) z(h->hist, sizeof(double) * 3 * (size_t)h->prm.history);
     if (e != cudaSuccess) return e;
     e = pmp::ctl_reset(h->ctl, h->prm.rho0, h->prm.alpha, h->prm.mu, h->prm.gamma,
@@ -279,6 +288,8 @@ int check_params(const num_params& p) {
         return fail(NUM_ERR_INVALID, "tile_items must be 0 or a power of two in [256, 8192]");
     if (p.history < 0) return fail(NUM_ERR_INVALID, "history must be >= 0");
     if (p.profile != 0 && p.profile != 1) return fail(NUM_ERR_INVALID, "profile must be 0 or 1");
+    if (p.schedule < 0 || p.schedule > NUM_SCHEDULE_TILES)
+        return fail(NUM_ERR_INVALID, "unknown schedule");
     if (p.allocator && (!p.allocator->alloc || !p.allocator->release))
         return fail(NUM_ERR_INVALID, "allocator needs alloc and release");
     return NUM_OK;
@@ -359,6 +370,9 @@ int create_impl(num_problem** out, int64_t n, int64_t m, const int64_t* route_pt
     h->ntiles_s = (int)((h->Js + (int64_t)h->tile_s - 1) / h->tile_s);
     h->ntiles_l = (int)((h->Jl + (int64_t)h->tile_l - 1) / h->tile_l);
     h->plain_nb = pmp::plain_partial_blocks((int)n, (int)m);
+    h->sched_kind = prm.schedule == NUM_SCHEDULE_TILES ? NUM_SCHEDULE_TILES : NUM_SCHEDULE_ROWS;
+    const bool tiles = !plain && h->sched_kind == NUM_SCHEDULE_TILES;
+    const bool rowk = !plain && h->sched_kind == NUM_SCHEDULE_ROWS;
     h->exp_blocks = pmp::export_partial_blocks((int)n);
 
     // ---- device memory: the handle's arrays, then the transient build buffers ----
@@ -393,12 +407,15 @@ int create_impl(num_problem** out, int64_t n, int64_t m, const int64_t* route_pt
         h->RxN = A(ts * M);
     } else {
         h->pby = A(2 * ts * M);
+    }
+    if (tiles) {
         h->tiles_s = (int2*)A(sizeof(int2) * (size_t)h->ntiles_s);
         h->tiles_l = (int2*)A(sizeof(int2) * (size_t)h->ntiles_l);
         h->carry_s = A(2 * ts * 2 * (size_t)h->ntiles_s);
         h->carry_l = A(ts * 2 * (size_t)h->ntiles_l);
         h->arrive_s = (int*)A(sizeof(int) * (size_t)h->ntiles_s);
         h->arrive_l = (int*)A(sizeof(int) * (size_t)h->ntiles_l);
+        h->narrive_l = h->ntiles_l;
     }
     const size_t npart = (size_t)(kMaxGrid > h->plain_nb ? kMaxGrid : h->plain_nb);
     h->part_s = (double*)A(sizeof(double) * npart);
@@ -433,6 +450,9 @@ int create_impl(num_problem** out, int64_t n, int64_t m, const int64_t* route_pt
     s.scan_tmp_len = pmp::scan_tmp_len(s.hist_len);
     s.hist = (int*)A(4 * s.hist_len);
     s.scan_tmp = (int*)A(4 * s.scan_tmp_len);
+    int* d_ccount = rowk ? (int*)A(4 * (M + 1)) : nullptr;
+    int* d_coff = rowk ? (int*)A(4 * (M + 1)) : nullptr;
+    int* d_ctmp = rowk ? (int*)A(4 * pmp::scan_tmp_len(M + 1)) : nullptr;
     if (!ok) {
         destroy_handle(h);
         return fail(NUM_ERR_OOM, "device allocation failed");
@@ -515,7 +535,7 @@ int create_impl(num_problem** out, int64_t n, int64_t m, const int64_t* route_pt
         CK(pmp::convert_params<double>((int)n, (int)m, c, utype, w, lo, hi, (double*)h->c,
                                        (double*)h->wt, (double*)h->lo, (double*)h->hi, st),
            "converting parameters");
-    if (!plain) {
+    if (tiles) {
         CK(pmp::build_tiles(h->col_ptr, (int)n, h->Js, h->tile_s, h->ntiles_s, h->tiles_s, st),
            "stream tiles");
         CK(pmp::build_tiles(h->row_ptr, (int)m, h->Jl, h->tile_l, h->ntiles_l, h->tiles_l, st),
@@ -524,12 +544,30 @@ int create_impl(num_problem** out, int64_t n, int64_t m, const int64_t* route_pt
                             &h->grid_s, &h->grid_l),
            "sizing the fused grids");
     }
+    if (rowk) {
+        CK(pmp::count_chunks(h->row_ptr, (int)m, d_ccount, d_coff, d_ctmp, &h->nchunks, st),
+           "counting long-link chunks");
+        const size_t nc = (size_t)(h->nchunks > 0 ? h->nchunks : 1);
+        h->chunks = (int4*)dev_alloc(h, sizeof(int4) * nc);
+        h->carry_l = dev_alloc(h, ts * nc);
+        h->arrive_l = (int*)dev_alloc(h, sizeof(int) * nc);
+        h->narrive_l = (int)nc;
+        if (!h->chunks || !h->carry_l || !h->arrive_l) {
+            destroy_handle(h);
+            return fail(NUM_ERR_OOM, "device allocation failed");
+        }
+        if (h->nchunks > 0)
+            CK(pmp::fill_chunks(h->row_ptr, (int)m, d_coff, h->chunks, st), "long-link chunks");
+        CK(pmp::rows_grids(fp32 ? 0 : 1, (int)n, (int)m, h->nchunks, &h->grid_s, &h->grid_l),
+           "sizing the row-kernel grids");
+    }
     CK(zero_state(h), "zeroing the state");
     CK(cudaStreamSynchronize(st), "setup");
     // release the transient buffers
     for (void* q : {(void*)d_rp, (void*)d_rl, (void*)d_c, (void*)d_w, (void*)d_lo, (void*)d_hi,
                     (void*)d_ut, (void*)d_err, (void*)d_box, (void*)s.keys_a, (void*)s.vals_a,
-                    (void*)s.keys_b, (void*)s.vals_b, (void*)s.hist, (void*)s.scan_tmp})
+                    (void*)s.keys_b, (void*)s.vals_b, (void*)s.hist, (void*)s.scan_tmp,
+                    (void*)d_ccount, (void*)d_coff, (void*)d_ctmp})
         dev_free(h, q);
 #undef CK
     *out = h;
@@ -558,6 +596,7 @@ void num_default_params(num_params* p) {
     p->tile_items = 0;
     p->history = 4096;
     p->use_graph = 1;
+    p->schedule = 0;
     p->profile = 0;
     p->allocator = nullptr;
 }

@@ -262,6 +262,31 @@ __global__ void k_tiles(const int* __restrict__ ptr, int nrows, int J, int tile,
     }
 }
 
+__global__ void k_chunk_counts(const int* __restrict__ row_ptr, int m, int* counts) {
+    for (int l = blockIdx.x * blockDim.x + threadIdx.x; l <= m; l += gridDim.x * blockDim.x) {
+        int c = 0;
+        if (l < m) {
+            const int deg = row_ptr[l + 1] - row_ptr[l];
+            c = deg > kLongRow ? (deg + kChunk - 1) / kChunk : 0;
+        }
+        counts[l] = c;
+    }
+}
+
+__global__ void k_chunk_fill(const int* __restrict__ row_ptr, int m, const int* __restrict__ offs,
+                             int4* chunks) {
+    for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < m; l += gridDim.x * blockDim.x) {
+        const int p0 = row_ptr[l], p1 = row_ptr[l + 1];
+        if (p1 - p0 <= kLongRow) continue;
+        const int first = offs[l];
+        for (int c = 0; first + c < offs[l + 1]; ++c) {
+            const int e0 = p0 + c * kChunk;
+            const int e1 = e0 + kChunk < p1 ? e0 + kChunk : p1;
+            chunks[first + c] = make_int4(l, e0, e1, first);
+        }
+    }
+}
+
 template <typename T>
 __global__ void k_convert(int n, int m, const double* __restrict__ c,
                           const uint8_t* __restrict__ utype, const double* __restrict__ w,
@@ -432,6 +457,25 @@ cudaError_t build_tiles(const int* ptr, int nrows, int J, int tile, int ntiles, 
                         cudaStream_t st) {
     k_tiles<<<blocks_for(ntiles, kThreads, 65535), kThreads, 0, st>>>(ptr, nrows, J, tile, ntiles,
                                                                       tiles);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t count_chunks(const int* row_ptr, int m, int* counts, int* offs, int* tmp,
+                         int* nchunks, cudaStream_t st) {
+    k_chunk_counts<<<blocks_for((long long)m + 1, kThreads, 65535), kThreads, 0, st>>>(row_ptr, m,
+                                                                                       counts);
+    note_launches(1);
+    cudaError_t e = scan_exclusive(counts, offs, (size_t)m + 1, tmp, st);
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpyAsync(nchunks, offs + m, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return e;
+    return cudaStreamSynchronize(st);
+}
+
+cudaError_t fill_chunks(const int* row_ptr, int m, const int* offs, int4* chunks,
+                        cudaStream_t st) {
+    k_chunk_fill<<<blocks_for(m, kThreads, 65535), kThreads, 0, st>>>(row_ptr, m, offs, chunks);
     note_launches(1);
     return cudaGetLastError();
 }

@@ -128,7 +128,7 @@ cudaError_t plain_iteration(const View<double>& v, int nb, cudaStream_t st, cuda
     double* partL = v.part_l + nb;
     int q = 0;
     auto mark = [&]() {
-        if (evs) cudaEventRecord(evs[q], st);
+        if (evs) cudaEventRecordWithFlags(evs[q], st, cudaEventRecordExternal);
         ++q;
     };
     k_plain_spmvT<<<blocks(v.n, 1 << 16), kTh, 0, st>>>(v);

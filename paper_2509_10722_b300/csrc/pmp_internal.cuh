@@ -38,6 +38,12 @@ struct Ctl {
 
 enum Stop { RUNNING = 0, CONVERGED = 1, LIMIT = 2, NONFINITE = 3 };
 
+// Row kernels (rows.cu): a link with more than kLongRow streams is summed in chunks of
+// kChunk entries by separate warps; persistent grids are capped at kMaxRowsGrid blocks.
+constexpr int kLongRow = 2048;
+constexpr int kChunk = 2048;
+constexpr int kMaxRowsGrid = 8192;
+
 template <typename T> struct Pair;
 template <> struct Pair<float> { using type = float2; };
 template <> struct Pair<double> { using type = double2; };
@@ -74,6 +80,8 @@ struct View {
     double* part_s;             // per-block residual partials of the stream kernel [grid_s]
     double* part_l;             // ... of the link kernel [2 * grid_l]
     int grid_s, grid_l;
+    const int4* chunks;         // row kernels: (link, first entry, end entry, first chunk)
+    int nchunks;
     Ctl* ctl;
     double* hist;
     const signed char* sched;
@@ -98,12 +106,25 @@ size_t fused_smem_link(int precision, int tile);
 cudaError_t fused_grids(int precision, int tile_s, int tile_l, int ntiles_s, int ntiles_l,
                         int* grid_s, int* grid_l);
 // One iteration on stream st.  If evs is not NULL, evs[q] is recorded on st right after
-// the q-th kernel of the iteration (for per-kernel timing).
+// the q-th kernel of the iteration (for per-kernel timing), as an external event so that
+// it is a real event-record node when the launch is captured into a graph.
 template <typename T>
 cudaError_t fused_iteration(const View<T>& v, cudaStream_t st, cudaEvent_t* evs);
 cudaError_t plain_iteration(const View<double>& v, int plain_blocks, cudaStream_t st,
                             cudaEvent_t* evs);
 constexpr int kFusedKernelsPerIter = 2;
+
+// ---- row kernels (rows.cu) ------------------------------------------------------------------
+cudaError_t rows_grids(int precision, int n, int m, int nchunks, int* grid_s, int* grid_l);
+template <typename T>
+cudaError_t rows_iteration(const View<T>& v, cudaStream_t st, cudaEvent_t* evs);
+// Chunk table of the links with more than kLongRow streams: counts[m+1] and offs[m+1] are
+// caller scratch, tmp is scan scratch of scan_tmp_len(m + 1) ints; *nchunks (host) is the
+// number of chunks; chunks (may be NULL on the counting call) receives them.
+cudaError_t count_chunks(const int* row_ptr, int m, int* counts, int* offs, int* tmp,
+                         int* nchunks, cudaStream_t st);
+cudaError_t fill_chunks(const int* row_ptr, int m, const int* offs, int4* chunks,
+                        cudaStream_t st);
 constexpr int kPlainKernelsPerIter = 8;
 
 // Process-wide count of kernel launches made by this library (graph replays count every

@@ -8,12 +8,15 @@ import oracle
 PREC = {"fp32": 0, "fp64": 1, "plain": 2}
 
 
-def run_gpu(inst, iters, precision="fp64", eps=0.0, schedule=None, device=False, **params):
+def run_gpu(inst, iters, precision="fp64", eps=0.0, schedule_decisions=None, device=False,
+            **params):
+    """Solve through the C ABI; schedule_decisions forces the rho decisions, other keyword
+    arguments are num_params fields (schedule = kernel schedule)."""
     from paper_2509_10722_b300 import capi
     params.setdefault("history", max(int(iters), 1))
     with capi.Problem(inst, device=device, precision=PREC[precision], **params) as p:
-        if schedule is not None:
-            p.set_rho_schedule(schedule)
+        if schedule_decisions is not None:
+            p.set_rho_schedule(schedule_decisions)
         status, done = p.solve(iters, eps)
         x, lam, info = p.get()
         hist = p.history()

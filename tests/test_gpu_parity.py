@@ -33,11 +33,11 @@ def _check_hist(gh, oh, rtol):
     assert np.allclose(gh[:, :2], oh[:, :2], rtol=rtol, atol=rtol * 1e-3 * scale)
 
 
-@pytest.mark.parametrize("precision", ["fp64", "plain"])
+@pytest.mark.parametrize("precision,schedule", [("fp64", 1), ("fp64", 2), ("plain", 0)])
 @pytest.mark.parametrize("iters", [1, 7, 50, 51, 300, 2000])
-def test_c1_fp64_paths_match_oracle(c1, c1_oracle, precision, iters):
+def test_c1_fp64_paths_match_oracle(c1, c1_oracle, precision, schedule, iters):
     ref = c1_oracle[iters]
-    g = run_gpu(c1, iters, precision)
+    g = run_gpu(c1, iters, precision, schedule=schedule)
     assert g["iters"] == iters
     e = compare(g, ref, FP64_TOL)
     assert e["x"] <= FP64_TOL and e["lam"] <= FP64_TOL, e
@@ -49,21 +49,24 @@ def test_c1_fp64_paths_match_oracle(c1, c1_oracle, precision, iters):
 @pytest.mark.parametrize("iters", [50, 300, 2000])
 def test_c1_fp32_matches_oracle_on_its_rho_schedule(c1, c1_oracle, iters):
     ref = c1_oracle[iters]
-    g = run_gpu(c1, iters, "fp32", schedule=ref["decisions"])
+    g = run_gpu(c1, iters, "fp32", schedule_decisions=ref["decisions"])
     e = compare(g, ref, FP32_TOL)
     assert e["x"] <= FP32_TOL and e["lam"] <= FP32_TOL, e
     assert np.array_equal(g["hist"][:, 2], ref["hist"][:, 2])
 
 
-def test_c1_fp32_own_decisions_converge_to_the_oracle_solution(c1):
-    ref = oracle_run(c1, 100_000, eps=1e-7)
-    g = run_gpu(c1, 100_000, "fp32", eps=1e-4)
-    assert g["status"] == 0
+@pytest.mark.parametrize("eps", [1e-4, 1e-5])
+def test_c1_fp32_own_decisions_objective_matches_oracle(c1, eps):
+    """FP32 with its own rho decisions, stopped by the same test as the oracle: the
+    objective agrees to 1e-5 relative (at eps = 1e-4 the stopped iterate itself is ~1e-3
+    away from the optimum, for the oracle just the same)."""
     from oracle import kkt
+    ref = oracle_run(c1, 100_000, eps=eps)
+    g = run_gpu(c1, 100_000, "fp32", eps=eps)
+    assert g["status"] == 0 and ref["converged"]
     u_ref = kkt.utility(c1, ref["x"])
-    assert abs(g["info"]["objective"] - u_ref) <= 1e-5 * abs(u_ref) * 10
-    # tolerance 1e-4 leaves x within the accuracy the residuals allow
-    assert rel(g["x"], ref["x"]) < 5e-3
+    assert abs(g["info"]["objective"] - u_ref) <= 1e-5 * abs(u_ref)
+    assert abs(g["iters"] - ref["iters"]) <= 5
 
 
 @pytest.mark.parametrize("precision", ["fp64", "plain", "fp32"])
@@ -71,7 +74,7 @@ def test_stopping_iteration_matches_oracle(c1, precision):
     eps = 1e-6 if precision != "fp32" else 1e-4
     ref = oracle_run(c1, 100_000, eps=eps)
     sched = ref["decisions"] if precision == "fp32" else None
-    g = run_gpu(c1, 100_000, precision, eps=eps, schedule=sched)
+    g = run_gpu(c1, 100_000, precision, eps=eps, schedule_decisions=sched)
     assert g["status"] == 0 and ref["converged"]
     if precision == "fp32":
         assert abs(g["iters"] - ref["iters"]) <= 2
@@ -106,22 +109,28 @@ def _cases():
 CASES = list(_cases())
 
 
+SCHED = {"rows": 1, "tiles": 2}
+
+
 @pytest.mark.parametrize("name,inst,params", CASES, ids=[c[0] for c in CASES])
-@pytest.mark.parametrize("precision", ["fp64", "plain"])
-def test_shapes_fp64_match_oracle(name, inst, params, precision):
+@pytest.mark.parametrize("precision,schedule", [("fp64", "rows"), ("fp64", "tiles"),
+                                                ("plain", "rows")])
+def test_shapes_fp64_match_oracle(name, inst, params, precision, schedule):
     iters = 200
     ref = oracle_run(inst, iters)
-    g = run_gpu(inst, iters, precision, **params)
+    g = run_gpu(inst, iters, precision, schedule=SCHED[schedule], **params)
     e = compare(g, ref, FP64_TOL)
     assert e["x"] <= FP64_TOL and e["lam"] <= FP64_TOL, e
     assert e["x_el"] <= 1e-9 and e["lam_el"] <= 1e-9, e
 
 
 @pytest.mark.parametrize("name,inst,params", CASES, ids=[c[0] for c in CASES])
-def test_shapes_fp32_match_oracle(name, inst, params):
+@pytest.mark.parametrize("schedule", ["rows", "tiles"])
+def test_shapes_fp32_match_oracle(name, inst, params, schedule):
     iters = 200
     ref = oracle_run(inst, iters)
-    g = run_gpu(inst, iters, "fp32", schedule=ref["decisions"], **params)
+    g = run_gpu(inst, iters, "fp32", schedule_decisions=ref["decisions"],
+                schedule=SCHED[schedule], **params)
     e = compare(g, ref, FP32_TOL)
     assert e["x"] <= FP32_TOL and e["lam"] <= FP32_TOL, e
 
@@ -137,13 +146,21 @@ def test_operator_is_bit_exact(name, inst, params):
 
 # ---- determinism, graph vs launches, device inputs ----------------------------------------------
 
-def test_runs_are_bit_identical(c1):
-    a = run_gpu(c1, 500, "fp32")
-    b = run_gpu(c1, 500, "fp32")
-    c = run_gpu(c1, 500, "fp32", use_graph=0)
-    d = run_gpu(c1, 500, "fp32", check_every=7)
+@pytest.mark.parametrize("schedule", [1, 2])
+def test_runs_are_bit_identical(c1, schedule):
+    a = run_gpu(c1, 500, "fp32", schedule=schedule)
+    b = run_gpu(c1, 500, "fp32", schedule=schedule)
+    c = run_gpu(c1, 500, "fp32", use_graph=0, schedule=schedule)
+    d = run_gpu(c1, 500, "fp32", check_every=7, schedule=schedule)
     for other in (b, c, d):
         assert np.array_equal(a["x"], other["x"]) and np.array_equal(a["lam"], other["lam"])
+
+
+def test_skewed_runs_are_bit_identical():
+    inst = CASES[5][1]  # Zipf links, several split into chunks
+    a = run_gpu(inst, 100, "fp32")
+    b = run_gpu(inst, 100, "fp32")
+    assert np.array_equal(a["x"], b["x"]) and np.array_equal(a["lam"], b["lam"])
 
 
 def test_device_inputs_equal_host_inputs(c1):
@@ -187,3 +204,19 @@ def test_four_stream_example_fp32():
     g = run_gpu(inst, 10_000, "fp32", eps=1e-5)
     assert np.allclose(g["x"], [1.0, 1 / 3, 2 / 3, 2 / 3], rtol=1e-4)
     assert np.allclose(g["lam"], [1.0, 1.5, 1.5], rtol=1e-4)
+
+
+def test_profile_times_and_launch_count(c1):
+    """Per-kernel CUDA-event times inside replayed graphs, and the launch counter."""
+    from paper_2509_10722_b300 import capi
+    with capi.Problem(c1, precision=0, profile=1, check_every=10) as p:
+        l0 = capi.num_kernel_launches()
+        status, done = p.solve(95, 0.0)
+        launched = capi.num_kernel_launches() - l0
+        ms, runs = p.kernel_times()
+    assert done == 95 and list(runs) == [95, 95] and np.all(ms > 0)
+    assert launched >= 10 * 10 * 2  # ten replays of ten iterations, two kernels each
+    with capi.Problem(c1, precision=2, profile=1, check_every=10) as p:
+        p.solve(30, 0.0)
+        ms, runs = p.kernel_times()
+    assert list(runs) == [30] * 8 and np.all(ms > 0)
