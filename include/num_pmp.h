@@ -211,6 +211,23 @@ NUM_API int num_get_kernel_times(const num_problem* h, double* ms, int64_t* laun
  * node of a replayed graph counts as one launch). */
 NUM_API int64_t num_kernel_launches(void);
 
+/* Total utility sum_j U_j(x_j) (U = w log x for utype 0, w x otherwise; Sec. II) of
+ * caller DEVICE arrays x[n], utype[n], w[n], written in FP64 to the caller's DEVICE double
+ * *objective; no handle, and NO ALLOCATION of any kind.  The paper has no counterpart.
+ * For callers that cannot allocate device memory when they need the number (allocation
+ * locked by a host framework's memory pool, a real-time loop where cudaMalloc's implicit
+ * synchronization is not allowed, a fixed memory budget): the block partials live in a
+ * static device array of the library (32 KB, held on every GPU that loads the library
+ * until the process exits), so n is limited to 33,554,432; larger n is rejected with
+ * NUM_ERR_INVALID and a message.  The first call on each device looks up that array's
+ * device address (cudaGetSymbolAddress) with the device current; make that first call
+ * before any stream capture.  Work is enqueued on cuda_stream (NULL = the legacy default
+ * stream) without synchronizing.  All calls share the array: calls that overlap on the GPU
+ * (other streams or host threads) race and give wrong sums; calls ordered on one stream
+ * are safe.  Inputs are not validated on the device. */
+NUM_API int num_objective_noalloc(int64_t n, const double* x, const uint8_t* utype,
+                                  const double* w, double* objective, void* cuda_stream);
+
 /* Free every resource of the handle.  NULL is ignored. */
 NUM_API void num_destroy(num_problem* h);
 

@@ -82,6 +82,7 @@ def _load():
         "num_iteration_bytes": (ctypes.c_int, [P, P]),
         "num_get_kernel_times": (ctypes.c_int, [P, P, P, i32, ctypes.POINTER(i32)]),
         "num_kernel_launches": (ctypes.c_int64, []),
+        "num_objective_noalloc": (ctypes.c_int, [i64, P, P, P, P, P]),
         "num_destroy": (None, [P]),
         "num_strerror": (ctypes.c_char_p, [ctypes.c_int]),
         "num_last_error": (ctypes.c_char_p, []),
@@ -97,7 +98,7 @@ _lib = _load()
 EXPORTED = ("num_default_params", "num_create", "num_create_device", "num_set_rho_schedule",
             "num_solve", "num_get", "num_get_device", "num_get_history", "num_get_operator",
             "num_reset", "num_iteration_bytes", "num_get_kernel_times", "num_kernel_launches",
-            "num_destroy", "num_strerror", "num_last_error")
+            "num_objective_noalloc", "num_destroy", "num_strerror", "num_last_error")
 
 
 def library():
@@ -257,6 +258,17 @@ def num_get_kernel_times(h, max_kernels=8):
 
 def num_kernel_launches():
     return int(_lib.num_kernel_launches())
+
+
+def num_objective_noalloc(n, x, utype, w, objective, stream=None):
+    """sum_j U_j(x_j) of CUDA tensors x (float64), utype (uint8), w (float64) into the
+    CUDA float64 tensor `objective` (first element), allocating nothing."""
+    n = int(n)
+    _check(_lib.num_objective_noalloc(n, _dptr(x, "float64", n, "x"),
+                                      _dptr(utype, "uint8", n, "utype"),
+                                      _dptr(w, "float64", n, "w"),
+                                      _dptr(objective, "float64", objective.numel(), "objective"),
+                                      ctypes.c_void_p(stream) if stream else None))
 
 
 def num_destroy(h):

@@ -42,6 +42,9 @@ std::atomic<long long> g_launches{0};
 namespace pmp {
 void note_launches(long long count) { g_launches.fetch_add(count, std::memory_order_relaxed); }
 long long launches() { return g_launches.load(std::memory_order_relaxed); }
+int report_error(int code, const std::string& msg) { return fail(code, msg); }
+int report_cuda_error(cudaError_t e, const char* what) { return cuda_fail(e, what); }
+void clear_error() { g_last_error.clear(); }
 }  // namespace pmp
 
 struct num_problem {

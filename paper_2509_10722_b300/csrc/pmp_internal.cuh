@@ -14,6 +14,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 namespace pmp {
 
 // Iteration control block, one per handle, in device memory.  Written by the finalize step
@@ -131,6 +133,11 @@ constexpr int kPlainKernelsPerIter = 8;
 // kernel node they run).
 void note_launches(long long count);
 long long launches();
+
+// Set the calling thread's num_last_error() message; returns code.
+int report_error(int code, const std::string& msg);
+int report_cuda_error(cudaError_t e, const char* what);  // NUM_ERR_CUDA
+void clear_error();
 int plain_partial_blocks(int n, int m);
 
 // ---- operator and state (operator.cu) -------------------------------------------------------
