@@ -3,21 +3,25 @@
 // bound by random gathers from L2 (one 32-byte sector per gathered value), so the design
 // goal is to keep as many gathers in flight as possible with no block-wide barriers:
 //
-//   stream kernel: one warp takes 32 consecutive streams, loads their route entries as
-//     one contiguous coalesced segment, gathers (pbar, y) for every entry into a
-//     warp-private shared buffer, then each lane sums its own route and runs the prox
-//     epilogue for its stream (routes longer than the buffer: the lane gathers directly);
-//   link kernel: one warp per link (two entries per lane in flight), the link epilogue by
-//     lane 0; links with more than kLongRow streams are cut into fixed chunks of kChunk
-//     entries, each chunk summed by one warp into its own slot, and the warp that brings
-//     the row's arrival count to the number of chunks sums the slots in chunk order and
-//     runs the epilogue (no waiting, deterministic);
+//   stream kernel: one thread per stream; the stream's state is loaded first, then its
+//     route entries four at a time (four independent gathers of (pbar, y) in flight);
+//   link kernel: a group of G lanes per link (G = 32 / rows per warp), the link's own
+//     state loaded by the group leader before the gathers, R x summed by the group in a
+//     fixed order, the link epilogue by the leader; links with more than kLongRow streams
+//     are cut into fixed chunks of kChunk entries, each chunk summed by one group into its
+//     own slot, and the group that brings the row's arrival count to the number of chunks
+//     sums the slots in chunk order and runs the epilogue (no waiting, deterministic);
 //   the last block of the link kernel finishes the iteration (FP64 residual sums, stopping
 //   test, rho), as in the tile engine.
+// Per-thread residual partial sums are compensated sums in the iteration precision; block
+// and grid sums are FP64.
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include "pmp_device.cuh"
 #include "pmp_internal.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace pmp {
 
@@ -25,135 +29,136 @@ namespace {
 
 constexpr int kTh = 256;
 constexpr int kWarps = kTh / 32;
-constexpr int kCap = 512;  // route entries of one warp tile held in shared memory
+constexpr int kGroup = 8;  // lanes per link (4 links per warp); 4 to 32 measured, 8 kept
 
+// Compensated (Neumaier) running sum in the iteration precision.
 template <typename T>
-__device__ __forceinline__ T warp_sum_t(T v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    return v;
-}
+struct Acc {
+    T s = T(0), c = T(0);
+    __device__ __forceinline__ void add(T v) {
+        const T t = s + v;
+        c += (fabs(s) >= fabs(v)) ? ((s - t) + v) : ((v - t) + s);
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
 
 // ---- stream kernel -------------------------------------------------------------------------------
 
 template <typename T>
+__device__ __forceinline__ void stream_epilogue(const View<T>& v, int j, typename Pair<T>::type sum,
+                                                T L, T xo, T Zo, T wt, T lo, T hi, T alpha,
+                                                T inv_rho, Acc<T>& acc) {
+    const T Zn = alpha * L * xo + (T(1) - alpha) * Zo - alpha * sum.x;
+    const T S = Zn - sum.y * inv_rho;
+    const T xn = stream_prox<T>(S, L, wt, inv_rho, lo, hi);
+    v.Z[j] = Zn;
+    v.x[j] = xn;
+    const T dx = xn - xo;
+    acc.add(L * dx * dx);
+}
+
+template <typename T>
 __global__ void __launch_bounds__(kTh) k_stream_rows(View<T> v) {
     using V = typename Pair<T>::type;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    V* buf = reinterpret_cast<V*>(smem_raw) + (threadIdx.x >> 5) * kCap;
     __shared__ double red[kWarps];
     const Ctl* ctl = v.ctl;
     if (ctl->stop) return;
     const T alpha = (T)ctl->alpha;
     const T inv_rho = (T)(1.0 / ctl->rho);
-    const int lane = threadIdx.x & 31;
     const int n = v.n;
     const int* __restrict__ col_ptr = v.col_ptr;
     const int* __restrict__ row_idx = v.row_idx;
     const V* __restrict__ pby = v.pby;
-    double dacc = 0.0;
-    const int wstride = gridDim.x * kWarps * 32;
-    for (int j0 = (blockIdx.x * kWarps + (threadIdx.x >> 5)) * 32; j0 < n; j0 += wstride) {
-        const int j = j0 + lane;
-        const bool valid = j < n;
-        const int jc = valid ? j : n;
-        const int p = __ldg(col_ptr + jc);
-        int pn = __shfl_down_sync(0xffffffffu, p, 1);
-        if (lane == 31 || jc == n) pn = __ldg(col_ptr + (jc < n ? jc + 1 : n));
-        // epilogue state early, so its loads overlap the gathers
-        T xo = T(0), Zo = T(0), wt = T(0), lo = v.lo_u, hi = v.hi_u;
-        if (valid) {
-            xo = v.x[j];
-            Zo = v.Z[j];
-            wt = __ldg(v.wt + j);
-            if (!v.box_uniform) {
-                lo = __ldg(v.lo + j);
-                hi = __ldg(v.hi + j);
-            }
-        }
-        const int seg0 = __shfl_sync(0xffffffffu, p, 0);
-        const int seg1 = __shfl_sync(0xffffffffu, pn, 31);
-        const int cnt = seg1 - seg0;
+    Acc<T> acc;
+    for (int j = blockIdx.x * kTh + threadIdx.x; j < n; j += gridDim.x * kTh) {
+        const int p = __ldg(col_ptr + j), pn = __ldg(col_ptr + j + 1);
+        const T xo = v.x[j], Zo = v.Z[j], wt = __ldg(v.wt + j);
+        const T lo = v.box_uniform ? v.lo_u : __ldg(v.lo + j);
+        const T hi = v.box_uniform ? v.hi_u : __ldg(v.hi + j);
         V sum = vzero(V());
-        if (cnt <= kCap) {
-            for (int e0 = 0; e0 < cnt; e0 += 128) {
-                int l[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int e = e0 + u * 32 + lane;
-                    l[u] = e < cnt ? __ldg(row_idx + seg0 + e) : -1;
-                }
-                V g[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) g[u] = l[u] >= 0 ? __ldg(pby + l[u]) : vzero(V());
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int e = e0 + u * 32 + lane;
-                    if (e < cnt) buf[e] = g[u];
-                }
-            }
-            __syncwarp();
-            if (valid)
-                for (int e = p - seg0; e < pn - seg0; ++e) sum = vadd(sum, buf[e]);
-            __syncwarp();
-        } else if (valid) {
-            for (int e = p; e < pn; ++e) sum = vadd(sum, __ldg(pby + __ldg(row_idx + e)));
+        int e = p;
+        for (; e + 4 <= pn; e += 4) {
+            const int l0 = __ldg(row_idx + e), l1 = __ldg(row_idx + e + 1);
+            const int l2 = __ldg(row_idx + e + 2), l3 = __ldg(row_idx + e + 3);
+            const V g0 = __ldg(pby + l0), g1 = __ldg(pby + l1);
+            const V g2 = __ldg(pby + l2), g3 = __ldg(pby + l3);
+            sum = vadd(sum, g0);
+            sum = vadd(sum, g1);
+            sum = vadd(sum, g2);
+            sum = vadd(sum, g3);
         }
-        if (valid) {
-            const T L = (T)(pn - p);
-            const T Zn = alpha * L * xo + (T(1) - alpha) * Zo - alpha * sum.x;
-            const T S = Zn - sum.y * inv_rho;
-            const T xn = stream_prox<T>(S, L, wt, inv_rho, lo, hi);
-            v.Z[j] = Zn;
-            v.x[j] = xn;
-            const T dx = xn - xo;
-            dacc += (double)(L * dx * dx);
-        }
+        for (; e < pn; ++e) sum = vadd(sum, __ldg(pby + __ldg(row_idx + e)));
+        stream_epilogue(v, j, sum, (T)(pn - p), xo, Zo, wt, lo, hi, alpha, inv_rho, acc);
     }
-    const double s = block_sum(dacc, red);
+    const double s = block_sum(acc.value(), red);
     if (threadIdx.x == 0) v.part_s[blockIdx.x] = s;
+}
+template <typename T>
+size_t stream_smem() {
+    return 0;
 }
 
 // ---- link kernel ---------------------------------------------------------------------------------
 
+template <typename T>
+struct LinkState {
+    typename Pair<T>::type py;
+    T Rxo, pso, zso, cl;
+};
+
+template <typename T>
+__device__ __forceinline__ LinkState<T> load_link(const View<T>& v, int l) {
+    LinkState<T> s;
+    s.py = v.pby[l];
+    s.Rxo = v.Rx[l];
+    s.pso = v.ps[l];
+    s.zso = v.zs[l];
+    s.cl = __ldg(v.c + l);
+    return s;
+}
+
 // Link epilogue (slack prox, average, z and price updates) and its residual terms.
 template <typename T>
-__device__ __forceinline__ void link_epilogue(const View<T>& v, int l, T Rxn, int deg, T alpha,
-                                              T rho, T inv_rho, double& r2, double& s2) {
+__device__ __forceinline__ void link_epilogue(const View<T>& v, int l, const LinkState<T>& st,
+                                              T Rxn, int deg, T alpha, T rho, T inv_rho,
+                                              Acc<T>& r2, Acc<T>& s2) {
     using T2 = typename Pair<T>::type;
-    const T2 py = v.pby[l];
-    const T pbo = py.x, y = py.y;
-    const T Rxo = v.Rx[l], pso = v.ps[l], zso = v.zs[l], cl = __ldg(v.c + l);
-    T psn = zso - y * inv_rho;
-    psn = psn < -cl ? -cl : psn;
+    const T pbo = st.py.x, y = st.py.y;
+    T psn = st.zso - y * inv_rho;
+    psn = psn < -st.cl ? -st.cl : psn;
     const T degf = (T)deg;
     const T pbn = (Rxn + psn) / (degf + T(1));
     T2 out;
     out.x = pbn;
     out.y = y + alpha * rho * pbn;
     v.pby[l] = out;
-    v.zs[l] = alpha * (psn - pbn) + (T(1) - alpha) * zso;
+    v.zs[l] = alpha * (psn - pbn) + (T(1) - alpha) * st.zso;
     v.Rx[l] = Rxn;
     v.ps[l] = psn;
-    const T dpb = pbn - pbo, dRx = Rxn - Rxo, dd = (psn - pbn) - (pso - pbo);
-    r2 += (double)((degf + T(1)) * pbn * pbn);
-    s2 += (double)(degf * dpb * dpb - T(2) * dpb * dRx + dd * dd);
+    const T dpb = pbn - pbo, dRx = Rxn - st.Rxo, dd = (psn - pbn) - (st.pso - pbo);
+    r2.add((degf + T(1)) * pbn * pbn);
+    s2.add(degf * dpb * dpb - T(2) * dpb * dRx + dd * dd);
 }
 
-// Sum of x over entries [e0, e1) of the link-major index array, by the whole warp, in a
-// fixed order (lane-strided, two loads in flight per lane, then a shuffle tree).
-template <typename T>
-__device__ __forceinline__ T warp_gather_sum(const int* __restrict__ col_idx,
-                                             const T* __restrict__ x, int e0, int e1, int lane) {
+// Sum of x over entries [e0, e1) of the link-major index array, by one group of G lanes,
+// in a fixed order (lane-strided, two loads in flight per lane, then a shuffle tree).
+template <typename T, class Group>
+__device__ __forceinline__ T group_gather_sum(const Group& g, const int* __restrict__ col_idx,
+                                              const T* __restrict__ x, int e0, int e1) {
+    constexpr int G = kGroup;
+    const int sl = g.thread_rank();
     T s = T(0);
-    for (int e = e0 + lane; e < e1; e += 64) {
+    for (int e = e0 + sl; e < e1; e += 2 * G) {
         const int i0 = __ldg(col_idx + e);
-        const int i1 = e + 32 < e1 ? __ldg(col_idx + e + 32) : -1;
+        const int i1 = e + G < e1 ? __ldg(col_idx + e + G) : -1;
         const T a = __ldg(x + i0);
         const T b = i1 >= 0 ? __ldg(x + i1) : T(0);
         s += a + b;
     }
-    return warp_sum_t(s);
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) s += g.shfl_down(s, o);
+    return s;
 }
 
 template <typename T>
@@ -163,48 +168,54 @@ __global__ void __launch_bounds__(kTh) k_link_rows(View<T> v) {
     Ctl* ctl = v.ctl;
     if (ctl->stop) return;
     const T alpha = (T)ctl->alpha, rho = (T)ctl->rho, inv_rho = (T)(1.0 / ctl->rho);
-    const int lane = threadIdx.x & 31;
+    auto g = cg::tiled_partition<kGroup>(cg::this_thread_block());
+    const bool leader = g.thread_rank() == 0;
     const int m = v.m;
     const int* __restrict__ row_ptr = v.row_ptr;
     const int* __restrict__ col_idx = v.col_idx;
     const T* __restrict__ x = v.x;
-    double r2 = 0.0, s2 = 0.0;
+    Acc<T> r2, s2;
     const int items = m + v.nchunks;
-    const int wstride = gridDim.x * kWarps;
-    for (int it = blockIdx.x * kWarps + (threadIdx.x >> 5); it < items; it += wstride) {
+    constexpr int kGroups = kTh / kGroup;
+    const int gstride = gridDim.x * kGroups;
+    for (int it = blockIdx.x * kGroups + (int)(threadIdx.x / kGroup); it < items; it += gstride) {
         if (it < m) {
             const int p0 = __ldg(row_ptr + it), p1 = __ldg(row_ptr + it + 1);
             if (p1 - p0 > kLongRow) continue;  // done by its chunks
-            const T s = warp_gather_sum(col_idx, x, p0, p1, lane);
-            if (lane == 0) link_epilogue(v, it, s, p1 - p0, alpha, rho, inv_rho, r2, s2);
+            LinkState<T> st;
+            if (leader) st = load_link(v, it);
+            const T s = group_gather_sum(g, col_idx, x, p0, p1);
+            if (leader) link_epilogue(v, it, st, s, p1 - p0, alpha, rho, inv_rho, r2, s2);
         } else {
             const int4 ch = __ldg(v.chunks + (it - m));  // (row, first entry, end entry, first chunk)
-            const T s = warp_gather_sum(col_idx, x, ch.y, ch.z, lane);
+            const T s = group_gather_sum(g, col_idx, x, ch.y, ch.z);
             int fin = 0;
-            if (lane == 0) {
+            if (leader) {
                 v.carry_l[it - m] = s;
                 __threadfence();
                 const int p0 = __ldg(row_ptr + ch.x), p1 = __ldg(row_ptr + ch.x + 1);
                 const int nch = (p1 - p0 + kChunk - 1) / kChunk;
                 fin = atomicAdd(v.arrive_l + ch.w, 1) == nch - 1;
             }
-            fin = __shfl_sync(0xffffffffu, fin, 0);
+            fin = g.shfl(fin, 0);
             if (fin) {  // every chunk of the row is in: sum the slots in chunk order
                 __threadfence();
                 const int p0 = __ldg(row_ptr + ch.x), p1 = __ldg(row_ptr + ch.x + 1);
                 const int nch = (p1 - p0 + kChunk - 1) / kChunk;
                 T t = T(0);
-                for (int q = lane; q < nch; q += 32) t += __ldcg(v.carry_l + ch.w + q);
-                t = warp_sum_t(t);
-                if (lane == 0) {
+                for (int q = g.thread_rank(); q < nch; q += kGroup) t += __ldcg(v.carry_l + ch.w + q);
+#pragma unroll
+                for (int o = kGroup / 2; o > 0; o >>= 1) t += g.shfl_down(t, o);
+                if (leader) {
                     v.arrive_l[ch.w] = 0;
-                    link_epilogue(v, ch.x, t, p1 - p0, alpha, rho, inv_rho, r2, s2);
+                    const LinkState<T> st = load_link(v, ch.x);
+                    link_epilogue(v, ch.x, st, t, p1 - p0, alpha, rho, inv_rho, r2, s2);
                 }
             }
         }
     }
-    const double R2 = block_sum(r2, red);
-    const double S2 = block_sum(s2, red);
+    const double R2 = block_sum(r2.value(), red);
+    const double S2 = block_sum(s2.value(), red);
     if (threadIdx.x == 0) {
         v.part_l[2 * blockIdx.x] = R2;
         v.part_l[2 * blockIdx.x + 1] = S2;
@@ -225,15 +236,11 @@ __global__ void __launch_bounds__(kTh) k_link_rows(View<T> v) {
 }
 
 template <typename T>
-size_t stream_smem() {
-    return sizeof(typename Pair<T>::type) * kCap * kWarps;
-}
-
-template <typename T>
 cudaError_t rows_occupancy(int* occ_s, int* occ_l) {
-    cudaError_t e = cudaFuncSetAttribute(k_stream_rows<T>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)stream_smem<T>());
+    cudaError_t e = cudaSuccess;
+    if (stream_smem<T>() > 48 * 1024)
+        e = cudaFuncSetAttribute(k_stream_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)stream_smem<T>());
     if (e != cudaSuccess) return e;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ_s, k_stream_rows<T>, kTh,
                                                       stream_smem<T>());
@@ -253,7 +260,7 @@ cudaError_t rows_grids(int precision, int n, int m, int nchunks, int* grid_s, in
     if (e != cudaSuccess) return e;
     if (occ_s < 1 || occ_l < 1) return cudaErrorInvalidConfiguration;
     const long long need_s = ((long long)n + kTh - 1) / kTh;
-    const long long need_l = ((long long)m + nchunks + kWarps - 1) / kWarps;
+    const long long need_l = ((long long)m + nchunks + (kTh / kGroup) - 1) / (kTh / kGroup);
     long long gs = (long long)occ_s * sms, gl = (long long)occ_l * sms;
     gs = gs < need_s ? gs : need_s;
     gl = gl < need_l ? gl : need_l;
