@@ -180,7 +180,7 @@ def traffic_record(kernel_key):
     rec = json.load(open(path)).get(kernel_key)
     if not rec:
         return None
-    src = os.path.join(ROOT, "paper_2509_10722_b300", "csrc", "fused.cu")
+    src = os.path.join(ROOT, "paper_2509_10722_b300", "csrc", "rows.cu")
     h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
     return rec if rec.get("source_sha") == h else None
 
@@ -347,7 +347,8 @@ def run_ours(args, dist):
     bytes_per_launch = fp32.bytes[dom]
     achieved = bytes_per_launch / (per_launch_ms[dom] / 1e3) / 1e9
     peak, peak_note = measured_peaks()
-    kernel_key = ["k_stream", "k_link"][dom]
+    kernel_key = ["k_stream_rows", "k_link_rows"][dom] if args.schedule == "rows" else \
+        ["k_stream", "k_link"][dom]
     trec = traffic_record(f"{args.workload}:{kernel_key}")
     iter_bytes = float(sum(fp32.bytes))
     iter_ms = float(np.sum(per_launch_ms))
