@@ -38,18 +38,27 @@ def _dedupe_routes(rng, route_ptr, links, draw, max_rounds=10_000):
         return links
     maxlen = int(lengths.max())
     if maxlen <= 64:
-        route_of = np.repeat(np.arange(n, dtype=np.int64), lengths)
-        pos = np.arange(nnz, dtype=np.int64) - route_ptr[:-1][route_of]
+        # first pass over every route, later passes only over the routes that had a repeat
+        routes = np.arange(n, dtype=np.int64)
         for _ in range(max_rounds):
-            bad = np.zeros(nnz, dtype=bool)
-            for d in range(1, maxlen):
-                eq = links[d:] == links[:-d]
+            lens = lengths[routes]
+            sub_ptr = np.zeros(routes.size + 1, dtype=np.int64)
+            np.cumsum(lens, out=sub_ptr[1:])
+            total = int(sub_ptr[-1])
+            owner = np.repeat(np.arange(routes.size, dtype=np.int64), lens)
+            pos = np.arange(total, dtype=np.int64) - sub_ptr[:-1][owner]
+            gidx = route_ptr[:-1][routes][owner] + pos   # positions in the full link array
+            sub = links[gidx]
+            bad = np.zeros(total, dtype=bool)
+            for d in range(1, int(lens.max()) if lens.size else 0):
+                eq = sub[d:] == sub[:-d]
                 eq &= pos[d:] >= d
                 bad[d:] |= eq
             idx = np.flatnonzero(bad)
             if idx.size == 0:
                 return links
-            links[idx] = draw(idx.size)
+            links[gidx[idx]] = draw(idx.size)
+            routes = np.unique(routes[owner[idx]])
         raise RuntimeError("could not draw distinct links for every route")
     route_of = np.repeat(np.arange(n, dtype=np.int64), lengths)
     for _ in range(max_rounds):

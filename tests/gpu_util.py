@@ -47,3 +47,14 @@ def compare(gpu, ref, tol, floor=1e-3):
 
 def oracle_run(inst, iters, eps=0.0, **kw):
     return oracle.solve(inst, iters, eps_abs=eps, **kw)
+
+
+def decisions_from_hist(hist, period=50):
+    """The rho decision (+1, 0, -1) taken at each update point of a run, read off the rho
+    column of its residual history (rho of iteration k+1 against iteration k)."""
+    rho = hist[:, 2]
+    out = []
+    for k in range(period, rho.size, period):
+        r = rho[k] / rho[k - 1]
+        out.append(1 if r > 1.0 + 1e-12 else (-1 if r < 1.0 - 1e-12 else 0))
+    return np.array(out, dtype=np.int8)

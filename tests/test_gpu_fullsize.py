@@ -1,0 +1,91 @@
+"""Full-size checks, in the launch configuration bench.py times (default schedule).
+
+c2 (n = 1e7, m = 1e6): every element of x and of the prices after the first iterations
+against the oracle run on the whole instance; at convergence, the KKT conditions of the
+problem (properties that hold at any size) and FP32 against the FP64 path.
+c3 (Zipf-skewed links, hot links cut into chunks): the oracle on a 1/50 instance; at full
+size FP32 against FP64 on one rho schedule (c3 does not reach eps_abs = 1e-4 within
+40,000 iterations in either precision, so it has no converged point to check).
+"""
+import numpy as np
+import pytest
+
+from gpu_util import compare, decisions_from_hist, oracle_run, rel, run_gpu
+from paper_2509_10722_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def c2():
+    return W.workload("c2")
+
+
+@pytest.fixture(scope="module")
+def c2_oracle3(c2):
+    return oracle_run(c2, 3)
+
+
+@pytest.mark.parametrize("precision,tol", [("fp32", 1e-4), ("fp64", 1e-10)])
+def test_c2_first_iterations_match_oracle(c2, c2_oracle3, precision, tol):
+    g = run_gpu(c2, 3, precision, history=8)
+    e = compare(g, c2_oracle3, tol)
+    assert e["x"] <= tol and e["lam"] <= tol, e
+    assert e["x_el"] <= 10 * tol and e["lam_el"] <= 10 * tol, e
+    scale = np.max(np.abs(c2_oracle3["hist"][:, :2]))
+    assert np.allclose(g["hist"][:, :2], c2_oracle3["hist"][:, :2], rtol=10 * tol,
+                       atol=tol * 1e-3 * scale)
+
+
+@pytest.fixture(scope="module")
+def c2_solutions(c2):
+    f32 = run_gpu(c2, 20_000, "fp32", eps=1e-4, history=64)
+    f64 = run_gpu(c2, 20_000, "fp64", eps=1e-4, history=64)
+    return f32, f64
+
+
+def test_c2_converges_and_fp32_agrees_with_fp64(c2_solutions):
+    f32, f64 = c2_solutions
+    assert f32["status"] == 0 and f64["status"] == 0
+    o32, o64 = f32["info"]["objective"], f64["info"]["objective"]
+    assert abs(o32 - o64) <= 1e-5 * abs(o64)
+    assert rel(f32["x"], f64["x"]) <= 1e-3 and rel(f32["lam"], f64["lam"]) <= 1e-3
+
+
+def test_c2_kkt_at_tight_tolerance(c2):
+    """The stopping test of the paper is an RMS over 5.6e7 terminals: at eps_abs = 1e-4 the
+    worst link can still be ~20% over capacity.  Run to eps_abs = 1e-6 in FP64 and check
+    the KKT conditions of the NUM problem at full size (duality gap ~1e-6 measured)."""
+    from oracle import kkt
+    g = run_gpu(c2, 20_000, "fp64", eps=1e-6, history=64)
+    assert g["status"] == 0
+    d = kkt.diagnostics(c2, g["x"], g["lam"])
+    assert d["box"] == 0.0 and d["dual_neg"] < 2e-3
+    assert d["feas"] < 2e-2 and d["comp"] < 2e-2 and d["stat"] < 2e-2
+    assert abs(d["gap"]) < 1e-5
+
+
+@pytest.fixture(scope="module")
+def c3_small():
+    return W.workload("c3", scale=0.02)  # n = 4e5, m = 4e4; hottest link ~57% of streams
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("fp32", 1e-4)])
+def test_c3_scaled_matches_oracle(c3_small, precision, tol):
+    ref = oracle_run(c3_small, 60)
+    sched = ref["decisions"] if precision == "fp32" else None
+    g = run_gpu(c3_small, 60, precision, schedule_decisions=sched)
+    e = compare(g, ref, tol)
+    assert e["x"] <= tol and e["lam"] <= tol, e
+
+
+def test_c3_full_size_fp32_tracks_fp64():
+    """Full c3 (1.4e8 entries; 3,906 links above 2,048 streams are cut into chunks, the
+    hottest has 1.1e7 streams): FP32 on the FP64 run's rho schedule stays within 1e-4 of
+    it after 300 iterations."""
+    c3 = W.workload("c3")
+    f64 = run_gpu(c3, 300, "fp64", history=300)
+    f32 = run_gpu(c3, 300, "fp32", history=300,
+                  schedule_decisions=decisions_from_hist(f64["hist"]))
+    e = compare(f32, f64, 1e-4)
+    assert e["x"] <= 1e-4 and e["lam"] <= 1e-4, e
