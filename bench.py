@@ -140,25 +140,31 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
-        rows = list(csv.reader(io.StringIO(open(self.path).read())))
+        text = open(self.path).read()
         os.unlink(self.path)
-        sm, smax, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for r in rows:
-            if len(r) < 9:
-                continue
-            try:
-                sm.append(float(r[1]))
-                smax.append(float(r[2]))
-            except ValueError:
-                continue
-            for name, val in zip(names, r[5:9]):
-                if val.strip().lower() == "active":
-                    reasons.add(name)
-        if not sm:
-            return None
-        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)),
-                "reasons": sorted(reasons), "samples": len(sm)}
+        return parse_clocks(text)
+
+
+def parse_clocks(text):
+    """Summary of `nvidia-smi --query-gpu=CLOCK_QUERY --format=csv,noheader,nounits`
+    samples: median SM clock, max SM clock, and the throttle reasons seen active."""
+    sm, smax, reasons = [], [], set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for r in csv.reader(io.StringIO(text)):
+        if len(r) < 9:
+            continue
+        try:
+            sm.append(float(r[1]))
+            smax.append(float(r[2]))
+        except ValueError:
+            continue
+        for name, val in zip(names, r[5:9]):
+            if val.strip().lower() == "active":
+                reasons.add(name)
+    if not sm:
+        return None
+    return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)),
+            "reasons": sorted(reasons), "samples": len(sm)}
 
 
 # ---- helpers --------------------------------------------------------------------------------------
