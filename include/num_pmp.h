@@ -92,6 +92,10 @@ typedef struct {
  *   schedule    0 (default) or NUM_SCHEDULE_ROWS: row-parallel fused kernels (a warp per
  *               32 streams, a warp per link, links above 2048 streams cut into chunks);
  *               NUM_SCHEDULE_TILES: merge-path tiles of tile_items items (any skew)
+ *   reorder     1 (default): place streams in the order of the first link of their route
+ *               (stable), so that streams sharing that link are adjacent and the gathers
+ *               of both kernels share L2 sectors; results are reported in the caller's
+ *               order; 0: keep the caller's order
  *   profile     1: record a CUDA event on the handle's stream after every kernel of every
  *               iteration (inside the replayed graphs) and accumulate per-kernel device
  *               times, read with num_get_kernel_times; 0 (default): no events
@@ -109,6 +113,7 @@ typedef struct {
     int32_t history;
     int32_t use_graph;
     int32_t schedule;
+    int32_t reorder;
     int32_t profile;
     const num_allocator* allocator;
 } num_params;

@@ -50,7 +50,8 @@ class num_params(ctypes.Structure):
                 ("rho_period", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("check_every", ctypes.c_int32), ("tile_items", ctypes.c_int32),
                 ("history", ctypes.c_int32), ("use_graph", ctypes.c_int32),
-                ("schedule", ctypes.c_int32), ("profile", ctypes.c_int32),
+                ("schedule", ctypes.c_int32), ("reorder", ctypes.c_int32),
+                ("profile", ctypes.c_int32),
                 ("allocator", ctypes.POINTER(num_allocator))]
 
 

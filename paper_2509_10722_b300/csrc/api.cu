@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstdio>
@@ -65,6 +66,7 @@ struct num_problem {
     int2 *tiles_s = nullptr, *tiles_l = nullptr;
     int ntiles_s = 0, ntiles_l = 0, tile_s = 0, tile_l = 0, grid_s = 0, grid_l = 0;
     int sched_kind = NUM_SCHEDULE_ROWS;  // fused paths: row kernels or merge-path tiles
+    int* perm = nullptr;                 // caller's index of the stream at each position
     int4* chunks = nullptr;              // row kernels: chunks of the long links
     int nchunks = 0;
     int narrive_l = 0;                   // entries of arrive_l
@@ -193,6 +195,7 @@ View<T> make_view(const num_problem* h) {
     v.grid_l = h->grid_l;
     v.chunks = h->chunks;
     v.nchunks = h->nchunks;
+    v.perm = h->perm;
     v.ctl = h->ctl;
     v.hist = h->hist;
     v.sched = h->sched;
@@ -293,6 +296,7 @@ int check_params(const num_params& p) {
     if (p.profile != 0 && p.profile != 1) return fail(NUM_ERR_INVALID, "profile must be 0 or 1");
     if (p.schedule < 0 || p.schedule > NUM_SCHEDULE_TILES)
         return fail(NUM_ERR_INVALID, "unknown schedule");
+    if (p.reorder != 0 && p.reorder != 1) return fail(NUM_ERR_INVALID, "reorder must be 0 or 1");
     if (p.allocator && (!p.allocator->alloc || !p.allocator->release))
         return fail(NUM_ERR_INVALID, "allocator needs alloc and release");
     return NUM_OK;
@@ -453,6 +457,13 @@ int create_impl(num_problem** out, int64_t n, int64_t m, const int64_t* route_pt
     s.scan_tmp_len = pmp::scan_tmp_len(s.hist_len);
     s.hist = (int*)A(4 * s.hist_len);
     s.scan_tmp = (int*)A(4 * s.scan_tmp_len);
+    const bool reorder = prm.reorder != 0;
+    h->perm = reorder ? (int*)A(4 * N) : nullptr;
+    int64_t* d_rp2 = reorder ? (int64_t*)A(8 * (N + 1)) : nullptr;
+    int* d_rl2 = reorder ? (int*)A(4 * NNZ) : nullptr;
+    int* d_lens = reorder ? (int*)A(4 * (N + 1)) : nullptr;
+    int* d_ptr32 = reorder ? (int*)A(4 * (N + 1)) : nullptr;
+    int* d_ptmp = reorder ? (int*)A(4 * pmp::scan_tmp_len(N + 1)) : nullptr;
     int* d_ccount = rowk ? (int*)A(4 * (M + 1)) : nullptr;
     int* d_coff = rowk ? (int*)A(4 * (M + 1)) : nullptr;
     int* d_ctmp = rowk ? (int*)A(4 * pmp::scan_tmp_len(M + 1)) : nullptr;
@@ -516,8 +527,14 @@ int create_impl(num_problem** out, int64_t n, int64_t m, const int64_t* route_pt
         destroy_handle(h);
         return fail(NUM_ERR_INVALID, describe_bits(err_bits));
     }
-    CK(pmp::build_operator((int)n, (int)m, (int)nnz, route_ptr, route_links, h->col_ptr,
-                           h->row_idx, h->row_ptr, h->col_idx, s, d_err, st),
+    if (reorder) {
+        CK(pmp::relabel_streams((int)n, (int)m, route_ptr, route_links, s, h->perm, d_lens,
+                                d_ptr32, d_ptmp, d_rp2, d_rl2, st),
+           "ordering the streams");
+    }
+    CK(pmp::build_operator((int)n, (int)m, (int)nnz, reorder ? d_rp2 : route_ptr,
+                           reorder ? d_rl2 : route_links, h->col_ptr, h->row_idx, h->row_ptr,
+                           h->col_idx, s, d_err, st),
        "building the operator");
     CK(cudaMemcpyAsync(&err_bits, d_err, sizeof(int), cudaMemcpyDeviceToHost, st), "read flags");
     CK(cudaStreamSynchronize(st), "operator build");
@@ -531,12 +548,14 @@ int create_impl(num_problem** out, int64_t n, int64_t m, const int64_t* route_pt
     h->lo_u = lmin;
     h->hi_u = hmin;
     if (fp32)
-        CK(pmp::convert_params<float>((int)n, (int)m, c, utype, w, lo, hi, (float*)h->c,
-                                      (float*)h->wt, (float*)h->lo, (float*)h->hi, st),
+        CK(pmp::convert_params<float>((int)n, (int)m, c, utype, w, lo, hi, h->perm,
+                                      (float*)h->c, (float*)h->wt, (float*)h->lo, (float*)h->hi,
+                                      st),
            "converting parameters");
     else
-        CK(pmp::convert_params<double>((int)n, (int)m, c, utype, w, lo, hi, (double*)h->c,
-                                       (double*)h->wt, (double*)h->lo, (double*)h->hi, st),
+        CK(pmp::convert_params<double>((int)n, (int)m, c, utype, w, lo, hi, h->perm,
+                                       (double*)h->c, (double*)h->wt, (double*)h->lo,
+                                       (double*)h->hi, st),
            "converting parameters");
     if (tiles) {
         CK(pmp::build_tiles(h->col_ptr, (int)n, h->Js, h->tile_s, h->ntiles_s, h->tiles_s, st),
@@ -570,7 +589,8 @@ int create_impl(num_problem** out, int64_t n, int64_t m, const int64_t* route_pt
     for (void* q : {(void*)d_rp, (void*)d_rl, (void*)d_c, (void*)d_w, (void*)d_lo, (void*)d_hi,
                     (void*)d_ut, (void*)d_err, (void*)d_box, (void*)s.keys_a, (void*)s.vals_a,
                     (void*)s.keys_b, (void*)s.vals_b, (void*)s.hist, (void*)s.scan_tmp,
-                    (void*)d_ccount, (void*)d_coff, (void*)d_ctmp})
+                    (void*)d_ccount, (void*)d_coff, (void*)d_ctmp, (void*)d_rp2, (void*)d_rl2,
+                    (void*)d_lens, (void*)d_ptr32, (void*)d_ptmp})
         dev_free(h, q);
 #undef CK
     *out = h;
@@ -600,6 +620,7 @@ void num_default_params(num_params* p) {
     p->history = 4096;
     p->use_graph = 1;
     p->schedule = 0;
+    p->reorder = 1;
     p->profile = 0;
     p->allocator = nullptr;
 }
@@ -801,9 +822,17 @@ int num_get_operator(const num_problem* hc, int64_t* row_ptr, int32_t* col_idx) 
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(col_idx, h->col_idx, 4 * (size_t)h->nnz, cudaMemcpyDeviceToHost,
                             h->stream);
+    std::vector<int> perm(h->perm ? (size_t)h->n : 0);
+    if (e == cudaSuccess && h->perm)
+        e = cudaMemcpyAsync(perm.data(), h->perm, 4 * perm.size(), cudaMemcpyDeviceToHost,
+                            h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(e, "reading the operator");
     for (size_t i = 0; i < rp.size(); ++i) row_ptr[i] = rp[i];
+    if (h->perm) {  // the device works on relabeled streams: report the caller's ids
+        for (int64_t q = 0; q < h->nnz; ++q) col_idx[q] = perm[col_idx[q]];
+        for (int64_t l = 0; l < h->m; ++l) std::sort(col_idx + rp[l], col_idx + rp[l + 1]);
+    }
     return NUM_OK;
 }
 

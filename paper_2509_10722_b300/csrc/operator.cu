@@ -262,6 +262,36 @@ __global__ void k_tiles(const int* __restrict__ ptr, int nrows, int J, int tile,
     }
 }
 
+// ---- stream relabeling: streams ordered by the first link of their route ---------------------
+__global__ void k_first_link(int n, const int64_t* __restrict__ route_ptr,
+                             const int* __restrict__ route_links, int* keys, int* vals) {
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+        keys[j] = route_links[route_ptr[j]];
+        vals[j] = j;
+    }
+}
+
+// lens[j] = route length of the stream placed at position j (lens[n] = 0, for the scan)
+__global__ void k_perm_lengths(int n, const int64_t* __restrict__ route_ptr,
+                               const int* __restrict__ perm, int* lens) {
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j <= n; j += gridDim.x * blockDim.x)
+        lens[j] = j < n ? (int)(route_ptr[perm[j] + 1] - route_ptr[perm[j]]) : 0;
+}
+
+__global__ void k_perm_routes(int n, const int64_t* __restrict__ route_ptr,
+                              const int* __restrict__ route_links, const int* __restrict__ perm,
+                              const int* __restrict__ ptr32, int64_t* route_ptr_new,
+                              int* route_links_new) {
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j <= n; j += gridDim.x * blockDim.x) {
+        route_ptr_new[j] = ptr32[j];
+        if (j < n) {
+            const int64_t src = route_ptr[perm[j]];
+            const int len = ptr32[j + 1] - ptr32[j];
+            for (int e = 0; e < len; ++e) route_links_new[ptr32[j] + e] = route_links[src + e];
+        }
+    }
+}
+
 __global__ void k_chunk_counts(const int* __restrict__ row_ptr, int m, int* counts) {
     for (int l = blockIdx.x * blockDim.x + threadIdx.x; l <= m; l += gridDim.x * blockDim.x) {
         int c = 0;
@@ -290,14 +320,15 @@ __global__ void k_chunk_fill(const int* __restrict__ row_ptr, int m, const int* 
 template <typename T>
 __global__ void k_convert(int n, int m, const double* __restrict__ c,
                           const uint8_t* __restrict__ utype, const double* __restrict__ w,
-                          const double* __restrict__ lo, const double* __restrict__ hi, T* c_t,
-                          T* wt_t, T* lo_t, T* hi_t) {
+                          const double* __restrict__ lo, const double* __restrict__ hi,
+                          const int* __restrict__ perm, T* c_t, T* wt_t, T* lo_t, T* hi_t) {
     const int stride = gridDim.x * blockDim.x;
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
-        const T wj = (T)w[j];
-        wt_t[j] = utype[j] == 0 ? wj : -wj;
-        if (lo_t) lo_t[j] = lo ? (T)lo[j] : T(0);
-        if (hi_t) hi_t[j] = (T)hi[j];
+        const int o = perm ? perm[j] : j;  // original index of the stream at position j
+        const T wj = (T)w[o];
+        wt_t[j] = utype[o] == 0 ? wj : -wj;
+        if (lo_t) lo_t[j] = lo ? (T)lo[o] : T(0);
+        if (hi_t) hi_t[j] = (T)hi[o];
     }
     for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < m; l += stride) c_t[l] = (T)c[l];
 }
@@ -335,7 +366,7 @@ k_export(View<T> v, double* x_out, double* y_out, double* part) {
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < v.n; j += stride) {
         const double xj = (double)v.x[j];
         const double wt = (double)v.wt[j];
-        if (x_out) x_out[j] = xj;
+        if (x_out) x_out[v.perm ? v.perm[j] : j] = xj;  // back to the caller's stream order
         obj += wt > 0.0 ? wt * log(xj) : -wt * xj;  // U_j(x_j), Sec. II
     }
     if (y_out) {
@@ -408,6 +439,35 @@ cudaError_t validate_inputs(int n, int m, const int64_t* route_ptr, const int* r
     return cudaGetLastError();
 }
 
+// Stable LSD radix sort of `count` (key, value) pairs held in s.keys_a / s.vals_a by key
+// (keys in [0, key_bound)); *keys / *vals receive the buffers holding the sorted pairs.
+cudaError_t radix_sort_pairs(int count, int key_bound, const Scratch& s, int** keys, int** vals,
+                             cudaStream_t st) {
+    cudaError_t e;
+    int bits = 0;
+    while (bits < 31 && (1ll << bits) < (long long)key_bound) ++bits;
+    const int passes = (bits + kRadixBits - 1) / kRadixBits;
+    int *ki = s.keys_a, *vi = s.vals_a, *ko = s.keys_b, *vo = s.vals_b;
+    const int nblocks = count > 0 ? (count + kSortTile - 1) / kSortTile : 0;
+    for (int p = 0; p < passes && nblocks > 0; ++p) {
+        const int shift = p * kRadixBits;
+        k_radix_hist<<<nblocks, kSortThreads, 0, st>>>(ki, count, shift, s.hist, nblocks);
+        note_launches(1);
+        if ((e = scan_exclusive(s.hist, s.hist, (size_t)nblocks * kRadix, s.scan_tmp, st)) !=
+            cudaSuccess)
+            return e;
+        k_radix_scatter<<<nblocks, kSortThreads, 0, st>>>(ki, vi, count, shift, s.hist, nblocks,
+                                                          ko, vo);
+        note_launches(1);
+        int* t;
+        t = ki; ki = ko; ko = t;
+        t = vi; vi = vo; vo = t;
+    }
+    *keys = ki;
+    *vals = vi;
+    return cudaGetLastError();
+}
+
 cudaError_t build_operator(int n, int m, int nnz, const int64_t* route_ptr,
                            const int* route_links, int* col_ptr, int* row_idx, int* row_ptr,
                            int* col_idx, const Scratch& s, int* err_bits, cudaStream_t st) {
@@ -421,35 +481,41 @@ cudaError_t build_operator(int n, int m, int nnz, const int64_t* route_ptr,
     if ((e = cudaMemcpyAsync(s.keys_a, route_links, sizeof(int) * (size_t)nnz,
                              cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
         return e;
-    int bits = 0;
-    while (bits < 31 && (1ll << bits) < (long long)m) ++bits;
-    const int passes = (bits + kRadixBits - 1) / kRadixBits;
-    int *ki = s.keys_a, *vi = s.vals_a, *ko = s.keys_b, *vo = s.vals_b;
-    const int nblocks = nnz > 0 ? (nnz + kSortTile - 1) / kSortTile : 0;
-    for (int p = 0; p < passes && nblocks > 0; ++p) {
-        const int shift = p * kRadixBits;
-        k_radix_hist<<<nblocks, kSortThreads, 0, st>>>(ki, nnz, shift, s.hist, nblocks);
-        note_launches(1);
-        if ((e = scan_exclusive(s.hist, s.hist, (size_t)nblocks * kRadix, s.scan_tmp, st)) !=
-            cudaSuccess)
-            return e;
-        k_radix_scatter<<<nblocks, kSortThreads, 0, st>>>(ki, vi, nnz, shift, s.hist, nblocks, ko,
-                                                          vo);
-        note_launches(1);
-        int* t;
-        t = ki; ki = ko; ko = t;
-        t = vi; vi = vo; vo = t;
-    }
+    int *ki = nullptr, *vi = nullptr;
+    if ((e = radix_sort_pairs(nnz, m, s, &ki, &vi, st)) != cudaSuccess) return e;
     if ((e = cudaMemcpyAsync(col_idx, vi, sizeof(int) * (size_t)nnz, cudaMemcpyDeviceToDevice,
                              st)) != cudaSuccess)
         return e;
     k_row_ptr<<<blocks_for((long long)nnz + 1, kThreads, 65535), kThreads, 0, st>>>(ki, nnz, m,
                                                                                     row_ptr);
     note_launches(1);
-    if (nnz > 1)
+    if (nnz > 1) {
         k_find_duplicates<<<blocks_for(nnz, kThreads, 8192), kThreads, 0, st>>>(ki, vi, nnz,
                                                                                 err_bits);
         note_launches(1);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t relabel_streams(int n, int m, const int64_t* route_ptr, const int* route_links,
+                            const Scratch& s, int* perm, int* lens, int* ptr32, int* scan_tmp,
+                            int64_t* route_ptr_new, int* route_links_new, cudaStream_t st) {
+    cudaError_t e;
+    k_first_link<<<blocks_for(n, kThreads, 65535), kThreads, 0, st>>>(n, route_ptr, route_links,
+                                                                       s.keys_a, s.vals_a);
+    note_launches(1);
+    int *ki = nullptr, *vi = nullptr;
+    if ((e = radix_sort_pairs(n, m, s, &ki, &vi, st)) != cudaSuccess) return e;
+    if ((e = cudaMemcpyAsync(perm, vi, sizeof(int) * (size_t)n, cudaMemcpyDeviceToDevice, st)) !=
+        cudaSuccess)
+        return e;
+    k_perm_lengths<<<blocks_for((long long)n + 1, kThreads, 65535), kThreads, 0, st>>>(
+        n, route_ptr, perm, lens);
+    note_launches(1);
+    if ((e = scan_exclusive(lens, ptr32, (size_t)n + 1, scan_tmp, st)) != cudaSuccess) return e;
+    k_perm_routes<<<blocks_for((long long)n + 1, kThreads, 65535), kThreads, 0, st>>>(
+        n, route_ptr, route_links, perm, ptr32, route_ptr_new, route_links_new);
+    note_launches(1);
     return cudaGetLastError();
 }
 
@@ -482,19 +548,21 @@ cudaError_t fill_chunks(const int* row_ptr, int m, const int* offs, int4* chunks
 
 template <typename T>
 cudaError_t convert_params(int n, int m, const double* c, const uint8_t* utype,
-                           const double* w, const double* lo, const double* hi, T* c_t,
-                           T* wt_t, T* lo_t, T* hi_t, cudaStream_t st) {
+                           const double* w, const double* lo, const double* hi, const int* perm,
+                           T* c_t, T* wt_t, T* lo_t, T* hi_t, cudaStream_t st) {
     k_convert<T><<<blocks_for(n > m ? n : m, kThreads, 65535), kThreads, 0, st>>>(
-        n, m, c, utype, w, lo, hi, c_t, wt_t, lo_t, hi_t);
+        n, m, c, utype, w, lo, hi, perm, c_t, wt_t, lo_t, hi_t);
     note_launches(1);
     return cudaGetLastError();
 }
 template cudaError_t convert_params<float>(int, int, const double*, const uint8_t*,
-                                           const double*, const double*, const double*, float*,
-                                           float*, float*, float*, cudaStream_t);
+                                           const double*, const double*, const double*,
+                                           const int*, float*, float*, float*, float*,
+                                           cudaStream_t);
 template cudaError_t convert_params<double>(int, int, const double*, const uint8_t*,
                                             const double*, const double*, const double*,
-                                            double*, double*, double*, double*, cudaStream_t);
+                                            const int*, double*, double*, double*, double*,
+                                            cudaStream_t);
 
 int export_partial_blocks(int n) { return blocks_for(n, kExportThreads, 1024); }
 

@@ -84,6 +84,7 @@ struct View {
     int grid_s, grid_l;
     const int4* chunks;         // row kernels: (link, first entry, end entry, first chunk)
     int nchunks;
+    const int* perm;            // caller's index of the stream at each position (or NULL)
     Ctl* ctl;
     double* hist;
     const signed char* sched;
@@ -169,6 +170,12 @@ cudaError_t validate_inputs(int n, int m, const int64_t* route_ptr, const int* r
                             const double* c, const uint8_t* utype, const double* w,
                             const double* lo, const double* hi, int* err_bits,
                             unsigned long long* box_minmax, cudaStream_t st);
+// Order the streams by the first link of their route (stable): perm[j] = caller's index of
+// the stream placed at position j; route_ptr_new / route_links_new receive the routes in
+// that order.  lens and ptr32 are int[n+1] scratch, scan_tmp holds scan_tmp_len(n + 1).
+cudaError_t relabel_streams(int n, int m, const int64_t* route_ptr, const int* route_links,
+                            const Scratch& s, int* perm, int* lens, int* ptr32, int* scan_tmp,
+                            int64_t* route_ptr_new, int* route_links_new, cudaStream_t st);
 // Build the CSC int32 pointer, and the CSR (row_ptr, col_idx) by a stable device radix sort.
 // Also flags duplicates (VB_DUPLICATE) into err_bits.
 cudaError_t build_operator(int n, int m, int nnz, const int64_t* route_ptr,
@@ -178,11 +185,11 @@ cudaError_t build_operator(int n, int m, int nnz, const int64_t* route_ptr,
 // array with one extra item per row (J = ptr[nrows] + nrows).
 cudaError_t build_tiles(const int* ptr, int nrows, int J, int tile, int ntiles, int2* tiles,
                         cudaStream_t st);
-// Convert parameters to the iteration precision.
+// Convert parameters to the iteration precision (stream arrays in relabeled order).
 template <typename T>
 cudaError_t convert_params(int n, int m, const double* c, const uint8_t* utype,
-                           const double* w, const double* lo, const double* hi, T* c_t,
-                           T* wt_t, T* lo_t, T* hi_t, cudaStream_t st);
+                           const double* w, const double* lo, const double* hi, const int* perm,
+                           T* c_t, T* wt_t, T* lo_t, T* hi_t, cudaStream_t st);
 double ordered_key_to_double(unsigned long long k);
 // x (T) -> double copies; objective partials and its FP64 reduction into ctl->objective.
 template <typename T>

@@ -33,11 +33,12 @@ def _check_hist(gh, oh, rtol):
     assert np.allclose(gh[:, :2], oh[:, :2], rtol=rtol, atol=rtol * 1e-3 * scale)
 
 
-@pytest.mark.parametrize("precision,schedule", [("fp64", 1), ("fp64", 2), ("plain", 0)])
+@pytest.mark.parametrize("precision,schedule,reorder", [("fp64", 1, 1), ("fp64", 2, 1),
+                                                        ("plain", 0, 1), ("fp64", 1, 0)])
 @pytest.mark.parametrize("iters", [1, 7, 50, 51, 300, 2000])
-def test_c1_fp64_paths_match_oracle(c1, c1_oracle, precision, schedule, iters):
+def test_c1_fp64_paths_match_oracle(c1, c1_oracle, precision, schedule, reorder, iters):
     ref = c1_oracle[iters]
-    g = run_gpu(c1, iters, precision, schedule=schedule)
+    g = run_gpu(c1, iters, precision, schedule=schedule, reorder=reorder)
     assert g["iters"] == iters
     e = compare(g, ref, FP64_TOL)
     assert e["x"] <= FP64_TOL and e["lam"] <= FP64_TOL, e
@@ -113,12 +114,13 @@ SCHED = {"rows": 1, "tiles": 2}
 
 
 @pytest.mark.parametrize("name,inst,params", CASES, ids=[c[0] for c in CASES])
-@pytest.mark.parametrize("precision,schedule", [("fp64", "rows"), ("fp64", "tiles"),
-                                                ("plain", "rows")])
-def test_shapes_fp64_match_oracle(name, inst, params, precision, schedule):
+@pytest.mark.parametrize("precision,schedule,reorder", [("fp64", "rows", 1), ("fp64", "tiles", 1),
+                                                        ("plain", "rows", 1),
+                                                        ("fp64", "rows", 0)])
+def test_shapes_fp64_match_oracle(name, inst, params, precision, schedule, reorder):
     iters = 200
     ref = oracle_run(inst, iters)
-    g = run_gpu(inst, iters, precision, schedule=SCHED[schedule], **params)
+    g = run_gpu(inst, iters, precision, schedule=SCHED[schedule], reorder=reorder, **params)
     e = compare(g, ref, FP64_TOL)
     assert e["x"] <= FP64_TOL and e["lam"] <= FP64_TOL, e
     assert e["x_el"] <= 1e-9 and e["lam_el"] <= 1e-9, e
@@ -136,9 +138,10 @@ def test_shapes_fp32_match_oracle(name, inst, params, schedule):
 
 
 @pytest.mark.parametrize("name,inst,params", CASES[:6], ids=[c[0] for c in CASES[:6]])
-def test_operator_is_bit_exact(name, inst, params):
+@pytest.mark.parametrize("reorder", [0, 1])
+def test_operator_is_bit_exact(name, inst, params, reorder):
     from paper_2509_10722_b300 import capi
-    with capi.Problem(inst, **params) as p:
+    with capi.Problem(inst, reorder=reorder, **params) as p:
         rp, ci = p.operator()
     rp_ref, ci_ref = W.csr_of(inst)
     assert np.array_equal(rp, rp_ref) and np.array_equal(ci, ci_ref)
