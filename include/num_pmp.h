@@ -236,6 +236,52 @@ NUM_API int num_objective_noalloc(int64_t n, const double* x, const uint8_t* uty
 /* Free every resource of the handle.  NULL is ignored. */
 NUM_API void num_destroy(num_problem* h);
 
+/* ---- batches of independent instances --------------------------------------------------- */
+/* Many NUM instances of uneven sizes solved together on one GPU: two kernel launches per
+ * iteration for the whole batch, each instance with its own rho, iteration count and
+ * stopping test (Sec. III-F, III-G); an instance that stops is skipped by later
+ * iterations.  Batches are a service of this library (the paper solves one instance at a
+ * time). */
+typedef struct num_batch num_batch; /* opaque; owns all of its device memory */
+
+/* Create a batch from HOST arrays.  The instances are stacked in one numbering: instance i
+ * owns streams [stream_off[i], stream_off[i+1]) and links [link_off[i], link_off[i+1])
+ * (int64[count+1] each, starting at 0, strictly increasing: every instance has >= 1 stream
+ * and >= 1 link).  route_ptr / route_links / c / utype / w / lo / hi describe the stacked
+ * problem exactly as for num_create, with GLOBAL link ids; every route of instance i must
+ * use links of instance i only (else NUM_ERR_INVALID).  p->precision must be
+ * NUM_FUSED_FP32 or NUM_FUSED_FP64 and p->schedule the row kernels; all instances share
+ * the other parameters.  Synchronizes the stream. */
+NUM_API int num_batch_create(num_batch** out, int32_t count, const int64_t* stream_off,
+                             const int64_t* link_off, const int64_t* route_ptr,
+                             const int32_t* route_links, const double* c,
+                             const uint8_t* utype, const double* w, const double* lo,
+                             const double* hi, const num_params* p, void* cuda_stream);
+
+/* Force the first len rho decisions of every instance: decisions[i * len + q] is the
+ * decision of instance i at its q-th update point (-1, 0, +1; host array, copied). */
+NUM_API int num_batch_set_rho_schedules(num_batch* b, const int8_t* decisions, int64_t len);
+
+/* Run at most max_iters further iterations of every instance (eps_abs as in num_solve,
+ * with eps_tol = eps_abs sqrt(J_i) per instance).  iters_done[count] and status[count]
+ * (host arrays, may be NULL) receive each instance's iterations and NUM_OK /
+ * NUM_NOT_CONVERGED / NUM_ERR_NUMERIC.  Returns NUM_OK if every instance converged,
+ * NUM_NOT_CONVERGED if some hit the limit, NUM_ERR_NUMERIC if some residual became
+ * non-finite.  Synchronizes the stream. */
+NUM_API int num_batch_solve(num_batch* b, int64_t max_iters, double eps_abs,
+                            int64_t* iters_done, int32_t* status);
+
+/* Host copies of the stacked solution: x[total n], prices[total m] (each may be NULL) and
+ * info[count * NUM_INFO_LEN], one NUM_INFO_* record per instance (may be NULL). */
+NUM_API int num_batch_get(const num_batch* b, double* x, double* prices, double* info);
+
+/* As num_get_kernel_times, for the batch's two kernels (profile = 1). */
+NUM_API int num_batch_get_kernel_times(const num_batch* b, double* ms, int64_t* launches,
+                                       int32_t max_kernels, int32_t* nkernels);
+
+/* Free every resource of the batch.  NULL is ignored. */
+NUM_API void num_batch_destroy(num_batch* b);
+
 /* Static text for a status code. */
 NUM_API const char* num_strerror(int code);
 

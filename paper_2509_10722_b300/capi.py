@@ -84,6 +84,13 @@ def _load():
         "num_get_kernel_times": (ctypes.c_int, [P, P, P, i32, ctypes.POINTER(i32)]),
         "num_kernel_launches": (ctypes.c_int64, []),
         "num_objective_noalloc": (ctypes.c_int, [i64, P, P, P, P, P]),
+        "num_batch_create": (ctypes.c_int, [ctypes.POINTER(P), i32, P, P, P, P, P, P, P, P, P,
+                                            pp, P]),
+        "num_batch_set_rho_schedules": (ctypes.c_int, [P, P, i64]),
+        "num_batch_solve": (ctypes.c_int, [P, i64, d, P, P]),
+        "num_batch_get": (ctypes.c_int, [P, P, P, P]),
+        "num_batch_get_kernel_times": (ctypes.c_int, [P, P, P, i32, ctypes.POINTER(i32)]),
+        "num_batch_destroy": (None, [P]),
         "num_destroy": (None, [P]),
         "num_strerror": (ctypes.c_char_p, [ctypes.c_int]),
         "num_last_error": (ctypes.c_char_p, []),
@@ -99,7 +106,9 @@ _lib = _load()
 EXPORTED = ("num_default_params", "num_create", "num_create_device", "num_set_rho_schedule",
             "num_solve", "num_get", "num_get_device", "num_get_history", "num_get_operator",
             "num_reset", "num_iteration_bytes", "num_get_kernel_times", "num_kernel_launches",
-            "num_objective_noalloc", "num_destroy", "num_strerror", "num_last_error")
+            "num_objective_noalloc", "num_destroy", "num_strerror", "num_last_error",
+            "num_batch_create", "num_batch_set_rho_schedules", "num_batch_solve",
+            "num_batch_get", "num_batch_get_kernel_times", "num_batch_destroy")
 
 
 def library():
@@ -274,6 +283,94 @@ def num_objective_noalloc(n, x, utype, w, objective, stream=None):
 
 def num_destroy(h):
     _lib.num_destroy(h)
+
+
+def stack_instances(insts):
+    """Stack instance dicts block-diagonally: returns (stream_off, link_off, stacked dict)
+    with global link ids (pure index bookkeeping for num_batch_create)."""
+    so = np.zeros(len(insts) + 1, dtype=np.int64)
+    lo = np.zeros(len(insts) + 1, dtype=np.int64)
+    for i, t in enumerate(insts):
+        so[i + 1] = so[i] + int(t["n"])
+        lo[i + 1] = lo[i] + int(t["m"])
+    nnz_off = np.cumsum([0] + [int(t["route_ptr"][-1]) for t in insts])
+    route_ptr = np.concatenate([[0]] + [np.asarray(t["route_ptr"][1:], np.int64) + nnz_off[i]
+                                        for i, t in enumerate(insts)]).astype(np.int64)
+    route_links = np.concatenate([np.asarray(t["route_links"], np.int64) + lo[i]
+                                  for i, t in enumerate(insts)]).astype(np.int32)
+    cat = {k: np.concatenate([np.asarray(t[k]) for t in insts])
+           for k in ("c", "utype", "w", "lo", "hi")}
+    stacked = dict(n=int(so[-1]), m=int(lo[-1]), route_ptr=route_ptr, route_links=route_links,
+                   **cat)
+    return so, lo, stacked
+
+
+class Batch:
+    """Owner of a num_batch over a list of instance dicts (see workloads.py)."""
+
+    def __init__(self, insts, stream=None, **params):
+        self.count = len(insts)
+        self.so, self.lo, st = stack_instances(insts)
+        self.n, self.m = st["n"], st["m"]
+        self.params = num_default_params(**params)
+        h = ctypes.c_void_p()
+        arrs = [np.ascontiguousarray(st["route_ptr"], np.int64),
+                np.ascontiguousarray(st["route_links"], np.int32),
+                np.ascontiguousarray(st["c"], np.float64), np.ascontiguousarray(st["utype"], np.uint8),
+                np.ascontiguousarray(st["w"], np.float64), np.ascontiguousarray(st["lo"], np.float64),
+                np.ascontiguousarray(st["hi"], np.float64)]
+        _check(_lib.num_batch_create(ctypes.byref(h), self.count, _hptr(self.so), _hptr(self.lo),
+                                     *[_hptr(a) for a in arrs], ctypes.byref(self.params),
+                                     ctypes.c_void_p(stream) if stream else None))
+        self.h = h
+
+    def set_rho_schedules(self, decisions):
+        """decisions: int8 array (count, len)."""
+        d = np.ascontiguousarray(decisions, dtype=np.int8)
+        _check(_lib.num_batch_set_rho_schedules(self.h, _hptr(d) if d.size else None,
+                                                d.shape[1] if d.ndim == 2 else 0))
+
+    def solve(self, max_iters, eps_abs=-1.0):
+        it = np.zeros(self.count, dtype=np.int64)
+        stt = np.zeros(self.count, dtype=np.int32)
+        rc = _check(_lib.num_batch_solve(self.h, int(max_iters), float(eps_abs), _hptr(it),
+                                         _hptr(stt)))
+        return rc, it, stt
+
+    def get(self):
+        """Per-instance lists of x and prices, and an info dict per instance."""
+        x = np.empty(self.n)
+        p = np.empty(self.m)
+        info = np.zeros((self.count, NUM_INFO_LEN))
+        _check(_lib.num_batch_get(self.h, _hptr(x), _hptr(p), _hptr(info)))
+        xs = [x[self.so[i]:self.so[i + 1]] for i in range(self.count)]
+        ps = [p[self.lo[i]:self.lo[i + 1]] for i in range(self.count)]
+        infos = [{k: float(info[i, j]) for k, j in INFO.items()} for i in range(self.count)]
+        return xs, ps, infos
+
+    def kernel_times(self):
+        ms = np.zeros(2)
+        cnt = np.zeros(2, dtype=np.int64)
+        nk = ctypes.c_int32(0)
+        _check(_lib.num_batch_get_kernel_times(self.h, _hptr(ms), _hptr(cnt), 2, ctypes.byref(nk)))
+        return ms, cnt
+
+    def close(self):
+        if getattr(self, "h", None) is not None:
+            _lib.num_batch_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def torch_allocator():

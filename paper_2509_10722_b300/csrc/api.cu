@@ -314,13 +314,21 @@ std::string describe_bits(int bits) {
     add(pmp::VB_WEIGHT, "a weight is not finite and > 0");
     add(pmp::VB_UTYPE, "a utility type is not NUM_LOG or NUM_LINEAR");
     add(pmp::VB_BOX, "a box is not finite with lo <= hi (and hi > 0 for log utility)");
+    add(pmp::VB_BLOCKS, "a route uses a link of another instance of the batch");
     return s;
 }
+
+// Instances of a batch: host arrays of count + 1 offsets into the stacked numbering.
+struct BatchSpec {
+    int count;
+    const int64_t* stream_off;
+    const int64_t* link_off;
+};
 
 int create_impl(num_problem** out, int64_t n, int64_t m, const int64_t* route_ptr,
                 const int32_t* route_links, const double* c, const uint8_t* utype,
                 const double* w, const double* lo, const double* hi, const num_params* p,
-                void* cuda_stream, bool on_device) {
+                void* cuda_stream, bool on_device, const BatchSpec* batch = nullptr) {
     g_last_error.clear();
     if (!out) return fail(NUM_ERR_INVALID, "out is NULL");
     *out = nullptr;
@@ -447,6 +455,8 @@ int create_impl(num_problem** out, int64_t n, int64_t m, const int64_t* route_pt
         d_ut = (uint8_t*)A(N);
     }
     int* d_err = (int*)A(sizeof(int) * 2);
+    int64_t* d_soff = batch ? (int64_t*)A(8 * ((size_t)batch->count + 1)) : nullptr;
+    int64_t* d_loff = batch ? (int64_t*)A(8 * ((size_t)batch->count + 1)) : nullptr;
     unsigned long long* d_box = (unsigned long long*)A(sizeof(unsigned long long) * 4);
     pmp::Scratch s{};
     s.keys_a = (int*)A(4 * NNZ);
@@ -518,11 +528,23 @@ int create_impl(num_problem** out, int64_t n, int64_t m, const int64_t* route_pt
     CK(pmp::validate_inputs((int)n, (int)m, route_ptr, route_links, c, utype, w, lo, hi, d_err,
                             d_box, st),
        "validating the inputs");
+    if (batch) {
+        CK(cudaMemcpyAsync(d_soff, batch->stream_off, 8 * ((size_t)batch->count + 1),
+                           cudaMemcpyHostToDevice, st), "copy offsets");
+        CK(cudaMemcpyAsync(d_loff, batch->link_off, 8 * ((size_t)batch->count + 1),
+                           cudaMemcpyHostToDevice, st), "copy offsets");
+    }
     int err_bits = 0;
     unsigned long long box[4];
     CK(cudaMemcpyAsync(&err_bits, d_err, sizeof(int), cudaMemcpyDeviceToHost, st), "read flags");
     CK(cudaMemcpyAsync(box, d_box, sizeof(box), cudaMemcpyDeviceToHost, st), "read box");
     CK(cudaStreamSynchronize(st), "validation");
+    if (!err_bits && batch) {
+        CK(pmp::check_blocks(batch->count, d_soff, d_loff, n, route_ptr, route_links, d_err, st),
+           "checking the instance blocks");
+        CK(cudaMemcpyAsync(&err_bits, d_err, sizeof(int), cudaMemcpyDeviceToHost, st), "read flags");
+        CK(cudaStreamSynchronize(st), "validation");
+    }
     if (err_bits) {
         destroy_handle(h);
         return fail(NUM_ERR_INVALID, describe_bits(err_bits));
@@ -590,7 +612,7 @@ int create_impl(num_problem** out, int64_t n, int64_t m, const int64_t* route_pt
                     (void*)d_ut, (void*)d_err, (void*)d_box, (void*)s.keys_a, (void*)s.vals_a,
                     (void*)s.keys_b, (void*)s.vals_b, (void*)s.hist, (void*)s.scan_tmp,
                     (void*)d_ccount, (void*)d_coff, (void*)d_ctmp, (void*)d_rp2, (void*)d_rl2,
-                    (void*)d_lens, (void*)d_ptr32, (void*)d_ptmp})
+                    (void*)d_lens, (void*)d_ptr32, (void*)d_ptmp, (void*)d_soff, (void*)d_loff})
         dev_free(h, q);
 #undef CK
     *out = h;
@@ -892,5 +914,402 @@ const char* num_strerror(int code) {
 }
 
 const char* num_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"
+
+// ---- batches of independent instances ----------------------------------------------------------
+
+struct num_batch {
+    num_problem* p = nullptr;  // the stacked problem; owns every device array below
+    int count = 0;
+    std::vector<int64_t> soff, loff;
+    pmp::Ctl* ctls = nullptr;
+    pmp::Ctl* ctls_host = nullptr;  // pinned [count]
+    pmp::BatchGlobal* glob = nullptr;
+    pmp::BatchGlobal* glob_host = nullptr;  // pinned
+    int4 *sitems = nullptr, *litems = nullptr;
+    int nsitems = 0, nlitems = 0;
+    int *sitem_off = nullptr, *litem_off = nullptr;
+    double *part_s = nullptr, *part_l = nullptr, *part_e = nullptr;
+    double* hist = nullptr;
+    signed char* sched = nullptr;
+    int sched_stride = 0;
+    double* eps_scale = nullptr;
+    int grid_s = 0, grid_l = 0, grid_e = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    double kernel_ms[2] = {0.0, 0.0};
+    long long kernel_runs[2] = {0, 0};
+    std::vector<double> J;  // terminals nnz_i + m_i of each instance
+};
+
+namespace {
+
+constexpr int kBatchStreamItem = 2048;  // streams per work item
+constexpr int kBatchLinkItem = 256;     // links per work item
+
+template <typename T>
+pmp::BatchView<T> make_batch_view(const num_batch* b) {
+    pmp::BatchView<T> v;
+    std::memset(&v, 0, sizeof(v));
+    v.v = make_view<T>(b->p);
+    v.ctls = b->ctls;
+    v.glob = b->glob;
+    v.sitems = b->sitems;
+    v.litems = b->litems;
+    v.nsitems = b->nsitems;
+    v.nlitems = b->nlitems;
+    v.sitem_off = b->sitem_off;
+    v.litem_off = b->litem_off;
+    v.count = b->count;
+    v.part_s = b->part_s;
+    v.part_l = b->part_l;
+    v.hist = b->hist;
+    v.sched = b->sched;
+    v.sched_stride = b->sched_stride;
+    return v;
+}
+
+cudaError_t batch_run(num_batch* b, int count) {
+    num_problem* h = b->p;
+    const bool prof = h->prm.profile != 0;
+    if (prof) {
+        cudaError_t e = cudaEventRecordWithFlags(h->evs[0], h->stream, cudaEventRecordExternal);
+        if (e != cudaSuccess) return e;
+    }
+    for (int i = 0; i < count; ++i) {
+        cudaEvent_t* ev = prof ? h->evs.data() + 1 + (size_t)i * 2 : nullptr;
+        cudaError_t e = h->prec == NUM_FUSED_FP32
+                            ? pmp::batch_iteration<float>(make_batch_view<float>(b), b->grid_s,
+                                                          b->grid_l, h->stream, ev)
+                            : pmp::batch_iteration<double>(make_batch_view<double>(b), b->grid_s,
+                                                           b->grid_l, h->stream, ev);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+void batch_destroy(num_batch* b) {
+    if (!b) return;
+    if (b->p && b->p->stream) cudaStreamSynchronize(b->p->stream);
+    if (b->graph_exec) cudaGraphExecDestroy(b->graph_exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->ctls_host) cudaFreeHost(b->ctls_host);
+    if (b->glob_host) cudaFreeHost(b->glob_host);
+    destroy_handle(b->p);
+    delete b;
+}
+
+int batch_reset_all(num_batch* b) {
+    const num_params& q = b->p->prm;
+    cudaError_t e = pmp::batch_reset(b->ctls, b->glob, b->count, q.rho0, q.alpha, q.mu, q.gamma,
+                                     q.rho_period, q.history, 0, b->p->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "resetting the instances");
+    return NUM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int num_batch_create(num_batch** out, int32_t count, const int64_t* stream_off,
+                     const int64_t* link_off, const int64_t* route_ptr,
+                     const int32_t* route_links, const double* c, const uint8_t* utype,
+                     const double* w, const double* lo, const double* hi, const num_params* p,
+                     void* cuda_stream) {
+    g_last_error.clear();
+    if (!out) return fail(NUM_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    if (count < 1 || !stream_off || !link_off || !route_ptr)
+        return fail(NUM_ERR_INVALID, "count must be >= 1 and the offsets non-NULL");
+    if (stream_off[0] != 0 || link_off[0] != 0)
+        return fail(NUM_ERR_INVALID, "stream_off[0] and link_off[0] must be 0");
+    for (int i = 0; i < count; ++i)
+        if (stream_off[i + 1] <= stream_off[i] || link_off[i + 1] <= link_off[i])
+            return fail(NUM_ERR_INVALID, "every instance needs >= 1 stream and >= 1 link");
+    num_params prm;
+    if (p)
+        prm = *p;
+    else
+        num_default_params(&prm);
+    if (prm.precision == NUM_PLAIN_FP64 || prm.schedule == NUM_SCHEDULE_TILES)
+        return fail(NUM_ERR_INVALID, "batches run the fused row kernels (FP32 or FP64)");
+    const int64_t n = stream_off[count], m = link_off[count];
+    if (n > INT32_MAX - 1 || m > INT32_MAX - 1)
+        return fail(NUM_ERR_INVALID, "total n and m must be < 2^31 - 1");
+    num_batch* b = new (std::nothrow) num_batch();
+    if (!b) return fail(NUM_ERR_OOM, "host allocation failed");
+    b->count = count;
+    b->soff.assign(stream_off, stream_off + count + 1);
+    b->loff.assign(link_off, link_off + count + 1);
+    BatchSpec spec{count, stream_off, link_off};
+    int rc = create_impl(&b->p, n, m, route_ptr, route_links, c, utype, w, lo, hi, &prm,
+                         cuda_stream, false, &spec);
+    if (rc != NUM_OK) {
+        delete b;
+        return rc;
+    }
+    num_problem* h = b->p;
+    // work items (instance, first row, end row): streams keep their instance's range after
+    // the first-link ordering because an instance's links are a contiguous id range
+    std::vector<int4> si, li;
+    std::vector<int> so(count + 1), lo_(count + 1);
+    std::vector<double> scale(count);
+    for (int i = 0; i < count; ++i) {
+        so[i] = (int)si.size();
+        for (int64_t r = stream_off[i]; r < stream_off[i + 1]; r += kBatchStreamItem)
+            si.push_back(make_int4(i, (int)r, (int)std::min<int64_t>(r + kBatchStreamItem,
+                                                                     stream_off[i + 1]), 0));
+        lo_[i] = (int)li.size();
+        for (int64_t r = link_off[i]; r < link_off[i + 1]; r += kBatchLinkItem)
+            li.push_back(make_int4(i, (int)r, (int)std::min<int64_t>(r + kBatchLinkItem,
+                                                                     link_off[i + 1]), 0));
+        const int64_t nnz_i = route_ptr[stream_off[i + 1]] - route_ptr[stream_off[i]];
+        b->J.push_back((double)(nnz_i + link_off[i + 1] - link_off[i]));
+        scale[i] = std::sqrt(b->J.back());
+    }
+    so[count] = (int)si.size();
+    lo_[count] = (int)li.size();
+    b->nsitems = (int)si.size();
+    b->nlitems = (int)li.size();
+    const int H = prm.history > 0 ? prm.history : 1;
+    b->ctls = (pmp::Ctl*)dev_alloc(h, sizeof(pmp::Ctl) * count);
+    b->glob = (pmp::BatchGlobal*)dev_alloc(h, sizeof(pmp::BatchGlobal));
+    b->sitems = (int4*)dev_alloc(h, sizeof(int4) * si.size());
+    b->litems = (int4*)dev_alloc(h, sizeof(int4) * li.size());
+    b->sitem_off = (int*)dev_alloc(h, sizeof(int) * (count + 1));
+    b->litem_off = (int*)dev_alloc(h, sizeof(int) * (count + 1));
+    b->part_s = (double*)dev_alloc(h, sizeof(double) * si.size());
+    b->part_l = (double*)dev_alloc(h, sizeof(double) * 2 * li.size());
+    b->part_e = (double*)dev_alloc(h, sizeof(double) * si.size());
+    b->hist = (double*)dev_alloc(h, sizeof(double) * 3 * (size_t)H * count);
+    b->eps_scale = (double*)dev_alloc(h, sizeof(double) * count);
+    if (!b->ctls || !b->glob || !b->sitems || !b->litems || !b->sitem_off || !b->litem_off ||
+        !b->part_s || !b->part_l || !b->part_e || !b->hist || !b->eps_scale) {
+        batch_destroy(b);
+        return fail(NUM_ERR_OOM, "device allocation failed");
+    }
+    cudaStream_t st = h->stream;
+    cudaError_t e;
+#define BK(call, what)                  \
+    do {                                \
+        e = (call);                     \
+        if (e != cudaSuccess) {         \
+            batch_destroy(b);           \
+            return cuda_fail(e, what);  \
+        }                               \
+    } while (0)
+    BK(cudaHostAlloc((void**)&b->ctls_host, sizeof(pmp::Ctl) * count, cudaHostAllocDefault),
+       "cudaHostAlloc");
+    BK(cudaHostAlloc((void**)&b->glob_host, sizeof(pmp::BatchGlobal), cudaHostAllocDefault),
+       "cudaHostAlloc");
+    BK(cudaMemcpyAsync(b->sitems, si.data(), sizeof(int4) * si.size(), cudaMemcpyHostToDevice, st),
+       "copy items");
+    BK(cudaMemcpyAsync(b->litems, li.data(), sizeof(int4) * li.size(), cudaMemcpyHostToDevice, st),
+       "copy items");
+    BK(cudaMemcpyAsync(b->sitem_off, so.data(), sizeof(int) * (count + 1), cudaMemcpyHostToDevice,
+                       st), "copy items");
+    BK(cudaMemcpyAsync(b->litem_off, lo_.data(), sizeof(int) * (count + 1),
+                       cudaMemcpyHostToDevice, st), "copy items");
+    BK(cudaMemcpyAsync(b->eps_scale, scale.data(), sizeof(double) * count, cudaMemcpyHostToDevice,
+                       st), "copy scales");
+    BK(cudaMemsetAsync(b->hist, 0, sizeof(double) * 3 * (size_t)H * count, st), "memset");
+    BK(pmp::batch_grids(h->prec == NUM_FUSED_FP32 ? 0 : 1, b->nsitems, b->nlitems, &b->grid_s,
+                        &b->grid_l, &b->grid_e), "sizing the batch grids");
+    rc = batch_reset_all(b);
+    if (rc != NUM_OK) {
+        batch_destroy(b);
+        return rc;
+    }
+    BK(cudaStreamSynchronize(st), "batch setup");
+#undef BK
+    *out = b;
+    return NUM_OK;
+}
+
+int num_batch_set_rho_schedules(num_batch* b, const int8_t* decisions, int64_t len) {
+    g_last_error.clear();
+    if (!b) return fail(NUM_ERR_INVALID, "batch is NULL");
+    if (len < 0 || len > INT32_MAX || (len > 0 && !decisions))
+        return fail(NUM_ERR_INVALID, "bad schedule");
+    for (int64_t i = 0; i < len * b->count; ++i)
+        if (decisions[i] < -1 || decisions[i] > 1)
+            return fail(NUM_ERR_INVALID, "schedule entries must be -1, 0 or +1");
+    num_problem* h = b->p;
+    cudaError_t e = order_after_legacy(h);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "ordering");
+    if (b->sched) {
+        dev_free(h, b->sched);
+        b->sched = nullptr;
+    }
+    b->sched_stride = 0;
+    if (len > 0) {
+        b->sched = (signed char*)dev_alloc(h, (size_t)len * b->count);
+        if (!b->sched) return fail(NUM_ERR_OOM, "device allocation failed");
+        e = cudaMemcpyAsync(b->sched, decisions, (size_t)len * b->count, cudaMemcpyHostToDevice,
+                            h->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "copy schedule");
+        b->sched_stride = (int)len;
+    }
+    if (b->graph_exec) {
+        cudaGraphExecDestroy(b->graph_exec);
+        b->graph_exec = nullptr;
+    }
+    if (b->graph) {
+        cudaGraphDestroy(b->graph);
+        b->graph = nullptr;
+    }
+    // every instance: sched_len = len (the rest of its control block is kept)
+    e = cudaMemcpyAsync(b->ctls_host, b->ctls, sizeof(pmp::Ctl) * b->count,
+                        cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "schedule");
+    for (int i = 0; i < b->count; ++i) b->ctls_host[i].sched_len = (int)len;
+    e = cudaMemcpyAsync(b->ctls, b->ctls_host, sizeof(pmp::Ctl) * b->count,
+                        cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    return finish_cuda(e, "schedule");
+}
+
+int num_batch_solve(num_batch* b, int64_t max_iters, double eps_abs, int64_t* iters_done,
+                    int32_t* status) {
+    g_last_error.clear();
+    if (!b) return fail(NUM_ERR_INVALID, "batch is NULL");
+    if (max_iters < 0) return fail(NUM_ERR_INVALID, "max_iters must be >= 0");
+    if (std::isnan(eps_abs)) return fail(NUM_ERR_INVALID, "eps_abs is NaN");
+    num_problem* h = b->p;
+    cudaStream_t st = h->stream;
+    cudaError_t e = order_after_legacy(h);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->ctls_host, b->ctls, sizeof(pmp::Ctl) * b->count,
+                            cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "reading the control blocks");
+    std::vector<long long> k0(b->count);
+    for (int i = 0; i < b->count; ++i) k0[i] = b->ctls_host[i].k;
+    const double eps = eps_abs > 0.0 ? eps_abs : (eps_abs < 0.0 ? h->prm.eps_abs : 0.0);
+    e = pmp::batch_arm(b->ctls, b->glob, b->count, max_iters, eps, b->eps_scale, st);
+    if (e != cudaSuccess) return cuda_fail(e, "arming the instances");
+    const int K = h->prm.check_every;
+    if (max_iters > 0) {
+        if (h->prm.use_graph && !b->graph_exec) {
+            e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
+            cudaError_t e2 = batch_run(b, K);
+            e = cudaStreamEndCapture(st, &b->graph);
+            if (e2 != cudaSuccess) return cuda_fail(e2, "capturing the batch graph");
+            if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+            e = cudaGraphInstantiate(&b->graph_exec, b->graph, 0);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+        }
+        const long long max_launches = (max_iters + K - 1) / K + 1;
+        long long done_prev = 0;
+        for (long long it = 0;; ++it) {
+            if (it >= max_launches) return fail(NUM_ERR_STATE, "the iteration limit was not honoured");
+            e = h->prm.use_graph ? cudaGraphLaunch(b->graph_exec, st) : batch_run(b, K);
+            if (e != cudaSuccess) return cuda_fail(e, "launching iterations");
+            pmp::note_launches((long long)K * 2);
+            e = cudaMemcpyAsync(b->glob_host, b->glob, sizeof(pmp::BatchGlobal),
+                                cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) return cuda_fail(e, "iterations");
+            if (h->prm.profile) {
+                // kernels of iterations after every instance stopped exit at once; the
+                // batch's slowest instance decides how many did work
+                e = cudaMemcpyAsync(b->ctls_host, b->ctls, sizeof(pmp::Ctl) * b->count,
+                                    cudaMemcpyDeviceToHost, st);
+                if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+                if (e != cudaSuccess) return cuda_fail(e, "iterations");
+                long long most = 0;
+                for (int i = 0; i < b->count; ++i)
+                    most = std::max(most, b->ctls_host[i].k - k0[i]);
+                const long long ran = most - done_prev;
+                done_prev = most;
+                for (long long i = 0; i < ran; ++i)
+                    for (int q = 0; q < 2; ++q) {
+                        float ms = 0.f;
+                        e = cudaEventElapsedTime(&ms, h->evs[i * 2 + q], h->evs[i * 2 + q + 1]);
+                        if (e != cudaSuccess) return cuda_fail(e, "reading kernel times");
+                        b->kernel_ms[q] += ms;
+                        b->kernel_runs[q] += 1;
+                    }
+            }
+            if (b->glob_host->running == 0) break;
+        }
+    }
+    e = cudaMemcpyAsync(b->ctls_host, b->ctls, sizeof(pmp::Ctl) * b->count,
+                        cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "reading the control blocks");
+    int rc = NUM_OK;
+    for (int i = 0; i < b->count; ++i) {
+        const pmp::Ctl& c = b->ctls_host[i];
+        if (iters_done) iters_done[i] = c.k - k0[i];
+        const int stt = max_iters == 0 ? (int)pmp::LIMIT : c.stop;
+        if (status) status[i] = stt == pmp::CONVERGED ? NUM_OK
+                                : stt == pmp::NONFINITE ? NUM_ERR_NUMERIC : NUM_NOT_CONVERGED;
+        if (stt == pmp::NONFINITE) rc = NUM_ERR_NUMERIC;
+        else if (stt != pmp::CONVERGED && rc == NUM_OK) rc = NUM_NOT_CONVERGED;
+    }
+    if (rc == NUM_ERR_NUMERIC) return fail(rc, "a residual of some instance became non-finite");
+    return rc;
+}
+
+int num_batch_get(const num_batch* bc, double* x, double* prices, double* info) {
+    g_last_error.clear();
+    if (!bc) return fail(NUM_ERR_INVALID, "batch is NULL");
+    num_batch* b = const_cast<num_batch*>(bc);
+    num_problem* h = b->p;
+    cudaStream_t st = h->stream;
+    cudaError_t e = order_after_legacy(h);
+    if (e != cudaSuccess) return cuda_fail(e, "ordering");
+    double* xo = x ? h->x64 : nullptr;
+    double* yo = prices ? h->y64 : nullptr;
+    e = h->prec == NUM_FUSED_FP32
+            ? pmp::batch_export<float>(make_batch_view<float>(b), b->grid_e, xo, yo, b->part_e, st)
+            : pmp::batch_export<double>(make_batch_view<double>(b), b->grid_e, xo, yo, b->part_e,
+                                        st);
+    if (e != cudaSuccess) return cuda_fail(e, "exporting the solutions");
+    if (x) e = cudaMemcpyAsync(x, h->x64, 8 * (size_t)h->n, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && prices)
+        e = cudaMemcpyAsync(prices, h->y64, 8 * (size_t)h->m, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->ctls_host, b->ctls, sizeof(pmp::Ctl) * b->count,
+                            cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "reading the results");
+    if (info) {
+        for (int i = 0; i < b->count; ++i) {
+            const pmp::Ctl& c = b->ctls_host[i];
+            double* o = info + (size_t)i * NUM_INFO_LEN;
+            o[NUM_INFO_PRIMAL] = c.rnorm;
+            o[NUM_INFO_DUAL] = c.snorm;
+            o[NUM_INFO_EPS_TOL] = c.eps_tol;
+            o[NUM_INFO_RHO] = c.rho;
+            o[NUM_INFO_OBJECTIVE] = c.objective;
+            o[NUM_INFO_ITERS] = (double)c.k;
+            o[NUM_INFO_STATUS] = (double)c.stop;
+            o[NUM_INFO_J] = b->J[i];
+        }
+    }
+    return NUM_OK;
+}
+
+int num_batch_get_kernel_times(const num_batch* b, double* ms, int64_t* launches,
+                               int32_t max_kernels, int32_t* nkernels) {
+    g_last_error.clear();
+    if (!b) return fail(NUM_ERR_INVALID, "batch is NULL");
+    if (max_kernels < 0 || (max_kernels > 0 && (!ms || !launches)))
+        return fail(NUM_ERR_INVALID, "bad buffers");
+    if (nkernels) *nkernels = 2;
+    for (int q = 0; q < 2 && q < max_kernels; ++q) {
+        ms[q] = b->kernel_ms[q];
+        launches[q] = b->kernel_runs[q];
+    }
+    return NUM_OK;
+}
+
+void num_batch_destroy(num_batch* b) { batch_destroy(b); }
 
 }  // extern "C"

@@ -1,0 +1,305 @@
+// Batched PMP: many independent NUM instances of uneven sizes solved together.
+//
+// The instances are stacked block-diagonally in one global numbering (instance i owns a
+// contiguous range of streams and of links), so one CSC / CSR pair, one state layout and
+// the same per-stream / per-link epilogues serve all of them.  What is per instance: the
+// penalty rho, the iteration count, the stopping test and rho rule (Sec. III-F, III-G),
+// i.e. one control block each.  Two kernels per iteration for the whole batch:
+//   - a list of work items (instance, first row, end row) that never cross an instance;
+//     a block takes an item, runs the rows of it (a thread per stream / 8 lanes per link,
+//     exactly the row-kernel arithmetic) unless that instance has stopped, and writes the
+//     item's residual partial sums to the item's own slot;
+//   - the last block of the link kernel finishes the iteration of every running instance
+//     (one thread per instance: FP64 sums of its item slots in item order, norms, stopping
+//     test, rho), and counts the instances still running (the host stops replaying when
+//     none is).
+// No block waits on another; sums are in a fixed order, so runs are deterministic.
+#include <cooperative_groups.h>
+#include <cuda_runtime.h>
+
+#include "pmp_device.cuh"
+#include "pmp_internal.cuh"
+#include "pmp_rows.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace pmp {
+
+namespace {
+
+constexpr int kTh = 256;
+constexpr int kWarps = kTh / 32;
+constexpr int kGroup = 8;
+
+template <typename T>
+__global__ void __launch_bounds__(kTh) k_stream_batch(BatchView<T> b) {
+    using V = typename Pair<T>::type;
+    __shared__ double red[kWarps];
+    if (b.glob->running == 0) return;
+    const View<T>& v = b.v;
+    for (int it = blockIdx.x; it < b.nsitems; it += gridDim.x) {
+        const int4 item = __ldg(b.sitems + it);
+        const Ctl* c = b.ctls + item.x;
+        if (c->stop) continue;  // block-uniform
+        const T alpha = (T)c->alpha;
+        const T inv_rho = (T)(1.0 / c->rho);
+        Acc<T> acc;
+        for (int j = item.y + threadIdx.x; j < item.z; j += kTh) {
+            const int p = __ldg(v.col_ptr + j), pn = __ldg(v.col_ptr + j + 1);
+            const T xo = v.x[j], Zo = v.Z[j], wt = __ldg(v.wt + j);
+            const T lo = v.box_uniform ? v.lo_u : __ldg(v.lo + j);
+            const T hi = v.box_uniform ? v.hi_u : __ldg(v.hi + j);
+            const V sum = route_sum<T>(v.row_idx, v.pby, p, pn);
+            stream_epilogue(v, j, sum, (T)(pn - p), xo, Zo, wt, lo, hi, alpha, inv_rho, acc);
+        }
+        const double s = block_sum(acc.value(), red);
+        if (threadIdx.x == 0) b.part_s[it] = s;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kTh) k_link_batch(BatchView<T> b) {
+    __shared__ double red[kWarps];
+    __shared__ int last;
+    if (b.glob->running == 0) return;
+    const View<T>& v = b.v;
+    auto g = cg::tiled_partition<kGroup>(cg::this_thread_block());
+    const bool leader = g.thread_rank() == 0;
+    constexpr int kGroups = kTh / kGroup;
+    for (int it = blockIdx.x; it < b.nlitems; it += gridDim.x) {
+        const int4 item = __ldg(b.litems + it);
+        const Ctl* c = b.ctls + item.x;
+        if (c->stop) continue;  // block-uniform
+        const T alpha = (T)c->alpha, rho = (T)c->rho, inv_rho = (T)(1.0 / c->rho);
+        Acc<T> r2, s2;
+        for (int l = item.y + (int)(threadIdx.x / kGroup); l < item.z; l += kGroups) {
+            const int p0 = __ldg(v.row_ptr + l), p1 = __ldg(v.row_ptr + l + 1);
+            LinkState<T> st;
+            if (leader) st = load_link(v, l);
+            const T s = group_gather_sum<kGroup>(g, v.col_idx, v.x, p0, p1);
+            if (leader) link_epilogue(v, l, st, s, p1 - p0, alpha, rho, inv_rho, r2, s2);
+        }
+        const double R2 = block_sum(r2.value(), red);
+        const double S2 = block_sum(s2.value(), red);
+        if (threadIdx.x == 0) {
+            b.part_l[2 * it] = R2;
+            b.part_l[2 * it + 1] = S2;
+        }
+    }
+    // the last block to get here finishes the iteration of every running instance
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(&b.glob->ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    int running = 0;
+    for (int i = threadIdx.x; i < b.count; i += kTh) {
+        Ctl* c = b.ctls + i;
+        if (c->stop) continue;
+        double ss = 0.0, rr = 0.0, sl = 0.0;
+        for (int q = b.sitem_off[i]; q < b.sitem_off[i + 1]; ++q) ss += __ldcg(b.part_s + q);
+        for (int q = b.litem_off[i]; q < b.litem_off[i + 1]; ++q) {
+            rr += __ldcg(b.part_l + 2 * q);
+            sl += __ldcg(b.part_l + 2 * q + 1);
+        }
+        finalize_iteration(c, rr, ss + sl, b.hist + (size_t)i * 3 * (c->hist_len > 0 ? c->hist_len : 1),
+                           b.sched + (size_t)i * b.sched_stride);
+        running += c->stop == RUNNING;
+    }
+    const int total = __syncthreads_count(running > 0) ? 1 : 0;
+    if (threadIdx.x == 0) {
+        b.glob->ticket = 0;
+        b.glob->running = total;
+    }
+}
+
+// x and prices to FP64 in the caller's order, and sum U_j(x_j) per instance (one block per
+// stream item, FP64, then the last block sums each instance's items in item order).
+template <typename T>
+__global__ void __launch_bounds__(kTh) k_export_batch(BatchView<T> b, double* x_out,
+                                                      double* y_out, double* part) {
+    __shared__ double red[kWarps];
+    __shared__ int last;
+    const View<T>& v = b.v;
+    for (int it = blockIdx.x; it < b.nsitems; it += gridDim.x) {
+        const int4 item = __ldg(b.sitems + it);
+        double obj = 0.0;
+        for (int j = item.y + threadIdx.x; j < item.z; j += kTh) {
+            const double xj = (double)v.x[j];
+            const double wt = (double)v.wt[j];
+            if (x_out) x_out[v.perm ? v.perm[j] : j] = xj;
+            obj += wt > 0.0 ? wt * log(xj) : -wt * xj;
+        }
+        const double s = block_sum(obj, red);
+        if (threadIdx.x == 0) part[it] = s;
+    }
+    if (y_out)
+        for (int l = blockIdx.x * kTh + threadIdx.x; l < v.m; l += gridDim.x * kTh)
+            y_out[l] = (double)v.pby[l].y;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(&b.glob->ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    for (int i = threadIdx.x; i < b.count; i += kTh) {
+        double s = 0.0;
+        for (int q = b.sitem_off[i]; q < b.sitem_off[i + 1]; ++q) s += __ldcg(part + q);
+        b.ctls[i].objective = s;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) b.glob->ticket = 0;
+}
+
+// Every route of instance i must use only links of instance i (block-diagonal R).
+__global__ void k_check_blocks(int count, const int64_t* __restrict__ stream_off,
+                               const int64_t* __restrict__ link_off,
+                               const int64_t* __restrict__ route_ptr,
+                               const int* __restrict__ route_links, int* err) {
+    const long long n = stream_off[count];
+    bool bad = false;
+    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n;
+         j += (long long)gridDim.x * blockDim.x) {
+        int lo = 0, hi = count - 1;  // instance of stream j
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (stream_off[mid] <= j)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        const long long l0 = link_off[lo], l1 = link_off[lo + 1];
+        for (long long e = route_ptr[j]; e < route_ptr[j + 1]; ++e) {
+            const int l = route_links[e];
+            bad |= l < l0 || l >= l1;
+        }
+    }
+    if (bad) atomicOr(err, VB_BLOCKS);
+}
+
+__global__ void k_batch_arm(Ctl* ctls, BatchGlobal* glob, int count, long long max_iters,
+                            double eps_abs, const double* eps_scale) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
+        Ctl* c = ctls + i;
+        c->k_limit = c->k + max_iters;
+        c->eps_tol = eps_abs > 0.0 ? eps_abs * eps_scale[i] : 0.0;
+        c->stop = RUNNING;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        glob->running = count > 0 && max_iters > 0 ? 1 : 0;
+        glob->ticket = 0;
+    }
+}
+
+__global__ void k_batch_reset(Ctl* ctls, BatchGlobal* glob, int count, double rho0,
+                              double alpha, double mu, double gamma, int period, int hist_len,
+                              int sched_len) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
+        Ctl c;
+        memset(&c, 0, sizeof(c));
+        c.rho = rho0;
+        c.alpha = alpha;
+        c.mu = mu;
+        c.gamma = gamma;
+        c.period = period;
+        c.hist_len = hist_len;
+        c.sched_len = sched_len;
+        ctls[i] = c;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        glob->running = 0;
+        glob->ticket = 0;
+    }
+}
+
+template <typename T>
+cudaError_t batch_occupancy(int* occ_s, int* occ_l, int* occ_e) {
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ_s, k_stream_batch<T>, kTh, 0);
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ_l, k_link_batch<T>, kTh, 0);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ_e, k_export_batch<T>, kTh, 0);
+}
+
+int blocks_for(long long count) {
+    long long b = (count + kTh - 1) / kTh;
+    return (int)(b < 1 ? 1 : (b > 4096 ? 4096 : b));
+}
+
+}  // namespace
+
+cudaError_t batch_grids(int precision, int nsitems, int nlitems, int* grid_s, int* grid_l,
+                        int* grid_e) {
+    int dev = 0, sms = 0, os = 0, ol = 0, oe = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    e = precision == 0 ? batch_occupancy<float>(&os, &ol, &oe) : batch_occupancy<double>(&os, &ol, &oe);
+    if (e != cudaSuccess) return e;
+    if (os < 1 || ol < 1 || oe < 1) return cudaErrorInvalidConfiguration;
+    const long long gs = (long long)os * sms, gl = (long long)ol * sms, ge = (long long)oe * sms;
+    *grid_s = (int)(gs < nsitems ? gs : nsitems);
+    *grid_l = (int)(gl < nlitems ? gl : nlitems);
+    *grid_e = (int)(ge < nsitems ? ge : nsitems);
+    return cudaSuccess;
+}
+
+cudaError_t check_blocks(int count, const int64_t* stream_off, const int64_t* link_off,
+                         long long n, const int64_t* route_ptr, const int* route_links, int* err,
+                         cudaStream_t st) {
+    k_check_blocks<<<blocks_for(n), kTh, 0, st>>>(count, stream_off, link_off, route_ptr,
+                                                  route_links, err);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t batch_iteration(const BatchView<T>& b, int grid_s, int grid_l, cudaStream_t st,
+                            cudaEvent_t* evs) {
+    k_stream_batch<T><<<grid_s, kTh, 0, st>>>(b);
+    if (evs) cudaEventRecordWithFlags(evs[0], st, cudaEventRecordExternal);
+    k_link_batch<T><<<grid_l, kTh, 0, st>>>(b);
+    if (evs) cudaEventRecordWithFlags(evs[1], st, cudaEventRecordExternal);
+    return cudaGetLastError();
+}
+template cudaError_t batch_iteration<float>(const BatchView<float>&, int, int, cudaStream_t,
+                                            cudaEvent_t*);
+template cudaError_t batch_iteration<double>(const BatchView<double>&, int, int, cudaStream_t,
+                                             cudaEvent_t*);
+
+template <typename T>
+cudaError_t batch_export(const BatchView<T>& b, int grid_e, double* x_out, double* y_out,
+                         double* part, cudaStream_t st) {
+    k_export_batch<T><<<grid_e, kTh, 0, st>>>(b, x_out, y_out, part);
+    note_launches(1);
+    return cudaGetLastError();
+}
+template cudaError_t batch_export<float>(const BatchView<float>&, int, double*, double*, double*,
+                                         cudaStream_t);
+template cudaError_t batch_export<double>(const BatchView<double>&, int, double*, double*, double*,
+                                          cudaStream_t);
+
+cudaError_t batch_arm(Ctl* ctls, BatchGlobal* glob, int count, long long max_iters,
+                      double eps_abs, const double* eps_scale, cudaStream_t st) {
+    k_batch_arm<<<blocks_for(count), kTh, 0, st>>>(ctls, glob, count, max_iters, eps_abs,
+                                                   eps_scale);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t batch_reset(Ctl* ctls, BatchGlobal* glob, int count, double rho0, double alpha,
+                        double mu, double gamma, int period, int hist_len, int sched_len,
+                        cudaStream_t st) {
+    k_batch_reset<<<blocks_for(count), kTh, 0, st>>>(ctls, glob, count, rho0, alpha, mu, gamma,
+                                                     period, hist_len, sched_len);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+}  // namespace pmp

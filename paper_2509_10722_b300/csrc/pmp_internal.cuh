@@ -117,6 +117,49 @@ cudaError_t plain_iteration(const View<double>& v, int plain_blocks, cudaStream_
                             cudaEvent_t* evs);
 constexpr int kFusedKernelsPerIter = 2;
 
+// ---- batched kernels (batch.cu) ---------------------------------------------------------------
+struct BatchGlobal {
+    unsigned int ticket;  // last-block-done counter
+    int running;          // 1 while any instance is running
+};
+
+// Work items are (instance, first row, end row, 0); item ranges of instance i are
+// [sitem_off[i], sitem_off[i+1]) and [litem_off[i], litem_off[i+1]).
+template <typename T>
+struct BatchView {
+    View<T> v;  // the stacked (block-diagonal) problem's arrays
+    Ctl* ctls;  // one control block per instance
+    BatchGlobal* glob;
+    const int4* sitems;
+    const int4* litems;
+    int nsitems, nlitems;
+    const int* sitem_off;
+    const int* litem_off;
+    int count;
+    double* part_s;  // [nsitems]
+    double* part_l;  // [2 nlitems]
+    double* hist;    // [count][max(hist_len, 1)][3]
+    const signed char* sched;  // [count][sched_stride]
+    int sched_stride;
+};
+
+cudaError_t batch_grids(int precision, int nsitems, int nlitems, int* grid_s, int* grid_l,
+                        int* grid_e);
+cudaError_t check_blocks(int count, const int64_t* stream_off, const int64_t* link_off,
+                         long long n, const int64_t* route_ptr, const int* route_links, int* err,
+                         cudaStream_t st);
+template <typename T>
+cudaError_t batch_iteration(const BatchView<T>& b, int grid_s, int grid_l, cudaStream_t st,
+                            cudaEvent_t* evs);
+template <typename T>
+cudaError_t batch_export(const BatchView<T>& b, int grid_e, double* x_out, double* y_out,
+                         double* part, cudaStream_t st);
+cudaError_t batch_arm(Ctl* ctls, BatchGlobal* glob, int count, long long max_iters,
+                      double eps_abs, const double* eps_scale, cudaStream_t st);
+cudaError_t batch_reset(Ctl* ctls, BatchGlobal* glob, int count, double rho0, double alpha,
+                        double mu, double gamma, int period, int hist_len, int sched_len,
+                        cudaStream_t st);
+
 // ---- row kernels (rows.cu) ------------------------------------------------------------------
 cudaError_t rows_grids(int precision, int n, int m, int nchunks, int* grid_s, int* grid_l);
 template <typename T>
@@ -151,6 +194,7 @@ enum ValidationBits {
     VB_WEIGHT = 16,   // w not finite or <= 0
     VB_UTYPE = 32,    // utility type not 0 or 1
     VB_BOX = 64,      // lo / hi not finite, lo > hi, or hi <= 0 for a log stream
+    VB_BLOCKS = 128,  // batch: a route uses a link of another instance
 };
 
 struct Scratch {  // transient buffers of the operator build, caller-allocated

@@ -1,0 +1,127 @@
+// Device pieces shared by the row kernels (rows.cu) and the batched kernels (batch.cu):
+// the per-stream and per-link epilogues of one PMP iteration and the group gather-sum.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "pmp_device.cuh"
+#include "pmp_internal.cuh"
+
+namespace pmp {
+
+// Per-thread residual partial sum: compensated (Neumaier) in FP32, plain in FP64.
+template <typename T>
+struct Acc {
+    T s = T(0), c = T(0);
+    __device__ __forceinline__ void add(T v) {
+        const T t = s + v;
+        c += (fabs(s) >= fabs(v)) ? ((s - t) + v) : ((v - t) + s);
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+template <>
+struct Acc<double> {
+    double s = 0.0;
+    __device__ __forceinline__ void add(double v) { s += v; }
+    __device__ __forceinline__ double value() const { return s; }
+};
+
+// Sum of (pbar, y) over the route entries [p, pn) of one stream, in entry order, with
+// four gathers in flight.
+template <typename T>
+__device__ __forceinline__ typename Pair<T>::type route_sum(const int* __restrict__ row_idx,
+                                                           const typename Pair<T>::type* __restrict__ pby,
+                                                           int p, int pn) {
+    using V = typename Pair<T>::type;
+    V sum = vzero(V());
+    int e = p;
+    for (; e + 4 <= pn; e += 4) {
+        const int l0 = __ldg(row_idx + e), l1 = __ldg(row_idx + e + 1);
+        const int l2 = __ldg(row_idx + e + 2), l3 = __ldg(row_idx + e + 3);
+        const V g0 = __ldg(pby + l0), g1 = __ldg(pby + l1);
+        const V g2 = __ldg(pby + l2), g3 = __ldg(pby + l3);
+        sum = vadd(sum, g0);
+        sum = vadd(sum, g1);
+        sum = vadd(sum, g2);
+        sum = vadd(sum, g3);
+    }
+    for (; e < pn; ++e) sum = vadd(sum, __ldg(pby + __ldg(row_idx + e)));
+    return sum;
+}
+
+// ---- stream kernel -------------------------------------------------------------------------------
+
+template <typename T>
+__device__ __forceinline__ void stream_epilogue(const View<T>& v, int j, typename Pair<T>::type sum,
+                                                T L, T xo, T Zo, T wt, T lo, T hi, T alpha,
+                                                T inv_rho, Acc<T>& acc) {
+    const T Zn = alpha * L * xo + (T(1) - alpha) * Zo - alpha * sum.x;
+    const T S = Zn - sum.y * inv_rho;
+    const T xn = stream_prox<T>(S, L, wt, inv_rho, lo, hi);
+    v.Z[j] = Zn;
+    v.x[j] = xn;
+    const T dx = xn - xo;
+    acc.add(L * dx * dx);
+}
+
+template <typename T>
+struct LinkState {
+    typename Pair<T>::type py;
+    T Rxo, pso, zso, cl;
+};
+
+template <typename T>
+__device__ __forceinline__ LinkState<T> load_link(const View<T>& v, int l) {
+    LinkState<T> s;
+    s.py = v.pby[l];
+    s.Rxo = v.Rx[l];
+    s.pso = v.ps[l];
+    s.zso = v.zs[l];
+    s.cl = __ldg(v.c + l);
+    return s;
+}
+
+// Link epilogue (slack prox, average, z and price updates) and its residual terms.
+template <typename T>
+__device__ __forceinline__ void link_epilogue(const View<T>& v, int l, const LinkState<T>& st,
+                                              T Rxn, int deg, T alpha, T rho, T inv_rho,
+                                              Acc<T>& r2, Acc<T>& s2) {
+    using T2 = typename Pair<T>::type;
+    const T pbo = st.py.x, y = st.py.y;
+    T psn = st.zso - y * inv_rho;
+    psn = psn < -st.cl ? -st.cl : psn;
+    const T degf = (T)deg;
+    const T pbn = (Rxn + psn) / (degf + T(1));
+    T2 out;
+    out.x = pbn;
+    out.y = y + alpha * rho * pbn;
+    v.pby[l] = out;
+    v.zs[l] = alpha * (psn - pbn) + (T(1) - alpha) * st.zso;
+    v.Rx[l] = Rxn;
+    v.ps[l] = psn;
+    const T dpb = pbn - pbo, dRx = Rxn - st.Rxo, dd = (psn - pbn) - (st.pso - pbo);
+    r2.add((degf + T(1)) * pbn * pbn);
+    s2.add(degf * dpb * dpb - T(2) * dpb * dRx + dd * dd);
+}
+
+// Sum of x over entries [e0, e1) of the link-major index array, by one group of G lanes,
+// in a fixed order (lane-strided, two loads in flight per lane, then a shuffle tree).
+template <int G, typename T, class Group>
+__device__ __forceinline__ T group_gather_sum(const Group& g, const int* __restrict__ col_idx,
+                                              const T* __restrict__ x, int e0, int e1) {
+    const int sl = g.thread_rank();
+    T s = T(0);
+    for (int e = e0 + sl; e < e1; e += 2 * G) {
+        const int i0 = __ldg(col_idx + e);
+        const int i1 = e + G < e1 ? __ldg(col_idx + e + G) : -1;
+        const T a = __ldg(x + i0);
+        const T b = i1 >= 0 ? __ldg(x + i1) : T(0);
+        s += a + b;
+    }
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) s += g.shfl_down(s, o);
+    return s;
+}
+
+}  // namespace pmp

@@ -20,6 +20,7 @@
 
 #include "pmp_device.cuh"
 #include "pmp_internal.cuh"
+#include "pmp_rows.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -30,33 +31,6 @@ namespace {
 constexpr int kTh = 256;
 constexpr int kWarps = kTh / 32;
 constexpr int kGroup = 8;  // lanes per link (4 links per warp); 4 to 32 measured, 8 kept
-
-// Compensated (Neumaier) running sum in the iteration precision.
-template <typename T>
-struct Acc {
-    T s = T(0), c = T(0);
-    __device__ __forceinline__ void add(T v) {
-        const T t = s + v;
-        c += (fabs(s) >= fabs(v)) ? ((s - t) + v) : ((v - t) + s);
-        s = t;
-    }
-    __device__ __forceinline__ double value() const { return (double)s + (double)c; }
-};
-
-// ---- stream kernel -------------------------------------------------------------------------------
-
-template <typename T>
-__device__ __forceinline__ void stream_epilogue(const View<T>& v, int j, typename Pair<T>::type sum,
-                                                T L, T xo, T Zo, T wt, T lo, T hi, T alpha,
-                                                T inv_rho, Acc<T>& acc) {
-    const T Zn = alpha * L * xo + (T(1) - alpha) * Zo - alpha * sum.x;
-    const T S = Zn - sum.y * inv_rho;
-    const T xn = stream_prox<T>(S, L, wt, inv_rho, lo, hi);
-    v.Z[j] = Zn;
-    v.x[j] = xn;
-    const T dx = xn - xo;
-    acc.add(L * dx * dx);
-}
 
 template <typename T>
 __global__ void __launch_bounds__(kTh) k_stream_rows(View<T> v) {
@@ -76,19 +50,7 @@ __global__ void __launch_bounds__(kTh) k_stream_rows(View<T> v) {
         const T xo = v.x[j], Zo = v.Z[j], wt = __ldg(v.wt + j);
         const T lo = v.box_uniform ? v.lo_u : __ldg(v.lo + j);
         const T hi = v.box_uniform ? v.hi_u : __ldg(v.hi + j);
-        V sum = vzero(V());
-        int e = p;
-        for (; e + 4 <= pn; e += 4) {
-            const int l0 = __ldg(row_idx + e), l1 = __ldg(row_idx + e + 1);
-            const int l2 = __ldg(row_idx + e + 2), l3 = __ldg(row_idx + e + 3);
-            const V g0 = __ldg(pby + l0), g1 = __ldg(pby + l1);
-            const V g2 = __ldg(pby + l2), g3 = __ldg(pby + l3);
-            sum = vadd(sum, g0);
-            sum = vadd(sum, g1);
-            sum = vadd(sum, g2);
-            sum = vadd(sum, g3);
-        }
-        for (; e < pn; ++e) sum = vadd(sum, __ldg(pby + __ldg(row_idx + e)));
+        const V sum = route_sum<T>(row_idx, pby, p, pn);
         stream_epilogue(v, j, sum, (T)(pn - p), xo, Zo, wt, lo, hi, alpha, inv_rho, acc);
     }
     const double s = block_sum(acc.value(), red);
@@ -100,66 +62,6 @@ size_t stream_smem() {
 }
 
 // ---- link kernel ---------------------------------------------------------------------------------
-
-template <typename T>
-struct LinkState {
-    typename Pair<T>::type py;
-    T Rxo, pso, zso, cl;
-};
-
-template <typename T>
-__device__ __forceinline__ LinkState<T> load_link(const View<T>& v, int l) {
-    LinkState<T> s;
-    s.py = v.pby[l];
-    s.Rxo = v.Rx[l];
-    s.pso = v.ps[l];
-    s.zso = v.zs[l];
-    s.cl = __ldg(v.c + l);
-    return s;
-}
-
-// Link epilogue (slack prox, average, z and price updates) and its residual terms.
-template <typename T>
-__device__ __forceinline__ void link_epilogue(const View<T>& v, int l, const LinkState<T>& st,
-                                              T Rxn, int deg, T alpha, T rho, T inv_rho,
-                                              Acc<T>& r2, Acc<T>& s2) {
-    using T2 = typename Pair<T>::type;
-    const T pbo = st.py.x, y = st.py.y;
-    T psn = st.zso - y * inv_rho;
-    psn = psn < -st.cl ? -st.cl : psn;
-    const T degf = (T)deg;
-    const T pbn = (Rxn + psn) / (degf + T(1));
-    T2 out;
-    out.x = pbn;
-    out.y = y + alpha * rho * pbn;
-    v.pby[l] = out;
-    v.zs[l] = alpha * (psn - pbn) + (T(1) - alpha) * st.zso;
-    v.Rx[l] = Rxn;
-    v.ps[l] = psn;
-    const T dpb = pbn - pbo, dRx = Rxn - st.Rxo, dd = (psn - pbn) - (st.pso - pbo);
-    r2.add((degf + T(1)) * pbn * pbn);
-    s2.add(degf * dpb * dpb - T(2) * dpb * dRx + dd * dd);
-}
-
-// Sum of x over entries [e0, e1) of the link-major index array, by one group of G lanes,
-// in a fixed order (lane-strided, two loads in flight per lane, then a shuffle tree).
-template <typename T, class Group>
-__device__ __forceinline__ T group_gather_sum(const Group& g, const int* __restrict__ col_idx,
-                                              const T* __restrict__ x, int e0, int e1) {
-    constexpr int G = kGroup;
-    const int sl = g.thread_rank();
-    T s = T(0);
-    for (int e = e0 + sl; e < e1; e += 2 * G) {
-        const int i0 = __ldg(col_idx + e);
-        const int i1 = e + G < e1 ? __ldg(col_idx + e + G) : -1;
-        const T a = __ldg(x + i0);
-        const T b = i1 >= 0 ? __ldg(x + i1) : T(0);
-        s += a + b;
-    }
-#pragma unroll
-    for (int o = G / 2; o > 0; o >>= 1) s += g.shfl_down(s, o);
-    return s;
-}
 
 template <typename T>
 __global__ void __launch_bounds__(kTh) k_link_rows(View<T> v) {
@@ -184,11 +86,11 @@ __global__ void __launch_bounds__(kTh) k_link_rows(View<T> v) {
             if (p1 - p0 > kLongRow) continue;  // done by its chunks
             LinkState<T> st;
             if (leader) st = load_link(v, it);
-            const T s = group_gather_sum(g, col_idx, x, p0, p1);
+            const T s = group_gather_sum<kGroup>(g, col_idx, x, p0, p1);
             if (leader) link_epilogue(v, it, st, s, p1 - p0, alpha, rho, inv_rho, r2, s2);
         } else {
             const int4 ch = __ldg(v.chunks + (it - m));  // (row, first entry, end entry, first chunk)
-            const T s = group_gather_sum(g, col_idx, x, ch.y, ch.z);
+            const T s = group_gather_sum<kGroup>(g, col_idx, x, ch.y, ch.z);
             int fin = 0;
             if (leader) {
                 v.carry_l[it - m] = s;

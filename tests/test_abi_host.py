@@ -24,7 +24,7 @@ def _declared():
 
 def test_every_declared_symbol_is_exported(capi):
     names = _declared()
-    assert len(names) == 17
+    assert len(names) == 23
     lib = ctypes.CDLL(capi.library_path())
     for name in names:
         assert hasattr(lib, name), name
@@ -137,3 +137,20 @@ def test_null_handle_calls(capi):
     with pytest.raises(capi.NumError):
         capi.num_reset(None)
     capi.num_destroy(None)
+
+
+@pytest.mark.parametrize("so,lo,msg", [([0], [0], "count"), ([1, 2], [0, 1], "must be 0"),
+                                       ([0, 0], [0, 1], "stream"), ([0, 1], [0, 0], "stream")])
+def test_batch_host_rejections(capi, so, lo, msg):
+    so = np.array(so, np.int64)
+    lo = np.array(lo, np.int64)
+    h = ctypes.c_void_p()
+    ptr = lambda a: ctypes.c_void_p(a.ctypes.data)
+    rp = np.array([0, 1], np.int64)
+    rl = np.zeros(1, np.int32)
+    one = np.ones(1)
+    ut = np.zeros(1, np.uint8)
+    rc = capi.library().num_batch_create(ctypes.byref(h), len(so) - 1, ptr(so), ptr(lo), ptr(rp),
+                                         ptr(rl), ptr(one), ptr(ut), ptr(one), None, ptr(one),
+                                         None, None)
+    assert rc == capi.NUM_ERR_INVALID and not h.value

@@ -1,0 +1,127 @@
+"""Batched solves against the oracle, instance by instance, through the C ABI.
+
+Each instance of a batch must follow its own trajectory: its own rho decisions, stopping
+iteration and solution, exactly as if solved alone."""
+import numpy as np
+import pytest
+
+from gpu_util import oracle_run, rel
+from paper_2509_10722_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def _mixed_batch():
+    def box(rng, n):
+        lo = rng.uniform(0.0, 0.3, n)
+        return lo, lo + rng.uniform(0.5, 4.0, n)
+    return [W.random_instance(1, 1, 1, 1, seed=1),
+            W.random_instance(5, 3, 1, 3, seed=2),
+            W.random_instance(37, 11, 1, 6, seed=3, frac_log=0.0),
+            W.random_instance(300, 40, 2, 8, seed=4),
+            W.random_instance(1000, 500, 2, 6, seed=5),
+            W.random_instance(3000, 200, 1, 6, seed=6, box=box),
+            W.random_instance(5000, 5000, 1, 4, seed=7, frac_log=1.0),
+            W.random_instance(20000, 2000, 2, 8, seed=8, link_dist="zipf", frac_log=1.0,
+                              c_scale=0.1, w_dist="lognormal", box=(0.0, 10.0))]
+
+
+@pytest.fixture(scope="module")
+def batch():
+    return _mixed_batch()
+
+
+def _run_batch(insts, iters, precision, eps=0.0, schedules=None, **params):
+    from paper_2509_10722_b300 import capi
+    params.setdefault("history", 64)
+    with capi.Batch(insts, precision=precision, **params) as b:
+        if schedules is not None:
+            b.set_rho_schedules(schedules)
+        rc, it, st = b.solve(iters, eps)
+        xs, ps, infos = b.get()
+    return dict(rc=rc, iters=it, status=st, x=[x.copy() for x in xs],
+                lam=[p.copy() for p in ps], info=infos)
+
+
+@pytest.mark.parametrize("iters", [1, 60, 300])
+def test_batch_fp64_matches_oracle_per_instance(batch, iters):
+    g = _run_batch(batch, iters, 1)
+    assert list(g["iters"]) == [iters] * len(batch)
+    for i, inst in enumerate(batch):
+        ref = oracle_run(inst, iters)
+        assert rel(g["x"][i], ref["x"]) <= 1e-10, i
+        assert rel(g["lam"][i], ref["lam"]) <= 1e-10, i
+
+
+def test_batch_fp32_matches_oracle_on_its_schedules(batch):
+    iters = 300
+    refs = [oracle_run(inst, iters) for inst in batch]
+    sched = np.zeros((len(batch), iters // 50), dtype=np.int8)
+    for i, r in enumerate(refs):
+        sched[i, :r["decisions"].size] = r["decisions"]
+    g = _run_batch(batch, iters, 0, schedules=sched)
+    for i, r in enumerate(refs):
+        assert rel(g["x"][i], r["x"]) <= 1e-4, i
+        assert rel(g["lam"][i], r["lam"]) <= 1e-4, i
+
+
+def test_batch_instances_stop_independently(batch):
+    """Instances that have a solution stop at the oracle's iteration, each at its own count
+    (left out: the per-stream-box instance, whose lower bounds exceed some capacities, so it
+    is infeasible and diverges in the oracle too, and the congested Zipf instance, which
+    does not reach 1e-6 within the limit)."""
+    batch = [batch[i] for i in (0, 1, 2, 3, 4, 6)]
+    eps = 1e-6
+    g = _run_batch(batch, 100_000, 1, eps=eps)
+    assert g["rc"] == 0 and np.all(g["status"] == 0)
+    refs = [oracle_run(inst, 100_000, eps=eps) for inst in batch]
+    assert list(g["iters"]) == [r["iters"] for r in refs]
+    assert len(set(g["iters"])) > 1
+    for i, r in enumerate(refs):
+        assert rel(g["x"][i], r["x"]) <= 1e-9, i
+
+
+def test_batch_equals_single_solves(batch):
+    """Same rows, same arithmetic: bit-identical to solving each instance alone, except
+    where the single-instance kernels cut a link above 2,048 streams into chunks (the
+    Zipf instance), which changes the FP32 summation order of that link."""
+    from paper_2509_10722_b300 import capi
+    g = _run_batch(batch, 200, 0)
+    for i, inst in enumerate(batch):
+        with capi.Problem(inst, precision=0, history=64) as p:
+            p.solve(200, 0.0)
+            x, lam, info = p.get()
+        if np.bincount(inst["route_links"], minlength=inst["m"]).max() > 2048:
+            assert rel(g["x"][i], x) <= 1e-5 and rel(g["lam"][i], lam) <= 1e-5, i
+            continue
+        assert np.array_equal(g["x"][i], x), i
+        assert np.array_equal(g["lam"][i], lam), i
+        assert abs(g["info"][i]["objective"] - info["objective"]) <= 1e-12 * max(1.0, abs(info["objective"]))
+
+
+def test_batch_rejects_cross_instance_routes():
+    from paper_2509_10722_b300 import capi
+    insts = [W.random_instance(20, 5, 1, 3, seed=11), W.random_instance(20, 5, 1, 3, seed=12)]
+    so, lo, st = capi.stack_instances(insts)
+    st["route_links"][0] = 7  # stream 0 (instance 0) uses a link of instance 1
+    h = capi.ctypes.c_void_p()
+    arr = [np.ascontiguousarray(st[k]) for k in ("route_ptr", "route_links", "c", "utype", "w",
+                                                  "lo", "hi")]
+    rc = capi.library().num_batch_create(capi.ctypes.byref(h), 2, capi._hptr(so), capi._hptr(lo),
+                                         *[capi._hptr(a) for a in arr], None, None)
+    assert rc == capi.NUM_ERR_INVALID and "another instance" in capi.num_last_error()
+
+
+def test_c4_recipe_batch_converges():
+    """The batched recipe (256 instances, n log-uniform in [1e3, 1e5], m = n / 10, routes of
+    2..8 links, degraded capacities): every instance reaches eps_abs = 1e-4, and sampled
+    instances match their FP64 oracle objective at the same tolerance to 1e-5."""
+    from oracle import kkt
+    insts = W.batched_instances(256, seed=0)
+    g = _run_batch(insts, 50_000, 0, eps=1e-4)
+    assert np.all(g["status"] == 0)
+    order = np.argsort([t["n"] for t in insts])
+    for i in order[:4]:
+        ref = oracle_run(insts[i], 100_000, eps=1e-4)
+        u = kkt.utility(insts[i], ref["x"])
+        assert abs(g["info"][i]["objective"] - u) <= 1e-5 * abs(u), i
