@@ -54,7 +54,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="c2", choices=sorted(WORKLOAD_TEXT))
+    ap.add_argument("--workload", default="c2", choices=sorted(WORKLOAD_TEXT) + ["c4"])
     ap.add_argument("--scale", type=float, default=None, help="shrink n and m (testing only)")
     ap.add_argument("--eps", type=float, default=1e-4)
     ap.add_argument("--max-iters", type=int, default=50_000)
@@ -449,11 +449,80 @@ def run_ours(args, dist):
     dist.close()
 
 
+def run_batched(args):
+    """The batched recipe: 256 independent instances (n log-uniform in [1e3, 1e5], m = n/10,
+    routes of 2..8 links, capacities degraded by U[0.3, 1], 70% log) solved to eps_abs =
+    1e-4 as one batch, against the same 256 instances solved one after the other with the
+    single-instance FP32 path and with the plain FP64 path.  Each leg includes creation from
+    host arrays, the solve and the host copy of the results; CUDA events on one stream."""
+    import ctypes
+
+    import torch
+    from paper_2509_10722_b300 import capi
+    insts = W.batched_instances(256, seed=0)
+    stream = torch.cuda.Stream()
+    sp = stream.cuda_stream
+
+    def batch_leg():
+        with capi.Batch(insts, stream=sp, precision=0, profile=1) as b:
+            rc, it, st = b.solve(args.max_iters, args.eps)
+            xs, ps, infos = b.get()
+            ms, runs = b.kernel_times()
+        return int(it.sum()), st, ms, runs
+
+    def seq_leg(precision):
+        tot = 0
+        for inst in insts:
+            with capi.Problem(inst, stream=sp, precision=precision) as p:
+                _, it = p.solve(args.max_iters, args.eps)
+                p.get()
+            tot += it
+        return tot
+
+    def timed_leg(fn, reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = [fn() for _ in range(reps)]
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / reps, out[-1]
+
+    for _ in range(args.warmup):
+        batch_leg()
+    seq_leg(0)
+    t_b, (it_b, st_b, kms, kruns) = timed_leg(batch_leg, args.steps)
+    t_s, it_s = timed_leg(lambda: seq_leg(0), 1)
+    t_p, it_p = timed_leg(lambda: seq_leg(2), 1)
+    n_tot = int(sum(t["n"] for t in insts))
+    nnz_tot = int(sum(int(t["route_ptr"][-1]) for t in insts))
+    line = {"metric": "batched PMP: 256 instances to eps_abs 1e-4, aggregate iterations/s",
+            "value": it_b / (t_b / 1e3), "unit": "iterations/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_b,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "c4: 256 instances, n log-uniform in [1e3, 1e5], m = n/10, "
+                                   "routes U{2..8}, c ~ U[1,10] x U[0.3,1], 70% log, box [0,20]",
+                       "total_n": n_tot, "total_nnz": nnz_tot,
+                       "step": "num_batch_create (host arrays) + num_batch_solve + num_batch_get"},
+            "converged": int(np.sum(st_b == 0)), "batch_ms": t_b,
+            "sequential_fp32_ms": t_s, "sequential_plain_fp64_ms": t_p,
+            "speedup_vs_sequential_fp32": t_s / t_b, "speedup_vs_sequential_plain_fp64": t_p / t_b,
+            "iterations": {"batch": it_b, "sequential_fp32": int(it_s),
+                           "sequential_plain_fp64": int(it_p)},
+            "kernels_ms_per_launch": {"stream": float(kms[0] / max(kruns[0], 1)),
+                                      "link": float(kms[1] / max(kruns[1], 1))},
+            "kernel_launches": {"stream": int(kruns[0]), "link": int(kruns[1])}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     dist = Dist()
     if args.impl == "reference":
         run_reference(args, dist)
+        return
+    if args.workload == "c4":
+        run_batched(args)
         return
     run_ours(args, dist)
 
