@@ -194,6 +194,26 @@ NUM_API int num_get_history(const num_problem* h, double* hist, int64_t max_rows
  * col_idx int32[nnz] (each row's stream ids ascending).  For checking the device build. */
 NUM_API int num_get_operator(const num_problem* h, int64_t* row_ptr, int32_t* col_idx);
 
+/* Replace the link capacities (HOST double[m], finite and > 0) and keep the iterate, so
+ * that the next num_solve continues from the current point: the warm start after a
+ * capacity degradation of Sec. V-D.  num_reset first for a cold start instead. */
+NUM_API int num_set_capacity(num_problem* h, const double* c);
+
+/* The iterate, as HOST doubles (each pointer may be NULL): per stream, in the caller's
+ * order, x[n] and Z[n] (sum over the stream's terminals of the link-side copies z); per
+ * link pbar[m] (link average), y[m] (price = rho u), zs[m] (the slack terminal's z),
+ * Rx[m] (R x of the last iteration), ps[m] (the slack terminal's flow); *rho. */
+NUM_API int num_get_state(const num_problem* h, double* x, double* Z, double* pbar, double* y,
+                          double* zs, double* Rx, double* ps, double* rho);
+
+/* Start a fresh run (iteration 0, empty history) from the given iterate and rho (> 0);
+ * arrays as in num_get_state, a NULL array leaves that part of the current iterate as is.
+ * Used to warm-start a modified instance (for example one pruned after link failures,
+ * Sec. V-D) from another instance's solution. */
+NUM_API int num_set_state(num_problem* h, const double* x, const double* Z, const double* pbar,
+                          const double* y, const double* zs, const double* Rx, const double* ps,
+                          double rho);
+
 /* Zero the iteration state and history (x = z = u = 0, rho = rho0, iteration 0). */
 NUM_API int num_reset(num_problem* h);
 

@@ -29,7 +29,8 @@ class _Params(ctypes.Structure):
     _fields_ = [("rho0", ctypes.c_double), ("alpha", ctypes.c_double),
                 ("mu", ctypes.c_double), ("gamma", ctypes.c_double),
                 ("eps_abs", ctypes.c_double), ("period", ctypes.c_int64),
-                ("max_iters", ctypes.c_int64), ("debug", ctypes.c_int32)]
+                ("max_iters", ctypes.c_int64), ("debug", ctypes.c_int32),
+                ("switch_iter", ctypes.c_int64), ("c_switch", ctypes.c_void_p)]
 
 
 def lib_path(plant=0):
@@ -94,8 +95,11 @@ def _ptr(a):
 
 
 def solve(inst, max_iters, *, eps_abs=None, rho0=None, alpha=None, mu=None, gamma=None,
-          period=None, rho_replay=None, debug=False, plant=0):
+          period=None, rho_replay=None, debug=False, plant=0, c_switch=None, switch_iter=0):
     """Run the literal PMP of Sec. III on `inst` (see workloads.py for the layout).
+
+    c_switch / switch_iter: after `switch_iter` iterations the capacities become c_switch
+    and the run continues from its current iterate (the warm start of Sec. V-D).
 
     Returns a dict: x[n], slack[m], lam[m] (prices rho u), hist[k, 3] = (||r||, ||s||, rho)
     per iteration, decisions (rho decision at each update point), iters, converged,
@@ -123,8 +127,11 @@ def solve(inst, max_iters, *, eps_abs=None, rho0=None, alpha=None, mu=None, gamm
     iters = ctypes.c_int64(0)
     conv = ctypes.c_int32(0)
     viol = ctypes.c_double(0.0)
+    cs = None if c_switch is None else np.ascontiguousarray(c_switch, dtype=np.float64)
     p = _Params(prm["rho0"], prm["alpha"], prm["mu"], prm["gamma"], prm["eps_abs"],
-                int(prm["period"]), int(max_iters), 1 if debug else 0)
+                int(prm["period"]), int(max_iters), 1 if debug else 0,
+                int(switch_iter) if cs is not None else 0,
+                None if cs is None else cs.ctypes.data)
     if rho_replay is not None:
         rr = np.ascontiguousarray(rho_replay, dtype=np.int8)
         rr_ptr, rr_len = _ptr(rr), rr.size

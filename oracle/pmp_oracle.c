@@ -55,6 +55,8 @@ typedef struct {
     int64_t period;    /* iterations between rho updates: 50 */
     int64_t max_iters;
     int32_t debug;     /* 1: check the ADMM identities after every iteration */
+    int64_t switch_iter;     /* > 0: capacities become c_switch after this many iterations */
+    const double* c_switch;  /* new capacities (a degraded network, Sec. V-D), or NULL */
 } oracle_params;
 
 /* ---- proximal operators, Sec. III-E ---------------------------------------------------- */
@@ -166,6 +168,9 @@ int oracle_solve(int64_t n, int64_t m, const int64_t* route_ptr, const int32_t* 
     double worst = 0.0;
 
     for (k = 1; k <= prm->max_iters; ++k) {
+        /* capacity change between two iterations (warm start after degradation, Sec. V-D):
+         * the slack streams' cost uses the new c from here on, the iterate is kept */
+        if (prm->c_switch && prm->switch_iter > 0 && k == prm->switch_iter + 1) c = prm->c_switch;
         /* 1. stream prox: traffic streams, then slack streams */
         for (int64_t s = 0; s < n; ++s) {
             double S = 0.0;

@@ -80,6 +80,9 @@ def _load():
         "num_get_history": (ctypes.c_int, [P, P, i64, ctypes.POINTER(i64)]),
         "num_get_operator": (ctypes.c_int, [P, P, P]),
         "num_reset": (ctypes.c_int, [P]),
+        "num_set_capacity": (ctypes.c_int, [P, P]),
+        "num_get_state": (ctypes.c_int, [P, P, P, P, P, P, P, P, ctypes.POINTER(d)]),
+        "num_set_state": (ctypes.c_int, [P, P, P, P, P, P, P, P, d]),
         "num_iteration_bytes": (ctypes.c_int, [P, P]),
         "num_get_kernel_times": (ctypes.c_int, [P, P, P, i32, ctypes.POINTER(i32)]),
         "num_kernel_launches": (ctypes.c_int64, []),
@@ -105,7 +108,8 @@ def _load():
 _lib = _load()
 EXPORTED = ("num_default_params", "num_create", "num_create_device", "num_set_rho_schedule",
             "num_solve", "num_get", "num_get_device", "num_get_history", "num_get_operator",
-            "num_reset", "num_iteration_bytes", "num_get_kernel_times", "num_kernel_launches",
+            "num_reset", "num_set_capacity", "num_get_state", "num_set_state",
+            "num_iteration_bytes", "num_get_kernel_times", "num_kernel_launches",
             "num_objective_noalloc", "num_destroy", "num_strerror", "num_last_error",
             "num_batch_create", "num_batch_set_rho_schedules", "num_batch_solve",
             "num_batch_get", "num_batch_get_kernel_times", "num_batch_destroy")
@@ -248,6 +252,31 @@ def num_get_operator(h, m, nnz):
 
 def num_reset(h):
     _check(_lib.num_reset(h))
+
+
+STATE_FIELDS = ("x", "Z", "pbar", "y", "zs", "Rx", "ps")
+
+
+def num_set_capacity(h, m, c):
+    _check(_lib.num_set_capacity(h, _hptr(_host(c, np.float64, int(m), "c"))))
+
+
+def num_get_state(h, n, m):
+    """The iterate as a dict of FP64 arrays (streams in the caller's order) plus rho."""
+    st = {k: np.empty(n if k in ("x", "Z") else m) for k in STATE_FIELDS}
+    rho = ctypes.c_double(0.0)
+    _check(_lib.num_get_state(h, *[_hptr(st[k]) for k in STATE_FIELDS], ctypes.byref(rho)))
+    st["rho"] = rho.value
+    return st
+
+
+def num_set_state(h, n, m, state):
+    """Start a fresh run from `state` (dict as from num_get_state; missing arrays kept)."""
+    arrs = []
+    for k in STATE_FIELDS:
+        a = state.get(k)
+        arrs.append(None if a is None else _host(a, np.float64, n if k in ("x", "Z") else m, k))
+    _check(_lib.num_set_state(h, *[_hptr(a) for a in arrs], float(state["rho"])))
 
 
 def num_iteration_bytes(h):
@@ -433,6 +462,15 @@ class Problem:
 
     def reset(self):
         num_reset(self.h)
+
+    def set_capacity(self, c):
+        num_set_capacity(self.h, self.m, c)
+
+    def get_state(self):
+        return num_get_state(self.h, self.n, self.m)
+
+    def set_state(self, state):
+        num_set_state(self.h, self.n, self.m, state)
 
     def iteration_bytes(self):
         return num_iteration_bytes(self.h)

@@ -867,6 +867,83 @@ int num_reset(num_problem* h) {
     return finish_cuda(e, "reset");
 }
 
+int num_set_capacity(num_problem* h, const double* c) {
+    g_last_error.clear();
+    if (!h || !c) return fail(NUM_ERR_INVALID, "NULL argument");
+    for (int64_t l = 0; l < h->m; ++l)
+        if (!(c[l] > 0.0) || !std::isfinite(c[l]))
+            return fail(NUM_ERR_INVALID, "a capacity is not finite and > 0");
+    cudaStream_t st = h->stream;
+    cudaError_t e = order_after_legacy(h);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h->y64, c, 8 * (size_t)h->m, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = h->prec == NUM_FUSED_FP32
+                ? pmp::convert_params<float>(0, (int)h->m, h->y64, nullptr, nullptr, nullptr,
+                                             nullptr, nullptr, (float*)h->c, nullptr, nullptr,
+                                             nullptr, st)
+                : pmp::convert_params<double>(0, (int)h->m, h->y64, nullptr, nullptr, nullptr,
+                                              nullptr, nullptr, (double*)h->c, nullptr, nullptr,
+                                              nullptr, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    return finish_cuda(e, "setting the capacities");
+}
+
+static int state_io(num_problem* h, double** arrays, double* rho, bool out) {
+    cudaStream_t st = h->stream;
+    cudaError_t e = order_after_legacy(h);
+    if (e != cudaSuccess) return cuda_fail(e, "ordering");
+    if (!out) {
+        // a fresh run from the given iterate: iteration 0, the given rho, no history
+        e = pmp::ctl_reset(h->ctl, *rho, h->prm.alpha, h->prm.mu, h->prm.gamma,
+                           h->prm.rho_period, h->prm.history, st);
+        if (e == cudaSuccess && h->sched_len > 0)
+            e = pmp::ctl_set_schedule_len(h->ctl, h->sched_len, st);
+        if (e != cudaSuccess) return cuda_fail(e, "resetting the control block");
+    }
+    for (int which = 0; which < 7; ++which) {
+        double* host = arrays[which];
+        if (!host) continue;
+        double* buf = which < 2 ? h->x64 : h->y64;
+        const size_t bytes = 8 * (size_t)(which < 2 ? h->n : h->m);
+        if (!out) e = cudaMemcpyAsync(buf, host, bytes, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess)
+            e = h->prec == NUM_FUSED_FP32
+                    ? pmp::state_transfer<float>(make_view<float>(h), which, buf, out, st)
+                    : pmp::state_transfer<double>(make_view<double>(h), which, buf, out, st);
+        if (e == cudaSuccess && out) e = cudaMemcpyAsync(host, buf, bytes, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // the staging buffer is reused
+        if (e != cudaSuccess) return cuda_fail(e, "transferring the state");
+    }
+    if (out) {
+        e = cudaMemcpyAsync(h->ctl_host, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_fail(e, "reading the control block");
+        *rho = h->ctl_host->rho;
+    }
+    return NUM_OK;
+}
+
+int num_get_state(const num_problem* hc, double* x, double* Z, double* pbar, double* y,
+                  double* zs, double* Rx, double* ps, double* rho) {
+    g_last_error.clear();
+    if (!hc || !rho) return fail(NUM_ERR_INVALID, "NULL argument");
+    double* arrays[7] = {x, Z, pbar, y, zs, Rx, ps};
+    return state_io(const_cast<num_problem*>(hc), arrays, rho, true);
+}
+
+int num_set_state(num_problem* h, const double* x, const double* Z, const double* pbar,
+                  const double* y, const double* zs, const double* Rx, const double* ps,
+                  double rho) {
+    g_last_error.clear();
+    if (!h) return fail(NUM_ERR_INVALID, "NULL argument");
+    if (!(rho > 0.0) || !std::isfinite(rho)) return fail(NUM_ERR_INVALID, "rho must be > 0");
+    double* arrays[7] = {const_cast<double*>(x), const_cast<double*>(Z), const_cast<double*>(pbar),
+                         const_cast<double*>(y), const_cast<double*>(zs), const_cast<double*>(Rx),
+                         const_cast<double*>(ps)};
+    return state_io(h, arrays, &rho, false);
+}
+
 int num_iteration_bytes(const num_problem* h, double* out) {
     g_last_error.clear();
     if (!h || !out) return fail(NUM_ERR_INVALID, "NULL argument");

@@ -392,6 +392,51 @@ k_export(View<T> v, double* x_out, double* y_out, double* part) {
     }
 }
 
+// ---- iterate export / import (warm starts) -----------------------------------------------------
+// which: 0 x, 1 Z (per stream, caller order); 2 pbar, 3 y, 4 zs, 5 Rx, 6 ps (per link)
+template <typename T>
+__device__ __forceinline__ T* state_array(const View<T>& v, int which) {
+    switch (which) {
+        case 0: return v.x;
+        case 1: return v.Z;
+        case 4: return v.zs;
+        case 5: return v.Rx;
+        case 6: return v.ps;
+        default: return nullptr;
+    }
+}
+
+template <typename T>
+__global__ void k_state_out(View<T> v, int which, double* out) {
+    const int count = which < 2 ? v.n : v.m;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < count; j += gridDim.x * blockDim.x) {
+        double val;
+        if (which == 2)
+            val = v.pbar ? (double)v.pbar[j] : (double)v.pby[j].x;
+        else if (which == 3)
+            val = v.y ? (double)v.y[j] : (double)v.pby[j].y;
+        else
+            val = (double)state_array(v, which)[j];
+        const int dst = (which < 2 && v.perm) ? v.perm[j] : j;  // caller's stream order
+        out[dst] = val;
+    }
+}
+
+template <typename T>
+__global__ void k_state_in(View<T> v, int which, const double* in) {
+    const int count = which < 2 ? v.n : v.m;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < count; j += gridDim.x * blockDim.x) {
+        const double val = in[(which < 2 && v.perm) ? v.perm[j] : j];
+        if (which == 2) {
+            if (v.pbar) v.pbar[j] = (T)val; else v.pby[j].x = (T)val;
+        } else if (which == 3) {
+            if (v.y) v.y[j] = (T)val; else v.pby[j].y = (T)val;
+        } else {
+            state_array(v, which)[j] = (T)val;
+        }
+    }
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------------------------
@@ -565,6 +610,19 @@ template cudaError_t convert_params<double>(int, int, const double*, const uint8
                                             cudaStream_t);
 
 int export_partial_blocks(int n) { return blocks_for(n, kExportThreads, 1024); }
+
+template <typename T>
+cudaError_t state_transfer(const View<T>& v, int which, double* buf, bool out, cudaStream_t st) {
+    const int count = which < 2 ? v.n : v.m;
+    if (out)
+        k_state_out<T><<<blocks_for(count, kThreads, 65535), kThreads, 0, st>>>(v, which, buf);
+    else
+        k_state_in<T><<<blocks_for(count, kThreads, 65535), kThreads, 0, st>>>(v, which, buf);
+    note_launches(1);
+    return cudaGetLastError();
+}
+template cudaError_t state_transfer<float>(const View<float>&, int, double*, bool, cudaStream_t);
+template cudaError_t state_transfer<double>(const View<double>&, int, double*, bool, cudaStream_t);
 
 template <typename T>
 cudaError_t export_solution(const View<T>& v, double* x_out, double* y_out, double* part,

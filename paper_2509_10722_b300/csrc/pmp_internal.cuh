@@ -240,6 +240,10 @@ template <typename T>
 cudaError_t export_solution(const View<T>& v, double* x_out, double* y_out, double* part,
                             int part_blocks, cudaStream_t st);
 int export_partial_blocks(int n);
+// One state array between the device iterate and an FP64 device buffer in the caller's
+// order: which = 0 x, 1 Z (streams), 2 pbar, 3 y, 4 zs, 5 Rx, 6 ps (links).
+template <typename T>
+cudaError_t state_transfer(const View<T>& v, int which, double* buf, bool out, cudaStream_t st);
 
 // Small control kernels.
 cudaError_t ctl_arm(Ctl* ctl, long long k_limit, double eps_tol, cudaStream_t st);

@@ -197,6 +197,45 @@ def batched_instances(count=256, seed=0):
     return out
 
 
+def degraded_capacities(inst, p=0.25, factor=0.5, seed=1):
+    """Capacity degradation of Sec. V-D: every link independently keeps its capacity, or
+    with probability p has it multiplied by `factor`."""
+    rng = np.random.default_rng(seed)
+    hit = rng.random(inst["m"]) < p
+    return np.where(hit, inst["c"] * factor, inst["c"]), hit
+
+
+def failed_links(inst, p=0.25, seed=2):
+    """Link failures of Sec. V-D: every link fails independently with probability p."""
+    rng = np.random.default_rng(seed)
+    return rng.random(inst["m"]) < p
+
+
+def prune(inst, failed):
+    """The instance left after link failures (Sec. V-D): failed links leave R, and so does
+    every stream whose route uses one of them.  Returns (pruned instance, kept stream ids,
+    kept link ids), ids in the original numbering, in increasing order."""
+    failed = np.asarray(failed, dtype=bool)
+    lengths = np.diff(inst["route_ptr"])
+    route_of = np.repeat(np.arange(inst["n"]), lengths)
+    dead_stream = np.zeros(inst["n"], dtype=bool)
+    np.logical_or.at(dead_stream, route_of, failed[inst["route_links"]])
+    keep_s = np.flatnonzero(~dead_stream)
+    keep_l = np.flatnonzero(~failed)
+    if keep_s.size == 0 or keep_l.size == 0:
+        raise ValueError("no stream or no link survives")
+    new_link = np.full(inst["m"], -1, dtype=np.int64)
+    new_link[keep_l] = np.arange(keep_l.size)
+    keep_entry = ~dead_stream[route_of]
+    route_ptr = np.zeros(keep_s.size + 1, dtype=np.int64)
+    np.cumsum(lengths[keep_s], out=route_ptr[1:])
+    out = dict(n=int(keep_s.size), m=int(keep_l.size), route_ptr=route_ptr,
+               route_links=new_link[inst["route_links"][keep_entry]].astype(np.int32),
+               c=inst["c"][keep_l], utype=inst["utype"][keep_s], w=inst["w"][keep_s],
+               lo=inst["lo"][keep_s], hi=inst["hi"][keep_s])
+    return out, keep_s, keep_l
+
+
 def four_stream_example():
     """The four-stream, three-link network of the paper's small example (Sec. III-A):
     R = [[1,0,0,0],[0,1,1,0],[0,1,0,1]].  The paper gives only the structure; capacities 1,

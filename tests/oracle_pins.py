@@ -310,6 +310,20 @@ def pin_large_rho_start(plant=0):
     return True, "ok"
 
 
+def pin_capacity_switch(plant=0):
+    """Warm start after a capacity change (Sec. V-D): converged on c = 3, then switched to
+    c = 6, the run converges to the closed form of the new capacity, x = w c / sum w."""
+    w = np.array([1.0, 2.0, 0.5])
+    inst = _inst([[0]] * 3, 1, [3.0], w, [0, 0, 0])
+    r = oracle.solve(inst, 3000, eps_abs=0.0, c_switch=np.array([6.0]), switch_iter=400,
+                     plant=plant)
+    before = oracle.solve(inst, 400, eps_abs=0.0, plant=plant)
+    ok = _close(before["x"], w * 3.0 / w.sum(), 1e-7) and \
+        _close(r["x"], w * 6.0 / w.sum(), 1e-7) and \
+        _close(r["lam"], [w.sum() / 6.0], 1e-7) and _close(r["slack"], [0.0], 0.0, 1e-6)
+    return ok, f"iters {r['iters']} x={r['x']} lam={r['lam']}"
+
+
 # ---- 4. residuals, stopping test and rho rule (Sec. III-F, III-G) ---------------------------
 
 def _terminal_flows(inst, x, slack):
@@ -393,7 +407,8 @@ def pin_identities(plant=0):
 PINS = [pin_prox_log, pin_prox_linear, pin_prox_slack, pin_single_link,
         pin_single_link_waterfill, pin_linear_single_link, pin_four_stream, pin_line_network,
         pin_dual_solver, pin_lp, pin_mixed_slsqp, pin_bruteforce, pin_kkt_random,
-        pin_large_rho_start, pin_residuals, pin_stop_rule, pin_rho_rule, pin_identities]
+        pin_large_rho_start, pin_capacity_switch, pin_residuals, pin_stop_rule, pin_rho_rule,
+        pin_identities]
 
 # planted mistakes of pmp_oracle.c (ORACLE_PLANT values) and what each one is
 PLANTS = {

@@ -79,3 +79,22 @@ def test_batched_recipe():
         assert 1000 <= inst["n"] <= 100000
         assert inst["m"] == max(8, inst["n"] // 10)
         _check(inst, 2, 8)
+
+
+def test_degrade_and_prune_bookkeeping():
+    inst = W.random_instance(500, 80, 1, 6, seed=9)
+    c2, hit = W.degraded_capacities(inst, p=0.25, factor=0.5, seed=3)
+    assert np.allclose(c2[hit], 0.5 * inst["c"][hit]) and np.array_equal(c2[~hit], inst["c"][~hit])
+    assert 0.1 < hit.mean() < 0.4
+    failed = W.failed_links(inst, p=0.25, seed=4)
+    pr, ks, kl = W.prune(inst, failed)
+    assert pr["n"] == ks.size and pr["m"] == kl.size == (~failed).sum()
+    # every kept stream keeps its whole route (renumbered); no removed stream survives
+    for new_j, old_j in enumerate(ks):
+        old = inst["route_links"][inst["route_ptr"][old_j]:inst["route_ptr"][old_j + 1]]
+        new = pr["route_links"][pr["route_ptr"][new_j]:pr["route_ptr"][new_j + 1]]
+        assert not failed[old].any()
+        assert np.array_equal(kl[new], old)
+    for old_j in np.setdiff1d(np.arange(inst["n"]), ks):
+        old = inst["route_links"][inst["route_ptr"][old_j]:inst["route_ptr"][old_j + 1]]
+        assert failed[old].any()
