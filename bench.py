@@ -66,8 +66,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-iters", type=int, default=3)
     ap.add_argument("--ref-iters", type=int, default=1, help="oracle iterations per reference step")
-    ap.add_argument("--scenario", choices=["none", "warmstart"], default="none",
-                    help="warmstart: degradation and failure re-solves of Sec. V-D")
+    ap.add_argument("--scenario", choices=["none", "warmstart", "adjoint"], default="none",
+                    help="warmstart: degradation and failure re-solves of Sec. V-D; "
+                         "adjoint: gradients of 500 unrolled iterations on c5")
     return ap.parse_args()
 
 
@@ -572,11 +573,58 @@ def run_warmstart(args):
     print(json.dumps(line), flush=True)
 
 
+def run_adjoint(args):
+    """The differentiation recipe (c5: n = 1e6, m = 1e5, routes of 2..8 links, log
+    utilities, box [0, 20]): d(sum U(x_500))/dc and /dw through 500 unrolled iterations with
+    checkpoints every 50, FP32 and FP64, timed with CUDA events against the plain forward
+    solve of the same 500 iterations; FP32 gradients compared with FP64 ones."""
+    import torch
+    from paper_2509_10722_b300 import capi
+    inst = W.workload("c5", scale=args.scale)
+    stream = torch.cuda.Stream()
+    sp = stream.cuda_stream
+    iters, kc = 500, 50
+    out = {}
+    grads = {}
+    for name, prec in (("fp32", 0), ("fp64", 1)):
+        with capi.Problem(inst, stream=sp, precision=prec) as p:
+            p.adjoint(iters, kc)  # warm-up
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            cg, wg, J = p.adjoint(iters, kc)
+            e1.record(stream)
+            e1.synchronize()
+            t_adj = e0.elapsed_time(e1)
+            p.reset()
+            e0.record(stream)
+            p.solve(iters, 0.0)
+            e1.record(stream)
+            e1.synchronize()
+            t_fwd = e0.elapsed_time(e1)
+        grads[name] = (cg, wg)
+        out[name] = {"adjoint_ms": t_adj, "forward_ms": t_fwd, "ratio": t_adj / t_fwd,
+                     "objective": J}
+    rel = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))
+    line = {"metric": "adjoint of 500 unrolled PMP iterations (dJ/dc, dJ/dw), c5",
+            "value": out["fp32"]["adjoint_ms"], "unit": "ms", "higher_is_better": False,
+            "n_gpus": 1, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "c5: n=1e6, m=1e5, routes U{2..8}, log utilities, "
+                                   "w~U[0.5,2], box [0,20]", "iters": iters,
+                       "checkpoint_every": kc, "scale": args.scale},
+            **out,
+            "fp32_vs_fp64": {"dc_rel": rel(grads["fp32"][0], grads["fp64"][0]),
+                             "dw_rel": rel(grads["fp32"][1], grads["fp64"][1])}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     dist = Dist()
     if args.impl == "reference":
         run_reference(args, dist)
+        return
+    if args.scenario == "adjoint":
+        run_adjoint(args)
         return
     if args.scenario == "warmstart":
         run_warmstart(args)

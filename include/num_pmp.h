@@ -214,6 +214,27 @@ NUM_API int num_set_state(num_problem* h, const double* x, const double* Z, cons
                           const double* y, const double* zs, const double* Rx, const double* ps,
                           double rho);
 
+/* Replace the utility weights (HOST double[n], caller order, finite and > 0); the utility
+ * types and the iterate are kept. */
+NUM_API int num_set_weights(num_problem* h, const double* w);
+
+/* Reverse-mode derivative of `iters` PMP iterations run from the zero state (the map from
+ * (c, w) to the rates x after exactly `iters` iterations, each iteration's rho fixed at the
+ * value this forward run takes): for the cotangent xbar (HOST double[n], caller order, or
+ * NULL) plus, if objective = 1, the total utility J = sum_j U_j(x_j) (its gradient in x
+ * and its direct dependence on w), writes dJ/dc to c_grad (HOST double[m]) and dJ/dw to
+ * w_grad (HOST double[n], caller order), each may be NULL, and J to *objective_out (may be
+ * NULL).  The derivative runs the adjoint of every step backwards: transposed gathers over
+ * R and the Jacobians of the stream prox (zero at the box bounds) and of the slack prox.
+ * It keeps the full iterate every checkpoint_every iterations (0: only at the start) and
+ * recomputes each segment (the iteration is deterministic), storing x and the slack flow
+ * of each iteration of the segment: device memory about
+ * checkpoint_every * (n + m) values + (iters / checkpoint_every) iterates.  A set rho
+ * schedule applies to the forward run.  The handle is left at the forward result. */
+NUM_API int num_adjoint(num_problem* h, int64_t iters, int32_t checkpoint_every,
+                        const double* xbar, int32_t objective, double* c_grad, double* w_grad,
+                        double* objective_out);
+
 /* Zero the iteration state and history (x = z = u = 0, rho = rho0, iteration 0). */
 NUM_API int num_reset(num_problem* h);
 

@@ -81,6 +81,8 @@ def _load():
         "num_get_operator": (ctypes.c_int, [P, P, P]),
         "num_reset": (ctypes.c_int, [P]),
         "num_set_capacity": (ctypes.c_int, [P, P]),
+        "num_set_weights": (ctypes.c_int, [P, P]),
+        "num_adjoint": (ctypes.c_int, [P, i64, i32, P, i32, P, P, ctypes.POINTER(d)]),
         "num_get_state": (ctypes.c_int, [P, P, P, P, P, P, P, P, ctypes.POINTER(d)]),
         "num_set_state": (ctypes.c_int, [P, P, P, P, P, P, P, P, d]),
         "num_iteration_bytes": (ctypes.c_int, [P, P]),
@@ -108,7 +110,8 @@ def _load():
 _lib = _load()
 EXPORTED = ("num_default_params", "num_create", "num_create_device", "num_set_rho_schedule",
             "num_solve", "num_get", "num_get_device", "num_get_history", "num_get_operator",
-            "num_reset", "num_set_capacity", "num_get_state", "num_set_state",
+            "num_reset", "num_set_capacity", "num_set_weights", "num_adjoint",
+            "num_get_state", "num_set_state",
             "num_iteration_bytes", "num_get_kernel_times", "num_kernel_launches",
             "num_objective_noalloc", "num_destroy", "num_strerror", "num_last_error",
             "num_batch_create", "num_batch_set_rho_schedules", "num_batch_solve",
@@ -259,6 +262,22 @@ STATE_FIELDS = ("x", "Z", "pbar", "y", "zs", "Rx", "ps")
 
 def num_set_capacity(h, m, c):
     _check(_lib.num_set_capacity(h, _hptr(_host(c, np.float64, int(m), "c"))))
+
+
+def num_set_weights(h, n, w):
+    _check(_lib.num_set_weights(h, _hptr(_host(w, np.float64, int(n), "w"))))
+
+
+def num_adjoint(h, n, m, iters, checkpoint_every=50, xbar=None, objective=True):
+    """Gradients of `iters` unrolled iterations from the zero state: returns
+    (dJ/dc [m], dJ/dw [n], J) for J = xbar . x (+ sum_j U_j(x_j) if objective)."""
+    cg = np.empty(int(m))
+    wg = np.empty(int(n))
+    xb = None if xbar is None else _host(xbar, np.float64, int(n), "xbar")
+    obj = ctypes.c_double(0.0)
+    _check(_lib.num_adjoint(h, int(iters), int(checkpoint_every), _hptr(xb),
+                            1 if objective else 0, _hptr(cg), _hptr(wg), ctypes.byref(obj)))
+    return cg, wg, obj.value
 
 
 def num_get_state(h, n, m):
@@ -465,6 +484,12 @@ class Problem:
 
     def set_capacity(self, c):
         num_set_capacity(self.h, self.m, c)
+
+    def set_weights(self, w):
+        num_set_weights(self.h, self.n, w)
+
+    def adjoint(self, iters, checkpoint_every=50, xbar=None, objective=True):
+        return num_adjoint(self.h, self.n, self.m, iters, checkpoint_every, xbar, objective)
 
     def get_state(self):
         return num_get_state(self.h, self.n, self.m)

@@ -1,0 +1,224 @@
+// Reverse-mode derivative of K unrolled PMP iterations (the reduced recurrence of fused.cu,
+// Sec. III-D..G) with respect to the capacities c and the weights w, for a cotangent on
+// the final rates x_K.  The rho of every iteration is held fixed (the forward run's own
+// decisions), which makes the K-step map piecewise smooth.
+//
+// Forward iteration k (rho = rho_k):
+//   stream j:  Z'_k = a L x_{k-1} + (1-a) Z'_{k-1} - a (R' pbar_{k-1})_j
+//              S_k  = Z'_k - (R' y_{k-1})_j / rho;   x_k = clip(prox(S_k; L, w, rho))
+//   link l:    ps_k = max(zs_{k-1} - y_{k-1} / rho, -c);   pbar_k = ((R x_k)_l + ps_k) / (deg+1)
+//              zs_k = a (ps_k - pbar_k) + (1-a) zs_{k-1};   y_k = y_{k-1} + a rho pbar_k
+// Backward iteration k, given the cotangents of the state after it:
+//   link pass (per link, gathering (Abar, Bbar) of the streams of the link from the stream
+//   pass of iteration k+1): pbar_bar_k = R Abar, y_bar_k += R Bbar; then
+//     t = pbar_bar_k + a rho y_bar_k - a zs_bar_k;  ps_bar = t / (deg+1) + a zs_bar_k;
+//     Rx_bar = t / (deg+1);  zs_bar_{k-1} = (1-a) zs_bar_k + [ps_k > -c] ps_bar;
+//     y_bar_{k-1} = y_bar_k - [ps_k > -c] ps_bar / rho;  c_bar -= [ps_k = -c] ps_bar
+//   stream pass (per stream, gathering Rx_bar over its route):
+//     x_bar_k += R' Rx_bar;  S_bar = x_bar_k dx/dS;  w_bar += x_bar_k dx/dw;
+//     t = Z'_bar_k + S_bar;  x_bar_{k-1} = a L t;  Z'_bar_{k-1} = (1-a) t;
+//     Abar = -a t;  Bbar = -S_bar / rho
+// with the prox Jacobian from x_k alone: unclipped log stream, sqrt(D) = L x + w / (rho x),
+// dx/dS = x / sqrt(D), dx/dw = 1 / (rho sqrt(D)); unclipped linear stream, dx/dS = 1/L,
+// dx/dw = 1 / (rho L); a stream at a bound of its box, 0.  Only x_k and ps_k of every
+// iteration are needed; they are recomputed segment by segment from checkpoints.
+#include <cooperative_groups.h>
+#include <cuda_runtime.h>
+
+#include "pmp_device.cuh"
+#include "pmp_internal.cuh"
+#include "pmp_rows.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace pmp {
+
+namespace {
+
+constexpr int kTh = 256;
+constexpr int kGroup = 8;
+
+template <typename T>
+__global__ void __launch_bounds__(kTh) k_adj_link(AdjView<T> a, const T* __restrict__ ps_k,
+                                                 const double* __restrict__ rho_ptr) {
+    using T2 = typename Pair<T>::type;
+    auto g = cg::tiled_partition<kGroup>(cg::this_thread_block());
+    const bool leader = g.thread_rank() == 0;
+    const View<T>& v = a.v;
+    const T alpha = (T)a.alpha, rho = (T)*rho_ptr;
+    constexpr int kGroups = kTh / kGroup;
+    for (int l = blockIdx.x * kGroups + (int)(threadIdx.x / kGroup); l < v.m;
+         l += gridDim.x * kGroups) {
+        const int p0 = __ldg(v.row_ptr + l), p1 = __ldg(v.row_ptr + l + 1);
+        T sa = T(0), sb = T(0);  // R Abar, R Bbar: fixed order over the link's streams
+        for (int e = p0 + g.thread_rank(); e < p1; e += kGroup) {
+            const T2 ab = a.ab[__ldg(v.col_idx + e)];
+            sa += ab.x;
+            sb += ab.y;
+        }
+#pragma unroll
+        for (int o = kGroup / 2; o > 0; o >>= 1) {
+            sa += g.shfl_down(sa, o);
+            sb += g.shfl_down(sb, o);
+        }
+        if (!leader) continue;
+        const T yb = a.yb[l] + sb;
+        const T zsb = a.zsb[l];
+        const T deg1 = (T)(p1 - p0 + 1);
+        const T t = sa + alpha * rho * yb - alpha * zsb;
+        const T psb = t / deg1 + alpha * zsb;
+        a.Rxb[l] = t / deg1;
+        const bool open = ps_k[l] > -v.c[l];  // slack prox not at its bound
+        a.zsb[l] = (T(1) - alpha) * zsb + (open ? psb : T(0));
+        a.yb[l] = yb - (open ? psb / rho : T(0));
+        if (!open) a.cb[l] -= psb;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kTh) k_adj_stream(AdjView<T> a, const T* __restrict__ x_k,
+                                                   const double* __restrict__ rho_ptr) {
+    using T2 = typename Pair<T>::type;
+    const View<T>& v = a.v;
+    const T alpha = (T)a.alpha, rho = (T)*rho_ptr;
+    for (int j = blockIdx.x * kTh + threadIdx.x; j < v.n; j += gridDim.x * kTh) {
+        const int p = __ldg(v.col_ptr + j), pn = __ldg(v.col_ptr + j + 1);
+        T r = T(0);
+        for (int e = p; e < pn; ++e) r += a.Rxb[__ldg(v.row_idx + e)];
+        const T xbk = a.xb[j] + r;
+        const T x = x_k[j], L = (T)(pn - p), wt = v.wt[j];
+        const T lo = v.box_uniform ? v.lo_u : v.lo[j];
+        const T hi = v.box_uniform ? v.hi_u : v.hi[j];
+        T dS = T(0), dw = T(0);
+        if (x > lo && x < hi) {
+            if (wt > T(0)) {
+                const T sqD = L * x + wt / (rho * x);
+                dS = x / sqD;
+                dw = T(1) / (rho * sqD);
+            } else {
+                dS = T(1) / L;
+                dw = T(1) / (rho * L);
+            }
+        }
+        const T Sb = xbk * dS;
+        a.wb[j] += xbk * dw;
+        const T t = a.Zb[j] + Sb;
+        a.xb[j] = alpha * L * t;
+        a.Zb[j] = (T(1) - alpha) * t;
+        T2 ab;
+        ab.x = -alpha * t;
+        ab.y = -Sb / rho;
+        a.ab[j] = ab;
+    }
+}
+
+// Initial cotangents for the final rates: x_bar = xbar_in (caller order) plus, for the
+// total utility, U'(x) (w / x or w); the direct dU/dw (log x or x) starts w_bar.
+template <typename T>
+__global__ void k_adj_init(AdjView<T> a, const double* __restrict__ xbar_in, int objective) {
+    using T2 = typename Pair<T>::type;
+    const View<T>& v = a.v;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < v.n; j += gridDim.x * blockDim.x) {
+        const int o = v.perm ? v.perm[j] : j;
+        T xb = xbar_in ? (T)xbar_in[o] : T(0);
+        T wb = T(0);
+        if (objective) {
+            const T x = v.x[j], wt = v.wt[j];
+            if (wt > T(0)) {
+                xb += wt / x;
+                wb = log(x);
+            } else {
+                xb += -wt;
+                wb = x;
+            }
+        }
+        a.xb[j] = xb;
+        a.wb[j] = wb;
+        a.Zb[j] = T(0);
+        T2 z;
+        z.x = T(0);
+        z.y = T(0);
+        a.ab[j] = z;
+    }
+    for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < v.m; l += gridDim.x * blockDim.x) {
+        a.yb[l] = T(0);
+        a.zsb[l] = T(0);
+        a.Rxb[l] = T(0);
+        a.cb[l] = T(0);
+    }
+}
+
+template <typename T>
+__global__ void k_adj_export(AdjView<T> a, double* c_grad, double* w_grad) {
+    const View<T>& v = a.v;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < v.n; j += gridDim.x * blockDim.x)
+        if (w_grad) w_grad[v.perm ? v.perm[j] : j] = (double)a.wb[j];
+    for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < v.m; l += gridDim.x * blockDim.x)
+        if (c_grad) c_grad[l] = (double)a.cb[l];
+}
+
+__global__ void k_record_rho(const Ctl* ctl, double* out) { *out = ctl->rho; }
+
+template <typename T>
+__global__ void k_set_weights(View<T> v, const double* __restrict__ w) {
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < v.n; j += gridDim.x * blockDim.x) {
+        const T wj = (T)w[v.perm ? v.perm[j] : j];
+        T* wt = const_cast<T*>(v.wt);
+        wt[j] = wt[j] > T(0) ? wj : -wj;  // the utility type rides on the sign
+    }
+}
+
+int grid_for(long long count) {
+    long long b = (count + kTh - 1) / kTh;
+    return (int)(b < 1 ? 1 : (b > 8192 ? 8192 : b));
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t adjoint_init(const AdjView<T>& a, const double* xbar, int objective, cudaStream_t st) {
+    k_adj_init<T><<<grid_for(a.v.n > a.v.m ? a.v.n : a.v.m), kTh, 0, st>>>(a, xbar, objective);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t adjoint_step(const AdjView<T>& a, const T* x_k, const T* ps_k, const double* rho,
+                         cudaStream_t st) {
+    k_adj_link<T><<<grid_for((long long)a.v.m * kGroup), kTh, 0, st>>>(a, ps_k, rho);
+    k_adj_stream<T><<<grid_for(a.v.n), kTh, 0, st>>>(a, x_k, rho);
+    note_launches(2);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t adjoint_export(const AdjView<T>& a, double* c_grad, double* w_grad, cudaStream_t st) {
+    k_adj_export<T><<<grid_for(a.v.n > a.v.m ? a.v.n : a.v.m), kTh, 0, st>>>(a, c_grad, w_grad);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t record_rho(const Ctl* ctl, double* out, cudaStream_t st) {
+    k_record_rho<<<1, 1, 0, st>>>(ctl, out);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t set_weights(const View<T>& v, const double* w, cudaStream_t st) {
+    k_set_weights<T><<<grid_for(v.n), kTh, 0, st>>>(v, w);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+#define PMP_ADJ_INST(T)                                                                        \
+    template cudaError_t adjoint_init<T>(const AdjView<T>&, const double*, int, cudaStream_t); \
+    template cudaError_t adjoint_step<T>(const AdjView<T>&, const T*, const T*, const double*,  \
+                                         cudaStream_t);                                        \
+    template cudaError_t adjoint_export<T>(const AdjView<T>&, double*, double*, cudaStream_t);  \
+    template cudaError_t set_weights<T>(const View<T>&, const double*, cudaStream_t);
+PMP_ADJ_INST(float)
+PMP_ADJ_INST(double)
+#undef PMP_ADJ_INST
+
+}  // namespace pmp

@@ -160,6 +160,31 @@ cudaError_t batch_reset(Ctl* ctls, BatchGlobal* glob, int count, double rho0, do
                         double mu, double gamma, int period, int hist_len, int sched_len,
                         cudaStream_t st);
 
+// ---- adjoint (adjoint.cu) -----------------------------------------------------------------------
+template <typename T>
+struct AdjView {
+    View<T> v;
+    double alpha;
+    T* xb;                        // x_bar [n]
+    T* Zb;                        // Z'_bar [n]
+    typename Pair<T>::type* ab;   // (Abar, Bbar) per stream [n]
+    T* yb;                        // y_bar [m]
+    T* zsb;                       // zs_bar [m]
+    T* Rxb;                       // Rx_bar [m]
+    T* cb;                        // dJ/dc [m]
+    T* wb;                        // dJ/dw [n]
+};
+template <typename T>
+cudaError_t adjoint_init(const AdjView<T>& a, const double* xbar, int objective, cudaStream_t st);
+template <typename T>
+cudaError_t adjoint_step(const AdjView<T>& a, const T* x_k, const T* ps_k, const double* rho,
+                         cudaStream_t st);
+template <typename T>
+cudaError_t adjoint_export(const AdjView<T>& a, double* c_grad, double* w_grad, cudaStream_t st);
+cudaError_t record_rho(const Ctl* ctl, double* out, cudaStream_t st);
+template <typename T>
+cudaError_t set_weights(const View<T>& v, const double* w, cudaStream_t st);
+
 // ---- row kernels (rows.cu) ------------------------------------------------------------------
 cudaError_t rows_grids(int precision, int n, int m, int nchunks, int* grid_s, int* grid_l);
 template <typename T>
