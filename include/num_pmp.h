@@ -5,7 +5,8 @@
  * Problem (Sec. II, Eq. vanilla_num):   maximize  sum_j U_j(x_j)
  *                                       subject to R x <= c,  lo_j <= x_j <= hi_j,
  * with the 0/1 link-route matrix R (R_lj = 1 iff stream j uses link l), capacities c > 0,
- * and U_j(x) = w_j log x (NUM_LOG) or w_j x (NUM_LINEAR), w_j > 0.  The box is the
+ * and U_j(x) = w_j log x (NUM_LOG), w_j x (NUM_LINEAR) or -w_j / x (NUM_ALPHA2), w_j > 0.
+ * The box is the
  * "indicator of a convex set" of Sec. II; lo = 0 gives the paper's x >= 0.
  *
  * Method: the ADMM form of Sec. III-D (prox device updates, link averages, scaled price
@@ -54,6 +55,8 @@ extern "C" {
 /* ---- utility types (Sec. III-B) ------------------------------------------------------------ */
 #define NUM_LOG 0    /* U(x) = w log x, the log-utility stream */
 #define NUM_LINEAR 1 /* U(x) = w x, the linear-utility stream */
+#define NUM_ALPHA2 2 /* U(x) = -w / x, alpha = 2 fairness ("minimum potential delay", the
+                        example of Sec. II of a utility with a simple prox) */
 
 /* ---- kernel path / precision --------------------------------------------------------------- */
 #define NUM_FUSED_FP32 0 /* two fused kernels per iteration; FP32 iterates, FP64 residuals,
@@ -130,9 +133,9 @@ NUM_API void num_default_params(num_params* p);
  *   route_links  int32[nnz], nnz = route_ptr[n] < 2^31 - m; link ids in [0, m), no link
  *                twice in one route, every route nonempty (a stream has >= 1 terminal)
  *   c            double[m], capacities, finite and > 0
- *   utype        uint8[n], NUM_LOG or NUM_LINEAR
+ *   utype        uint8[n], NUM_LOG, NUM_LINEAR or NUM_ALPHA2
  *   w            double[n], weights, finite and > 0
- *   lo, hi       double[n] box of each rate, finite, lo <= hi, hi > 0 for log streams;
+ *   lo, hi       double[n] box of each rate, finite, lo <= hi, hi > 0 for log and alpha2;
  *                lo may be NULL (all zero)
  *   p            parameters (NULL = defaults)
  *   cuda_stream  cudaStream_t to order all work on (NULL = the legacy default stream)
@@ -257,7 +260,7 @@ NUM_API int num_get_kernel_times(const num_problem* h, double* ms, int64_t* laun
  * node of a replayed graph counts as one launch). */
 NUM_API int64_t num_kernel_launches(void);
 
-/* Total utility sum_j U_j(x_j) (U = w log x for utype 0, w x otherwise; Sec. II) of
+/* Total utility sum_j U_j(x_j) (U = w log x for utype 0, -w / x for 2, w x otherwise) of
  * caller DEVICE arrays x[n], utype[n], w[n], written in FP64 to the caller's DEVICE double
  * *objective; no handle, and NO ALLOCATION of any kind.  The paper has no counterpart.
  * For callers that cannot allocate device memory when they need the number (allocation

@@ -64,6 +64,8 @@ def _lib(plant=0):
             lib.oracle_prox_log.argtypes = [d, d, d, d, d, d]
             lib.oracle_prox_linear.restype = d
             lib.oracle_prox_linear.argtypes = [d, d, d, d, d, d]
+            lib.oracle_prox_alpha2.restype = d
+            lib.oracle_prox_alpha2.argtypes = [d, d, d, d, d, d]
             lib.oracle_prox_slack.restype = d
             lib.oracle_prox_slack.argtypes = [d, d]
             lib.oracle_solve.restype = ctypes.c_int
@@ -81,6 +83,10 @@ def prox_log(S, L, w, rho, lo, hi, plant=0):
 
 def prox_linear(S, L, w, rho, lo, hi, plant=0):
     return _lib(plant).oracle_prox_linear(S, L, w, rho, lo, hi)
+
+
+def prox_alpha2(S, L, w, rho, lo, hi, plant=0):
+    return _lib(plant).oracle_prox_alpha2(S, L, w, rho, lo, hi)
 
 
 def prox_slack(zeta, c, plant=0):

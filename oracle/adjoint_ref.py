@@ -19,6 +19,24 @@ def _segment_sum(values, index, size):
     return out.index_add(0, index, values)
 
 
+def _alpha2_root(S, L, w, rho):
+    """Positive root of rho L x^3 - rho S x^2 - w (U = -w / x): bisection without
+    gradient, then one Newton step with it, whose derivative at the root is the implicit
+    derivative -f_theta / f_x."""
+    with torch.no_grad():
+        a = torch.zeros_like(S)
+        b = torch.clamp(S, min=0.0) / L + torch.pow(w / (rho * L), 1.0 / 3.0)
+        for _ in range(200):
+            mid = 0.5 * (a + b)
+            f = rho * L * mid ** 3 - rho * S * mid ** 2 - w
+            b = torch.where(f > 0, mid, b)
+            a = torch.where(f > 0, a, mid)
+        x0 = 0.5 * (a + b)
+    f = rho * L * x0 ** 3 - rho * S * x0 ** 2 - w
+    fx = 3.0 * rho * L * x0 ** 2 - 2.0 * rho * S * x0
+    return x0 - f / fx
+
+
 def unrolled_x(inst, iters, c, w, decisions, rho0=1.0, alpha=1.6, period=50):
     """x after `iters` literal PMP iterations from zero; c [m], w [n] float64 tensors (may
     require grad); decisions = the rho decision (+1, 0, -1) at each update point."""
@@ -33,6 +51,7 @@ def unrolled_x(inst, iters, c, w, decisions, rho0=1.0, alpha=1.6, period=50):
     L = torch.as_tensor(lengths, dtype=torch.float64)
     cnt = _segment_sum(torch.ones(J, dtype=torch.float64), link_of, m)
     is_log = torch.as_tensor(np.asarray(inst["utype"]) == 0)
+    is_a2 = torch.as_tensor(np.asarray(inst["utype"]) == 2)
     lo = torch.as_tensor(np.asarray(inst["lo"], np.float64))
     hi = torch.as_tensor(np.asarray(inst["hi"], np.float64))
     p = torch.zeros(J, dtype=torch.float64)
@@ -48,7 +67,8 @@ def unrolled_x(inst, iters, c, w, decisions, rho0=1.0, alpha=1.6, period=50):
         sq = torch.sqrt(D)
         x_log = torch.where(S >= 0, (S + sq) / (2.0 * L), (2.0 * w / rho) / (sq - S))
         x_lin = (S + w / rho) / L
-        x = torch.clamp(torch.where(is_log, x_log, x_lin), min=lo, max=hi)
+        x_a2 = _alpha2_root(S, L, w, rho)
+        x = torch.clamp(torch.where(is_log, x_log, torch.where(is_a2, x_a2, x_lin)), min=lo, max=hi)
         p = torch.cat([x[stream_of], torch.maximum(zeta[nnz:], -c)])
         pplus = alpha * p + (1.0 - alpha) * z
         v = pplus + u
@@ -72,8 +92,11 @@ def gradients(inst, iters, decisions, xbar=None, objective=True, **kw):
     if xbar is not None:
         J = J + torch.dot(torch.as_tensor(np.asarray(xbar, np.float64)), x)
     if objective:
-        is_log = torch.as_tensor(np.asarray(inst["utype"]) == 0)
-        J = J + torch.where(is_log, w * torch.log(torch.where(is_log, x, torch.ones_like(x))),
-                            w * x).sum()
+        t = np.asarray(inst["utype"])
+        is_log = torch.as_tensor(t == 0)
+        is_a2 = torch.as_tensor(t == 2)
+        safe = torch.where(is_log | is_a2, x, torch.ones_like(x))
+        J = J + torch.where(is_log, w * torch.log(safe),
+                            torch.where(is_a2, -w / safe, w * x)).sum()
     J.backward()
     return c.grad.numpy().copy(), w.grad.numpy().copy(), float(J.detach())

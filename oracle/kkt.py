@@ -12,6 +12,7 @@ from __future__ import annotations
 import numpy as np
 
 LOG = 0
+ALPHA2 = 2
 
 
 def link_loads(inst, x):
@@ -28,12 +29,15 @@ def path_prices(inst, lam):
 
 
 def utility(inst, x):
-    """sum_j U_j(x_j) with U = w log x (type 0) or w x (type 1), in FP64."""
+    """sum_j U_j(x_j) with U = w log x (type 0), w x (type 1) or -w / x (type 2, alpha = 2
+    fairness), in FP64."""
     x = np.asarray(x, dtype=np.float64)
     w = inst["w"]
-    is_log = inst["utype"] == LOG
+    t = inst["utype"]
     with np.errstate(divide="ignore"):
-        return float(np.sum(np.where(is_log, w * np.log(np.where(is_log, x, 1.0)), w * x)))
+        xs = np.where(t == 1, 1.0, x)
+        return float(np.sum(np.where(t == LOG, w * np.log(xs),
+                                     np.where(t == ALPHA2, -w / xs, w * x))))
 
 
 def dual_value(inst, lam):
@@ -41,15 +45,20 @@ def dual_value(inst, lam):
     lam = np.maximum(np.asarray(lam, dtype=np.float64), 0.0)
     pi = path_prices(inst, lam)
     w, lo, hi = inst["w"], inst["lo"], inst["hi"]
-    is_log = inst["utype"] == LOG
+    t = inst["utype"]
+    is_log = t == LOG
+    is_a2 = t == ALPHA2
     with np.errstate(divide="ignore", invalid="ignore"):
-        xl = np.where(pi > 0, w / np.where(pi > 0, pi, 1.0), hi)
+        xl = np.where(pi > 0, w / np.where(pi > 0, pi, 1.0), hi)      # argmax w log x - pi x
+        xa = np.where(pi > 0, np.sqrt(w / np.where(pi > 0, pi, 1.0)), hi)  # of -w/x - pi x
     xl = np.clip(xl, lo, hi)
+    xa = np.clip(xa, lo, hi)
     with np.errstate(divide="ignore"):
         vlog = w * np.log(np.where(is_log, xl, 1.0)) - pi * xl
+        va2 = -w / np.where(is_a2, xa, 1.0) - pi * xa
     xlin = np.where(w > pi, hi, lo)
     vlin = (w - pi) * xlin
-    return float(np.sum(np.where(is_log, vlog, vlin)) + lam @ inst["c"])
+    return float(np.sum(np.where(is_log, vlog, np.where(is_a2, va2, vlin))) + lam @ inst["c"])
 
 
 def diagnostics(inst, x, lam, bound_tol=1e-9):
@@ -69,12 +78,13 @@ def diagnostics(inst, x, lam, bound_tol=1e-9):
     w, lo, hi = inst["w"], inst["lo"], inst["hi"]
     rx = link_loads(inst, x)
     pi = path_prices(inst, np.maximum(lam, 0.0))
-    is_log = inst["utype"] == LOG
+    t = inst["utype"]
     span = np.maximum(hi - lo, 1e-300)
     at_lo = x <= lo + bound_tol * span
     at_hi = x >= hi - bound_tol * span
     with np.errstate(divide="ignore", invalid="ignore"):
-        grad = np.where(is_log, w / np.where(x > 0, x, np.nan), w)   # U'(x)
+        xp = np.where(x > 0, x, np.nan)
+        grad = np.where(t == LOG, w / xp, np.where(t == ALPHA2, w / (xp * xp), w))   # U'(x)
     # stationarity of max U(x) - pi x over the box: U' = pi inside, U' <= pi at lo, >= pi at hi
     scale = np.maximum(np.abs(grad), 1e-300)
     viol = np.where(at_lo & ~at_hi, np.maximum(grad - pi, 0.0),

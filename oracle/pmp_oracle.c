@@ -97,6 +97,30 @@ double oracle_prox_linear(double S, double L, double w, double rho, double lo, d
     return clip(x, lo, hi);
 }
 
+/* argmin_x  w / x + (rho/2) sum_t (x - zeta_t)^2 over x > 0 and the box: the utility
+ * U = -w / x of alpha = 2 fairness ("minimum potential delay", named in Sec. II as a
+ * utility with a simple prox, Sec. III-B).  The stationarity condition is the cubic
+ * f(x) = rho L x^3 - rho S x^2 - w = 0, which has exactly one positive root; it lies in
+ * (0, max(S, 0) / L + cbrt(w / (rho L))] (f is negative at 0 and non-negative at the right
+ * end), and is found here by bisection down to the last representable bracket. */
+double oracle_prox_alpha2(double S, double L, double w, double rho, double lo, double hi) {
+    double a = 0.0, b = (S > 0.0 ? S / L : 0.0) + cbrt(w / (rho * L));
+    for (int it = 0; it < 400; ++it) {
+        const double mid = 0.5 * (a + b);
+        if (mid <= a || mid >= b) break;
+#if ORACLE_PLANT == 14
+        const double f = rho * L * mid * mid * mid + rho * S * mid * mid - w;
+#else
+        const double f = rho * L * mid * mid * mid - rho * S * mid * mid - w;
+#endif
+        if (f > 0.0)
+            b = mid;
+        else
+            a = mid;
+    }
+    return clip(0.5 * (a + b), lo, hi);
+}
+
 /* argmin_p  I{p + c >= 0} + (rho/2)(p - zeta)^2 = max(zeta, -c). */
 double oracle_prox_slack(double zeta, double c) {
 #if ORACLE_PLANT == 3
@@ -110,7 +134,8 @@ double oracle_prox_slack(double zeta, double c) {
 
 /*
  * Inputs follow the problem statement of Sec. II: R given by its routes (CSC, stream-major),
- * capacities c, utility type (0 log, 1 linear), weight w and box [lo, hi] per stream.
+ * capacities c, utility type (0 log, 1 linear, 2 alpha = 2 fairness), weight w and box
+ * [lo, hi] per stream.
  * rho_replay (optional, length rho_replay_len) forces the decision of the i-th rho update
  * (-1 divide by gamma, 0 keep, +1 multiply by gamma) instead of Eq. (rho-update).
  *
@@ -176,8 +201,9 @@ int oracle_solve(int64_t n, int64_t m, const int64_t* route_ptr, const int32_t* 
             double S = 0.0;
             for (int64_t t = route_ptr[s]; t < route_ptr[s + 1]; ++t) S += z[t] - u[t];
             double L = (double)(route_ptr[s + 1] - route_ptr[s]);
-            double xs = utype[s] == 0 ? oracle_prox_log(S, L, w[s], rho, lo[s], hi[s])
-                                      : oracle_prox_linear(S, L, w[s], rho, lo[s], hi[s]);
+            double xs = utype[s] == 0   ? oracle_prox_log(S, L, w[s], rho, lo[s], hi[s])
+                        : utype[s] == 2 ? oracle_prox_alpha2(S, L, w[s], rho, lo[s], hi[s])
+                                        : oracle_prox_linear(S, L, w[s], rho, lo[s], hi[s]);
             for (int64_t t = route_ptr[s]; t < route_ptr[s + 1]; ++t) p[t] = xs;
         }
         for (int64_t l = 0; l < m; ++l) {

@@ -48,8 +48,12 @@ def solve_x(problem, c, w, iters, checkpoint_every=50):
 
 
 def total_utility(problem, utype, c, w, iters, checkpoint_every=50):
-    """sum_j U_j(x_j) (w log x for utype 0, w x otherwise) at the x of `iters` iterations."""
+    """sum_j U_j(x_j) (w log x for utype 0, w x for 1, -w / x for 2) at the x of `iters`
+    iterations."""
     x = solve_x(problem, c, w, iters, checkpoint_every)
-    is_log = torch.as_tensor(np.asarray(utype) == 0, device=x.device)
-    return torch.where(is_log, w * torch.log(torch.where(is_log, x, torch.ones_like(x))),
-                       w * x).sum()
+    t = np.asarray(utype)
+    is_log = torch.as_tensor(t == 0, device=x.device)
+    is_a2 = torch.as_tensor(t == 2, device=x.device)
+    safe = torch.where(is_log | is_a2, x, torch.ones_like(x))
+    return torch.where(is_log, w * torch.log(safe),
+                       torch.where(is_a2, -w / safe, w * x)).sum()

@@ -24,6 +24,7 @@ NUM_ERR_STATE = -5
 
 NUM_LOG = 0
 NUM_LINEAR = 1
+NUM_ALPHA2 = 2
 
 NUM_FUSED_FP32 = 0
 NUM_FUSED_FP64 = 1

@@ -91,7 +91,13 @@ __global__ void __launch_bounds__(kTh) k_adj_stream(AdjView<T> a, const T* __res
         const T hi = v.box_uniform ? v.hi_u : v.hi[j];
         T dS = T(0), dw = T(0);
         if (x > lo && x < hi) {
-            if (wt > T(0)) {
+            if (v.ut && v.ut[j] == 2) {
+                // rho L x^3 - rho S x^2 - w = 0 with S = L x - w / (rho x^2):
+                // f_x = rho L x^2 + 2 w / x, dx/dS = rho x^2 / f_x, dx/dw = 1 / f_x
+                const T fx = rho * L * x * x + T(2) * wt / x;
+                dS = rho * x * x / fx;
+                dw = T(1) / fx;
+            } else if (wt > T(0)) {
                 const T sqD = L * x + wt / (rho * x);
                 dS = x / sqD;
                 dw = T(1) / (rho * sqD);
@@ -124,7 +130,10 @@ __global__ void k_adj_init(AdjView<T> a, const double* __restrict__ xbar_in, int
         T wb = T(0);
         if (objective) {
             const T x = v.x[j], wt = v.wt[j];
-            if (wt > T(0)) {
+            if (v.ut && v.ut[j] == 2) {
+                xb += wt / (x * x);  // U = -w / x
+                wb = -T(1) / x;
+            } else if (wt > T(0)) {
                 xb += wt / x;
                 wb = log(x);
             } else {

@@ -67,6 +67,7 @@ struct num_problem {
     int ntiles_s = 0, ntiles_l = 0, tile_s = 0, tile_l = 0, grid_s = 0, grid_l = 0;
     int sched_kind = NUM_SCHEDULE_ROWS;  // fused paths: row kernels or merge-path tiles
     int* perm = nullptr;                 // caller's index of the stream at each position
+    uint8_t* ut = nullptr;               // utility types, only if some stream has U = -w / x
     int4* chunks = nullptr;              // row kernels: chunks of the long links
     int nchunks = 0;
     int narrive_l = 0;                   // entries of arrive_l
@@ -196,6 +197,7 @@ View<T> make_view(const num_problem* h) {
     v.chunks = h->chunks;
     v.nchunks = h->nchunks;
     v.perm = h->perm;
+    v.ut = h->ut;
     v.ctl = h->ctl;
     v.hist = h->hist;
     v.sched = h->sched;
@@ -312,8 +314,8 @@ std::string describe_bits(int bits) {
     add(pmp::VB_DUPLICATE, "a link appears twice in one route");
     add(pmp::VB_CAPACITY, "a capacity is not finite and > 0");
     add(pmp::VB_WEIGHT, "a weight is not finite and > 0");
-    add(pmp::VB_UTYPE, "a utility type is not NUM_LOG or NUM_LINEAR");
-    add(pmp::VB_BOX, "a box is not finite with lo <= hi (and hi > 0 for log utility)");
+    add(pmp::VB_UTYPE, "a utility type is not NUM_LOG, NUM_LINEAR or NUM_ALPHA2");
+    add(pmp::VB_BOX, "a box is not finite with lo <= hi (and hi > 0 for log and alpha = 2)");
     add(pmp::VB_BLOCKS, "a route uses a link of another instance of the batch");
     return s;
 }
@@ -534,11 +536,12 @@ int create_impl(num_problem** out, int64_t n, int64_t m, const int64_t* route_pt
         CK(cudaMemcpyAsync(d_loff, batch->link_off, 8 * ((size_t)batch->count + 1),
                            cudaMemcpyHostToDevice, st), "copy offsets");
     }
-    int err_bits = 0;
+    int err_bits = 0, flags[2] = {0, 0};
     unsigned long long box[4];
-    CK(cudaMemcpyAsync(&err_bits, d_err, sizeof(int), cudaMemcpyDeviceToHost, st), "read flags");
+    CK(cudaMemcpyAsync(flags, d_err, sizeof(flags), cudaMemcpyDeviceToHost, st), "read flags");
     CK(cudaMemcpyAsync(box, d_box, sizeof(box), cudaMemcpyDeviceToHost, st), "read box");
     CK(cudaStreamSynchronize(st), "validation");
+    err_bits = flags[0];
     if (!err_bits && batch) {
         CK(pmp::check_blocks(batch->count, d_soff, d_loff, n, route_ptr, route_links, d_err, st),
            "checking the instance blocks");
@@ -567,17 +570,24 @@ int create_impl(num_problem** out, int64_t n, int64_t m, const int64_t* route_pt
     const double lmin = pmp::ordered_key_to_double(box[0]), lmax = pmp::ordered_key_to_double(box[1]);
     const double hmin = pmp::ordered_key_to_double(box[2]), hmax = pmp::ordered_key_to_double(box[3]);
     h->box_uniform = (lmin == lmax && hmin == hmax) ? 1 : 0;
+    if (flags[1]) {  // some stream has U = -w / x: keep the types on the device
+        h->ut = (uint8_t*)dev_alloc(h, N);
+        if (!h->ut) {
+            destroy_handle(h);
+            return fail(NUM_ERR_OOM, "device allocation failed");
+        }
+    }
     h->lo_u = lmin;
     h->hi_u = hmin;
     if (fp32)
         CK(pmp::convert_params<float>((int)n, (int)m, c, utype, w, lo, hi, h->perm,
                                       (float*)h->c, (float*)h->wt, (float*)h->lo, (float*)h->hi,
-                                      st),
+                                      st, h->ut),
            "converting parameters");
     else
         CK(pmp::convert_params<double>((int)n, (int)m, c, utype, w, lo, hi, h->perm,
                                        (double*)h->c, (double*)h->wt, (double*)h->lo,
-                                       (double*)h->hi, st),
+                                       (double*)h->hi, st, h->ut),
            "converting parameters");
     if (tiles) {
         CK(pmp::build_tiles(h->col_ptr, (int)n, h->Js, h->tile_s, h->ntiles_s, h->tiles_s, st),

@@ -131,7 +131,10 @@ __global__ void __launch_bounds__(kTh) k_export_batch(BatchView<T> b, double* x_
             const double xj = (double)v.x[j];
             const double wt = (double)v.wt[j];
             if (x_out) x_out[v.perm ? v.perm[j] : j] = xj;
-            obj += wt > 0.0 ? wt * log(xj) : -wt * xj;
+            if (v.ut && v.ut[j] == 2)
+                obj += -wt / xj;
+            else
+                obj += wt > 0.0 ? wt * log(xj) : -wt * xj;
         }
         const double s = block_sum(obj, red);
         if (threadIdx.x == 0) part[it] = s;

@@ -114,7 +114,7 @@ struct StreamPolicy {
         const T S = Zn - sum.y * inv_rho;
         const T lo = v.box_uniform ? v.lo_u : __ldg(v.lo + j);
         const T hi = v.box_uniform ? v.hi_u : __ldg(v.hi + j);
-        const T xn = stream_prox<T>(S, Lf, wt, inv_rho, lo, hi);
+        const T xn = stream_prox<T>(S, Lf, wt, inv_rho, lo, hi, v.ut && v.ut[j] == 2);
         v.Z[j] = Zn;
         v.x[j] = xn;
         const T dx = xn - xo;

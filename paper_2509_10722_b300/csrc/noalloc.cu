@@ -50,7 +50,8 @@ k_noalloc_partials(long long n, const double* __restrict__ x, const uint8_t* __r
         const long long j = base + (long long)k * kThreads + threadIdx.x;
         if (j < n) {
             const double xj = x[j];
-            s += utype[j] == 0 ? w[j] * log(xj) : w[j] * xj;  // U_j of Sec. II
+            const uint8_t t = utype[j];
+            s += t == 0 ? w[j] * log(xj) : (t == 2 ? -w[j] / xj : w[j] * xj);  // U_j, Sec. II
         }
     }
     s = pmp::block_sum(s, red);

@@ -35,7 +35,7 @@ __global__ void k_validate_streams(int n, const int64_t* __restrict__ route_ptr,
                                    const double* __restrict__ w, const double* __restrict__ lo,
                                    const double* __restrict__ hi, int* err,
                                    unsigned long long* box) {
-    int bits = 0;
+    int bits = 0, alpha2 = 0;
     unsigned long long lo_min = ~0ull, lo_max = 0ull, hi_min = ~0ull, hi_max = 0ull;
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
         const int64_t p0 = route_ptr[j], p1 = route_ptr[j + 1];
@@ -43,9 +43,10 @@ __global__ void k_validate_streams(int n, const int64_t* __restrict__ route_ptr,
         const double wj = w[j];
         if (!(wj > 0.0) || !isfinite(wj)) bits |= VB_WEIGHT;
         const uint8_t t = utype[j];
-        if (t > 1) bits |= VB_UTYPE;
+        if (t > 2) bits |= VB_UTYPE;
+        if (t == 2) alpha2 = 1;
         const double l = lo ? lo[j] : 0.0, h = hi[j];
-        if (!isfinite(l) || !isfinite(h) || l > h || (t == 0 && !(h > 0.0))) bits |= VB_BOX;
+        if (!isfinite(l) || !isfinite(h) || l > h || (t != 1 && !(h > 0.0))) bits |= VB_BOX;
         const unsigned long long kl = ordered_key(l), kh = ordered_key(h);
         lo_min = kl < lo_min ? kl : lo_min;
         lo_max = kl > lo_max ? kl : lo_max;
@@ -53,6 +54,7 @@ __global__ void k_validate_streams(int n, const int64_t* __restrict__ route_ptr,
         hi_max = kh > hi_max ? kh : hi_max;
     }
     if (bits) atomicOr(err, bits);
+    if (alpha2) atomicOr(err + 1, 1);  // some stream has U = -w / x
     atomicMin(box + 0, lo_min);
     atomicMax(box + 1, lo_max);
     atomicMin(box + 2, hi_min);
@@ -321,12 +323,14 @@ template <typename T>
 __global__ void k_convert(int n, int m, const double* __restrict__ c,
                           const uint8_t* __restrict__ utype, const double* __restrict__ w,
                           const double* __restrict__ lo, const double* __restrict__ hi,
-                          const int* __restrict__ perm, T* c_t, T* wt_t, T* lo_t, T* hi_t) {
+                          const int* __restrict__ perm, T* c_t, T* wt_t, T* lo_t, T* hi_t,
+                          uint8_t* ut_out) {
     const int stride = gridDim.x * blockDim.x;
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += stride) {
         const int o = perm ? perm[j] : j;  // original index of the stream at position j
         const T wj = (T)w[o];
-        wt_t[j] = utype[o] == 0 ? wj : -wj;
+        wt_t[j] = utype[o] == 1 ? -wj : wj;  // log and alpha = 2: +w; linear: -w
+        if (ut_out) ut_out[j] = utype[o];
         if (lo_t) lo_t[j] = lo ? (T)lo[o] : T(0);
         if (hi_t) hi_t[j] = (T)hi[o];
     }
@@ -367,7 +371,10 @@ k_export(View<T> v, double* x_out, double* y_out, double* part) {
         const double xj = (double)v.x[j];
         const double wt = (double)v.wt[j];
         if (x_out) x_out[v.perm ? v.perm[j] : j] = xj;  // back to the caller's stream order
-        obj += wt > 0.0 ? wt * log(xj) : -wt * xj;  // U_j(x_j), Sec. II
+        if (v.ut && v.ut[j] == 2)
+            obj += -wt / xj;  // U_j(x_j), Sec. II
+        else
+            obj += wt > 0.0 ? wt * log(xj) : -wt * xj;
     }
     if (y_out) {
         for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < v.m; l += stride)
@@ -594,20 +601,21 @@ cudaError_t fill_chunks(const int* row_ptr, int m, const int* offs, int4* chunks
 template <typename T>
 cudaError_t convert_params(int n, int m, const double* c, const uint8_t* utype,
                            const double* w, const double* lo, const double* hi, const int* perm,
-                           T* c_t, T* wt_t, T* lo_t, T* hi_t, cudaStream_t st) {
+                           T* c_t, T* wt_t, T* lo_t, T* hi_t, cudaStream_t st,
+                           uint8_t* ut_out) {
     k_convert<T><<<blocks_for(n > m ? n : m, kThreads, 65535), kThreads, 0, st>>>(
-        n, m, c, utype, w, lo, hi, perm, c_t, wt_t, lo_t, hi_t);
+        n, m, c, utype, w, lo, hi, perm, c_t, wt_t, lo_t, hi_t, ut_out);
     note_launches(1);
     return cudaGetLastError();
 }
 template cudaError_t convert_params<float>(int, int, const double*, const uint8_t*,
                                            const double*, const double*, const double*,
                                            const int*, float*, float*, float*, float*,
-                                           cudaStream_t);
+                                           cudaStream_t, uint8_t*);
 template cudaError_t convert_params<double>(int, int, const double*, const uint8_t*,
                                             const double*, const double*, const double*,
                                             const int*, double*, double*, double*, double*,
-                                            cudaStream_t);
+                                            cudaStream_t, uint8_t*);
 
 int export_partial_blocks(int n) { return blocks_for(n, kExportThreads, 1024); }
 

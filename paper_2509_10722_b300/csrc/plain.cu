@@ -42,7 +42,8 @@ __global__ void k_plain_stream(View<double> v) {
         const double S = Zn - v.B[j] * inv_rho;
         const double lo = v.box_uniform ? v.lo_u : v.lo[j];
         const double hi = v.box_uniform ? v.hi_u : v.hi[j];
-        const double xn = stream_prox<double>(S, L, v.wt[j], inv_rho, lo, hi);
+        const double xn = stream_prox<double>(S, L, v.wt[j], inv_rho, lo, hi,
+                                              v.ut && v.ut[j] == 2);
         v.Z[j] = Zn;
         v.x[j] = xn;
         v.tS[j] = L * (xn - xo) * (xn - xo);

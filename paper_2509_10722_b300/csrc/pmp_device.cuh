@@ -98,11 +98,31 @@ __device__ __forceinline__ void finalize_iteration(Ctl* ctl, double r2, double s
 // Stream prox: the minimizer over [lo, hi] of -U(x) + (rho/2) sum_t (x - zeta_t)^2, which
 // depends on zeta only through S = sum_t zeta_t.  wt > 0: U = wt log x, the positive root
 // of rho L x^2 - rho S x - wt = 0 (evaluated without cancellation for S < 0); wt < 0:
-// U = |wt| x, x = (S + |wt| / rho) / L.  inv_rho = 1 / rho.
+// U = |wt| x, x = (S + |wt| / rho) / L; alpha2: U = -wt / x (alpha = 2 fairness), the one
+// positive root of L x^3 - S x^2 - wt / rho = 0.  inv_rho = 1 / rho.
 template <typename T>
-__device__ __forceinline__ T stream_prox(T S, T L, T wt, T inv_rho, T lo, T hi) {
+__device__ __forceinline__ T alpha2_root(T S, T L, T c0) {
+    // Newton from the right end of the bracket (0, max(S, 0)/L + cbrt(c0 / L)]: f is convex
+    // and increasing to the right of the root, so the iterates decrease monotonically to
+    // it; stop when they stop decreasing (at most 64 steps)
+    T x = (S > T(0) ? S / L : T(0)) + cbrt(c0 / L);
+    for (int it = 0; it < 64; ++it) {
+        const T f = (L * x - S) * x * x - c0;
+        const T fp = (T(3) * L * x - T(2) * S) * x;
+        const T xn = x - f / fp;
+        if (!(xn < x)) break;
+        x = xn;
+    }
+    return x;
+}
+
+template <typename T>
+__device__ __forceinline__ T stream_prox(T S, T L, T wt, T inv_rho, T lo, T hi,
+                                         bool alpha2 = false) {
     T xn;
-    if (wt > T(0)) {
+    if (alpha2) {
+        xn = alpha2_root<T>(S, L, wt * inv_rho);
+    } else if (wt > T(0)) {
         const T wr = wt * inv_rho;
         const T D = S * S + T(4) * wr * L;
         const T sq = sqrt(D);

@@ -85,6 +85,7 @@ struct View {
     const int4* chunks;         // row kernels: (link, first entry, end entry, first chunk)
     int nchunks;
     const int* perm;            // caller's index of the stream at each position (or NULL)
+    const uint8_t* ut;          // utility type per stream, only when some stream has type 2
     Ctl* ctl;
     double* hist;
     const signed char* sched;
@@ -258,7 +259,8 @@ cudaError_t build_tiles(const int* ptr, int nrows, int J, int tile, int ntiles, 
 template <typename T>
 cudaError_t convert_params(int n, int m, const double* c, const uint8_t* utype,
                            const double* w, const double* lo, const double* hi, const int* perm,
-                           T* c_t, T* wt_t, T* lo_t, T* hi_t, cudaStream_t st);
+                           T* c_t, T* wt_t, T* lo_t, T* hi_t, cudaStream_t st,
+                           uint8_t* ut_out = nullptr);
 double ordered_key_to_double(unsigned long long k);
 // x (T) -> double copies; objective partials and its FP64 reduction into ctl->objective.
 template <typename T>

@@ -58,7 +58,7 @@ __device__ __forceinline__ void stream_epilogue(const View<T>& v, int j, typenam
                                                 T inv_rho, Acc<T>& acc) {
     const T Zn = alpha * L * xo + (T(1) - alpha) * Zo - alpha * sum.x;
     const T S = Zn - sum.y * inv_rho;
-    const T xn = stream_prox<T>(S, L, wt, inv_rho, lo, hi);
+    const T xn = stream_prox<T>(S, L, wt, inv_rho, lo, hi, v.ut && v.ut[j] == 2);
     v.Z[j] = Zn;
     v.x[j] = xn;
     const T dx = xn - xo;

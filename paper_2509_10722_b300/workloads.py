@@ -23,6 +23,7 @@ import numpy as np
 
 LOG = 0
 LINEAR = 1
+ALPHA2 = 2  # U = -w / x, alpha = 2 fairness (minimum potential delay)
 
 
 def _dedupe_routes(rng, route_ptr, links, draw, max_rounds=10_000):
@@ -93,12 +94,13 @@ def _zipf_sampler(rng, m, s):
 
 def random_instance(n, m, len_lo, len_hi, *, seed=0, link_dist="uniform", zipf_s=1.1,
                     c_lo=1.0, c_hi=10.0, c_scale=1.0, frac_log=0.5, w_dist="uniform",
-                    w_lo=0.5, w_hi=2.0, box=(0.0, 20.0), degrade=None):
+                    w_lo=0.5, w_hi=2.0, box=(0.0, 20.0), degrade=None, frac_alpha2=0.0):
     """Draw one NUM instance.
 
     len_lo..len_hi    route length, uniform over the integers in that range (capped at m)
     link_dist         "uniform" (links uniform without replacement) or "zipf"
     frac_log          fraction of streams with log utility (exact count, random positions)
+    frac_alpha2       fraction with U = -w / x (alpha = 2 fairness), taken from the others
     w_dist            "uniform" (U[w_lo, w_hi]) or "lognormal" (LogNormal(0, 0.5))
     box               (lo, hi) applied to every stream, or a callable(rng, n) -> (lo, hi) arrays
     degrade           None or (lo, hi): capacities multiplied by a per-link U[lo, hi] factor
@@ -126,7 +128,11 @@ def random_instance(n, m, len_lo, len_hi, *, seed=0, link_dist="uniform", zipf_s
         c = c * rng.uniform(degrade[0], degrade[1], size=m)
     n_log = int(round(frac_log * n))
     utype = np.full(n, LINEAR, dtype=np.uint8)
-    utype[rng.permutation(n)[:n_log]] = LOG
+    order = rng.permutation(n)
+    utype[order[:n_log]] = LOG
+    if frac_alpha2 > 0.0:
+        n_a2 = min(int(round(frac_alpha2 * n)), n - n_log)
+        utype[order[n_log:n_log + n_a2]] = ALPHA2
     if w_dist == "uniform":
         w = rng.uniform(w_lo, w_hi, size=n)
     elif w_dist == "lognormal":

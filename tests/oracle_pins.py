@@ -104,6 +104,21 @@ def pin_prox_linear(plant=0):
     return worst < 1e-9, f"max rel err {worst:.3e}"
 
 
+def pin_prox_alpha2(plant=0):
+    """prox of U = -w / x: the positive root of rho L x^3 - rho S x^2 - w (numpy.roots, a
+    library eigenvalue solve of the companion matrix), clipped to the box."""
+    rng = np.random.default_rng(9)
+    worst = 0.0
+    for S, L, w, rho, lo, hi in _prox_cases(rng, 300):
+        r = np.roots([rho * L, -rho * S, 0.0, -w])
+        r = r[np.abs(r.imag) <= 1e-9 * np.abs(r)].real
+        root = float(r[r > 0].max())
+        ref = min(max(root, lo), hi)
+        got = oracle.prox_alpha2(S, L, w, rho, lo, hi, plant=plant)
+        worst = max(worst, abs(got - ref) / max(abs(ref), 1e-300))
+    return worst < 1e-8, f"max rel err {worst:.3e}"
+
+
 def pin_prox_slack(plant=0):
     """prox of the indicator of {p + c >= 0}: the closest feasible point, found here by
     minimizing (p - zeta)^2 over a dense grid of feasible points."""
@@ -152,6 +167,29 @@ def pin_linear_single_link(plant=0):
     r = _solve(inst, plant)
     ok = _close(r["x"], [0.0, 5.0], 1e-6, 1e-7) and _close(r["lam"], [2.0], 1e-6)
     return ok, f"x={r['x']} lam={r['lam']}"
+
+
+def pin_alpha2_single_link(plant=0):
+    """alpha = 2 fairness on one link: w_j / x_j^2 = lambda gives x_j = sqrt(w_j) c / sum
+    sqrt(w), lambda = (sum sqrt(w) / c)^2."""
+    w = np.array([1.0, 4.0, 0.25, 2.0])
+    c = 3.0
+    inst = _inst([[0]] * 4, 1, [c], w, [2] * 4)
+    r = _solve(inst, plant)
+    sw = np.sqrt(w)
+    ok = _close(r["x"], sw * c / sw.sum(), 1e-7) and _close(r["lam"], [(sw.sum() / c) ** 2], 1e-7)
+    return ok, f"x={r['x']} lam={r['lam']}"
+
+
+def pin_alpha2_kkt(plant=0):
+    """A random instance mixing all three utilities satisfies the KKT conditions."""
+    inst = W.random_instance(200, 60, 1, 5, seed=44, frac_log=0.4, frac_alpha2=0.3,
+                             box=(0.0, 20.0))
+    r = _solve(inst, plant, eps=1e-11)
+    d = kkt.diagnostics(inst, r["x"], r["lam"])
+    ok = (r["converged"] and d["feas"] < 1e-7 and d["comp"] < 1e-7 and d["stat"] < 1e-6
+          and abs(d["gap"]) < 1e-7)
+    return ok, str(d)
 
 
 def pin_four_stream(plant=0):
@@ -404,7 +442,8 @@ def pin_identities(plant=0):
     return r["identity_violation"] < 1e-11, f"violation {r['identity_violation']:.3e}"
 
 
-PINS = [pin_prox_log, pin_prox_linear, pin_prox_slack, pin_single_link,
+PINS = [pin_prox_log, pin_prox_linear, pin_prox_alpha2, pin_prox_slack, pin_single_link,
+        pin_alpha2_single_link, pin_alpha2_kkt,
         pin_single_link_waterfill, pin_linear_single_link, pin_four_stream, pin_line_network,
         pin_dual_solver, pin_lp, pin_mixed_slsqp, pin_bruteforce, pin_kkt_random,
         pin_large_rho_start, pin_capacity_switch, pin_residuals, pin_stop_rule, pin_rho_rule,
@@ -425,4 +464,5 @@ PLANTS = {
     11: "stopping tolerance without sqrt(J)",
     12: "z projection averages over traffic terminals only",
     13: "log prox not clipped to the box",
+    14: "alpha = 2 prox with the wrong sign of the S x^2 term",
 }

@@ -17,6 +17,12 @@ def small():
 
 
 @pytest.fixture(scope="module")
+def small_a2():
+    return W.random_instance(300, 60, 1, 6, seed=42, frac_log=0.4, frac_alpha2=0.4,
+                             box=(0.0, 20.0))
+
+
+@pytest.fixture(scope="module")
 def slice_c5():
     # a 10^3-stream slice of the differentiation recipe: routes of 2..8 links, log
     # utilities, w ~ U[0.5, 2], box [0, 20], m = n / 10
@@ -38,6 +44,16 @@ def test_fp64_adjoint_equals_reference(small, precision, tol):
     gc, gw, J = _gpu_adjoint(small, iters, precision)
     rc, rw, rJ = adjoint_ref.gradients(small, iters, dec)
     assert abs(J - rJ) <= 1e-12 * abs(rJ)
+    assert rel(gc, rc) <= tol and rel(gw, rw) <= tol
+
+
+@pytest.mark.parametrize("precision,tol", [(1, 1e-9), (0, 1e-3)])
+def test_alpha2_adjoint_equals_reference(small_a2, precision, tol):
+    iters = 120
+    dec = oracle_run(small_a2, iters)["decisions"]
+    gc, gw, J = _gpu_adjoint(small_a2, iters, precision, sched=dec)
+    rc, rw, rJ = adjoint_ref.gradients(small_a2, iters, dec)
+    assert abs(J - rJ) <= max(tol, 1e-12) * abs(rJ)
     assert rel(gc, rc) <= tol and rel(gw, rw) <= tol
 
 

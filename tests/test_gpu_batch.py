@@ -21,7 +21,7 @@ def _mixed_batch():
             W.random_instance(300, 40, 2, 8, seed=4),
             W.random_instance(1000, 500, 2, 6, seed=5),
             W.random_instance(3000, 200, 1, 6, seed=6, box=box),
-            W.random_instance(5000, 5000, 1, 4, seed=7, frac_log=1.0),
+            W.random_instance(5000, 5000, 1, 4, seed=7, frac_log=0.5, frac_alpha2=0.5),
             W.random_instance(20000, 2000, 2, 8, seed=8, link_dist="zipf", frac_log=1.0,
                               c_scale=0.1, w_dist="lognormal", box=(0.0, 10.0))]
 

@@ -100,6 +100,8 @@ def _cases():
     yield "long_routes", W.random_instance(300, 200, 60, 150, seed=7), dict(tile_items=512)
     yield "ragged_tail", W.random_instance(4097, 1025, 1, 10, seed=8), dict(tile_items=1024)
     yield "all_linear", W.random_instance(2000, 300, 1, 6, seed=9, frac_log=0.0), {}
+    yield "alpha2_mixed", W.random_instance(3000, 400, 1, 6, seed=12, frac_log=0.4,
+                                            frac_alpha2=0.4), {}
 
     def box(rng, n):
         lo = rng.uniform(0.0, 0.5, n)
@@ -200,7 +202,42 @@ def test_objective_matches_fp64_utility(c1):
         kkt.utility(c1, g["x"]))
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_alpha2_objective_and_kkt(precision):
+    """U = -w / x streams mixed with log and linear ones: the reported objective is the
+    FP64 utility of the returned rates (the FP32 path sums with its FP32 copy of w), and a
+    tight FP64 solve satisfies the KKT conditions."""
+    from oracle import kkt
+    inst = W.random_instance(3000, 400, 1, 6, seed=13, frac_log=0.4, frac_alpha2=0.4,
+                             box=(0.0, 20.0))
+    eps = 1e-9 if precision == "fp64" else 1e-5
+    g = run_gpu(inst, 200_000, precision, eps=eps)
+    wi = inst["w"] if precision == "fp64" else inst["w"].astype(np.float32).astype(np.float64)
+    u = kkt.utility(dict(inst, w=wi), g["x"])
+    assert abs(g["info"]["objective"] - u) <= 1e-12 * abs(u)
+    if precision == "fp64":
+        d = kkt.diagnostics(inst, g["x"], g["lam"])
+        assert d["feas"] < 1e-6 and d["stat"] < 1e-5 and abs(d["gap"]) < 1e-6, d
+
+
 # ---- the paper's example and closed forms through the GPU path --------------------------------
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "plain"])
+def test_alpha2_single_link_closed_form(precision):
+    """alpha = 2 fairness on one link: x_j = sqrt(w_j) c / sum sqrt(w), lambda = (sum sqrt(w)
+    / c)^2 (w_j / x_j^2 equal to the link price)."""
+    w = np.array([1.0, 4.0, 0.25, 2.0])
+    c = 3.0
+    inst = dict(n=4, m=1, route_ptr=np.arange(5, dtype=np.int64),
+                route_links=np.zeros(4, np.int32), c=np.array([c]),
+                utype=np.full(4, W.ALPHA2, np.uint8), w=w, lo=np.zeros(4),
+                hi=np.full(4, 50.0))
+    g = run_gpu(inst, 50_000, precision, eps=1e-6 if precision == "fp32" else 1e-11)
+    sw = np.sqrt(w)
+    rt = 1e-4 if precision == "fp32" else 1e-7
+    assert np.allclose(g["x"], sw * c / sw.sum(), rtol=rt)
+    assert np.allclose(g["lam"], [(sw.sum() / c) ** 2], rtol=rt)
+
 
 def test_four_stream_example_fp32():
     inst = W.four_stream_example()

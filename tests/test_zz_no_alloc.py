@@ -14,12 +14,13 @@ from paper_2509_10722_b300 import workloads as W
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("n,m", [(20_000, 2_000), (1_000, 500)])
-def test_noalloc_objective_matches_num_get(n, m):
+@pytest.mark.parametrize("n,m,a2", [(20_000, 2_000, 0.0), (1_000, 500, 0.0), (5_000, 800, 0.3)])
+def test_noalloc_objective_matches_num_get(n, m, a2):
     import torch
 
     from paper_2509_10722_b300 import capi
-    inst = W.random_instance(n, m, 1, 8, seed=17, frac_log=0.6, box=(0.0, 20.0))
+    inst = W.random_instance(n, m, 1, 8, seed=17, frac_log=0.6 - a2, frac_alpha2=a2,
+                             box=(0.0, 20.0))
     # the FP64 path keeps the caller's FP64 weights, so both sides sum the same doubles
     with capi.Problem(inst, precision=capi.NUM_FUSED_FP64) as p:
         p.solve(300, 0.0)
