@@ -69,6 +69,8 @@ def parse():
     ap.add_argument("--scenario", choices=["none", "warmstart", "adjoint"], default="none",
                     help="warmstart: degradation and failure re-solves of Sec. V-D; "
                          "adjoint: gradients of 500 unrolled iterations on c5")
+    ap.add_argument("--record-traffic", metavar="CSV", default=None,
+                    help="write profiles/traffic.json from an ncu CSV (TRAFFIC_CMD) and exit")
     return ap.parse_args()
 
 
@@ -180,18 +182,68 @@ def measured_peaks():
     return 6400.0, "of fallback (6.4 TB/s)"
 
 
+ROW_SOURCES = ("rows.cu", "pmp_rows.cuh", "pmp_device.cuh", "pmp_internal.cuh")
+TRAFFIC_CMD = ("ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum --clock-control none "
+               "--print-units base -k regex:\"k_(stream|link)_rows\" -s 200 -c 2 --csv "
+               "--log-file gpurun_out/traffic.csv python bench.py --steps 1 --warmup 0 "
+               "--no-fp64 --no-e2e --no-cpu-baseline")
+
+
+def row_sources_sha():
+    """First 16 hex digits of sha256 over the sources the row kernels are compiled from."""
+    h = hashlib.sha256()
+    for f in ROW_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_2509_10722_b300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
 def traffic_record(kernel_key):
     """DRAM bytes per launch from a committed ncu capture, if it was taken on the current
-    kernel source (profiles/traffic.json holds the source hash it was taken on)."""
+    kernel sources (profiles/traffic.json holds the source hash it was taken on)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
     rec = json.load(open(path)).get(kernel_key)
     if not rec:
         return None
-    src = os.path.join(ROOT, "paper_2509_10722_b300", "csrc", "rows.cu")
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    return rec if rec.get("source_sha") == h else None
+    return rec if rec.get("source_sha") == row_sources_sha() else None
+
+
+_UNIT = {"byte": 1, "kbyte": 1e3, "mbyte": 1e6, "gbyte": 1e9}
+
+
+def record_traffic(csv_path, workload, out_path=None):
+    """Write profiles/traffic.json from the CSV of an ncu capture of the row kernels (the
+    capture command is TRAFFIC_CMD): mean DRAM bytes per launch of each kernel."""
+    import csv
+    sums = {}
+    with open(csv_path) as f:
+        lines = [ln for ln in f if ln.startswith('"')]
+    for row in csv.DictReader(lines):
+        name = row["Kernel Name"]
+        kern = "k_stream_rows" if "k_stream_rows" in name else (
+            "k_link_rows" if "k_link_rows" in name else None)
+        metric = row["Metric Name"]
+        if kern is None or metric not in ("dram__bytes_read.sum", "dram__bytes_write.sum"):
+            continue
+        v = float(row["Metric Value"].replace(",", "")) * _UNIT[row["Metric Unit"].lower()]
+        d = sums.setdefault(kern, {"launches": set(), "read": 0.0, "write": 0.0})
+        d["launches"].add(row["ID"])
+        d["read" if metric.endswith("read.sum") else "write"] += v
+    out = {"_about": "DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of "
+                     "the fused row kernels on the full solve, from one ncu capture; "
+                     "source_sha = first 16 hex digits of sha256 over csrc/" +
+                     ", csrc/".join(ROW_SOURCES) + " when captured. Command: " + TRAFFIC_CMD}
+    sha = row_sources_sha()
+    for kern, d in sorted(sums.items()):
+        k = len(d["launches"])
+        out[f"{workload}:{kern}"] = {
+            "dram_bytes_per_launch": int(round((d["read"] + d["write"]) / k)),
+            "read": int(round(d["read"] / k)), "write": int(round(d["write"] / k)),
+            "launches": k, "source_sha": sha}
+    with open(out_path or os.path.join(ROOT, "profiles", "traffic.json"), "w") as f:
+        json.dump(out, f, indent=1)
+    return out
 
 
 def to_device(inst, torch):
@@ -619,6 +671,9 @@ def run_adjoint(args):
 
 def main():
     args = parse()
+    if args.record_traffic:
+        print(json.dumps(record_traffic(args.record_traffic, args.workload)))
+        return
     dist = Dist()
     if args.impl == "reference":
         run_reference(args, dist)

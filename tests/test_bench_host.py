@@ -49,6 +49,34 @@ def test_parse_clocks():
     assert bench.parse_clocks("") is None
 
 
+def test_record_traffic_parses_ncu_csv(tmp_path):
+    """Two captured launches of each row kernel in ncu's CSV layout (header line, quoted
+    fields, thousands separators, scaled units): per-launch means per kernel."""
+    hdr = ('"ID","Process ID","Process Name","Host Name","Kernel Name","Context","Stream",'
+           '"Block Size","Grid Size","Device","CC","Section Name","Metric Name","Metric Unit",'
+           '"Metric Value"')
+    rows = []
+    for i, (kern, rd, wr, unit) in enumerate([
+            ("k_stream_rows<float>", "400,000,000", "60,000,000", "byte"),
+            ("k_link_rows<float>(pmp::View<float>)", "300", "20", "Mbyte"),
+            ("k_stream_rows<float>", "410,000,000", "62,000,000", "byte"),
+            ("k_link_rows<float>(pmp::View<float>)", "302", "18", "Mbyte")]):
+        for metric, v in (("dram__bytes_read.sum", rd), ("dram__bytes_write.sum", wr)):
+            rows.append(f'"{i}","1","python","h","{kern}","1","7","(256, 1, 1)","(1184, 1, 1)",'
+                        f'"0","10.3","Command line profiler metrics","{metric}","{unit}","{v}"')
+    csv_path = tmp_path / "traffic.csv"
+    csv_path.write_text("==PROF== Connected to process 1\n" + hdr + "\n" + "\n".join(rows) + "\n")
+    out = tmp_path / "traffic.json"
+    rec = bench.record_traffic(str(csv_path), "c2", out_path=str(out))
+    s = rec["c2:k_stream_rows"]
+    assert s["launches"] == 2 and s["read"] == 405_000_000 and s["write"] == 61_000_000
+    assert s["dram_bytes_per_launch"] == 466_000_000
+    l = rec["c2:k_link_rows"]
+    assert l["read"] == 301_000_000 and l["write"] == 19_000_000
+    assert s["source_sha"] == bench.row_sources_sha()
+    assert json.loads(out.read_text()) == rec
+
+
 def test_traffic_record_requires_matching_source():
     rec = bench.traffic_record("c2:k_link_rows")
     if rec is not None:
