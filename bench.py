@@ -366,6 +366,33 @@ def cpu_baseline(args, inst):
                       f"{k}-iteration and a 1-iteration run, single thread)"}
 
 
+def gather_roofline(capi, n, m, nnz, per_launch_ms, iter_ms):
+    """The kernels against the ceiling that bounds them: each pass makes nnz reads at
+    positions set by the routes (link kernel: x, 4 bytes, from the n-vector; stream kernel:
+    (pbar, y), 8 bytes, from the m-vector).  The ceiling is this GPU's rate of uniformly
+    random reads of the same element size from a vector of the same length, measured now
+    (num_measure_gather_rate, outside the timed region).  The streams are ordered by their
+    first link, which makes some reads adjacent, so a kernel can come out a little above 1."""
+    rate = {4: capi.num_measure_gather_rate(nnz, n, 4, 5),
+            8: capi.num_measure_gather_rate(nnz, m, 8, 5)}
+    kern = {}
+    bound_ms = 0.0
+    for q, (vb, what) in enumerate([(8, "(pbar, y) pairs, 8 B, from the m-vector"),
+                                    (4, "x, 4 B, from the n-vector")]):
+        b = nnz / rate[vb] * 1e3
+        bound_ms += b
+        kern[KERNEL_NAMES[0][q]] = {"reads": nnz, "gathers": what,
+                                    "achieved_g_per_s": nnz / (per_launch_ms[q] / 1e3) / 1e9,
+                                    "ceiling_g_per_s": rate[vb] / 1e9,
+                                    "frac": b / float(per_launch_ms[q])}
+    return {"bound": "random L2 reads (one 32-byte sector each)", "unit": "G reads/s",
+            "kernels": kern,
+            "iteration": {"bound_ms": bound_ms, "ms": iter_ms, "frac": bound_ms / iter_ms},
+            "measured_by": "num_measure_gather_rate: nnz uniformly random reads of the same "
+                           "element size and vector length, 4 in flight per thread, full "
+                           "occupancy, 5 timed passes after 1 warm-up"}
+
+
 def run_ours(args, dist):
     import torch
     dist.init("nccl")
@@ -429,6 +456,8 @@ def run_ours(args, dist):
                                                  "gbs": float(fp32.bytes[q] / (per_launch_ms[q] / 1e3) / 1e9)}
                             for q in range(len(kms))}}
 
+    gather = gather_roofline(capi, n, m, nnz, per_launch_ms, iter_ms)
+
     line = {"metric": METRIC, "value": value, "unit": "iterations/s", "n_gpus": dist.world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
@@ -446,7 +475,8 @@ def run_ours(args, dist):
             "final_residuals": {"primal": info["primal"], "dual": info["dual"],
                                 "eps_tol": info["eps_tol"]},
             "objective": info["objective"],
-            "roofline": roofline, "gpu_launches": int(launches), "clocks": clocks}
+            "roofline": roofline, "gather_roofline": gather, "gpu_launches": int(launches),
+            "clocks": clocks}
 
     if not args.no_fp64:
         plain = Solver(capi, torch, dev, n, m, PRECISION["plain"], args.eps, args.max_iters,

@@ -277,6 +277,21 @@ NUM_API int64_t num_kernel_launches(void);
 NUM_API int num_objective_noalloc(int64_t n, const double* x, const uint8_t* utype,
                                   const double* w, double* objective, void* cuda_stream);
 
+/* Measured rate of uniformly random reads on the current device, in reads per second,
+ * written to the HOST double *gathers_per_s.  Both passes of an iteration (Sec. III-D) read
+ * one value per route entry at positions set by the routes (x per stream in the link pass,
+ * the (pbar, y) pair per link in the stream pass); on random routes these reads, one
+ * 32-byte memory sector each, bound the iteration more tightly than HBM bandwidth.  This
+ * call measures that ceiling: `count` reads (1 .. 2e9) of 4-byte (vec_bytes = 4) or
+ * 8-byte (vec_bytes = 8) elements at uniformly random positions of a vector of vec_len
+ * elements (1 .. 2^31 - 1), four independent reads in flight per thread at full
+ * occupancy, repeated `repeats` times (1 .. 1000) after one warm-up pass, timed with CUDA
+ * events.  Allocates count * 4 + vec_len * vec_bytes bytes of device memory with
+ * cudaMalloc for the duration of the call (NUM_ERR_OOM if that fails) and synchronizes its
+ * own stream.  The paper has no counterpart; it is a measurement service. */
+NUM_API int num_measure_gather_rate(int64_t count, int64_t vec_len, int32_t vec_bytes,
+                                    int32_t repeats, double* gathers_per_s);
+
 /* Free every resource of the handle.  NULL is ignored. */
 NUM_API void num_destroy(num_problem* h);
 

@@ -90,6 +90,7 @@ def _load():
         "num_get_kernel_times": (ctypes.c_int, [P, P, P, i32, ctypes.POINTER(i32)]),
         "num_kernel_launches": (ctypes.c_int64, []),
         "num_objective_noalloc": (ctypes.c_int, [i64, P, P, P, P, P]),
+        "num_measure_gather_rate": (ctypes.c_int, [i64, i64, i32, i32, ctypes.POINTER(d)]),
         "num_batch_create": (ctypes.c_int, [ctypes.POINTER(P), i32, P, P, P, P, P, P, P, P, P,
                                             pp, P]),
         "num_batch_set_rho_schedules": (ctypes.c_int, [P, P, i64]),
@@ -114,7 +115,8 @@ EXPORTED = ("num_default_params", "num_create", "num_create_device", "num_set_rh
             "num_reset", "num_set_capacity", "num_set_weights", "num_adjoint",
             "num_get_state", "num_set_state",
             "num_iteration_bytes", "num_get_kernel_times", "num_kernel_launches",
-            "num_objective_noalloc", "num_destroy", "num_strerror", "num_last_error",
+            "num_objective_noalloc", "num_measure_gather_rate", "num_destroy", "num_strerror",
+            "num_last_error",
             "num_batch_create", "num_batch_set_rho_schedules", "num_batch_solve",
             "num_batch_get", "num_batch_get_kernel_times", "num_batch_destroy")
 
@@ -328,6 +330,14 @@ def num_objective_noalloc(n, x, utype, w, objective, stream=None):
                                       _dptr(w, "float64", n, "w"),
                                       _dptr(objective, "float64", objective.numel(), "objective"),
                                       ctypes.c_void_p(stream) if stream else None))
+
+
+def num_measure_gather_rate(count, vec_len, vec_bytes, repeats=5):
+    """Uniformly random 4- or 8-byte reads per second from a vector of vec_len elements."""
+    out = ctypes.c_double(0.0)
+    _check(_lib.num_measure_gather_rate(int(count), int(vec_len), int(vec_bytes), int(repeats),
+                                        ctypes.byref(out)))
+    return out.value
 
 
 def num_destroy(h):
