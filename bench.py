@@ -69,6 +69,8 @@ def parse():
     ap.add_argument("--scenario", choices=["none", "warmstart", "adjoint"], default="none",
                     help="warmstart: degradation and failure re-solves of Sec. V-D; "
                          "adjoint: gradients of 500 unrolled iterations on c5")
+    ap.add_argument("--tune-iters", type=int, default=10,
+                    help="c4: timed iterations per candidate partition of the autotuner")
     ap.add_argument("--record-traffic", metavar="CSV", default=None,
                     help="write profiles/traffic.json from an ncu CSV (TRAFFIC_CMD) and exit")
     return ap.parse_args()
@@ -539,7 +541,10 @@ def run_batched(args):
     routes of 2..8 links, capacities degraded by U[0.3, 1], 70% log) solved to eps_abs =
     1e-4 as one batch, against the same 256 instances solved one after the other with the
     single-instance FP32 path and with the plain FP64 path.  Each leg includes creation from
-    host arrays, the solve and the host copy of the results; CUDA events on one stream."""
+    host arrays, the solve and the host copy of the results; CUDA events on one stream.
+    The batch runs with the partition chosen by num_batch_autotune (headline: that partition
+    set with num_batch_set_schedule, as a caller that tuned once would), and is also timed
+    with the tuning inside the step and with the default partition."""
     import ctypes
 
     import torch
@@ -548,12 +553,17 @@ def run_batched(args):
     stream = torch.cuda.Stream()
     sp = stream.cuda_stream
 
-    def batch_leg():
+    def batch_leg(mode="default", part=None):
+        tune = None
         with capi.Batch(insts, stream=sp, precision=0, profile=1) as b:
+            if mode == "autotune":
+                tune = b.autotune(trial_iters=args.tune_iters)
+            elif mode == "pinned":
+                b.set_schedule(*part)
             rc, it, st = b.solve(args.max_iters, args.eps)
             xs, ps, infos = b.get()
             ms, runs = b.kernel_times()
-        return int(it.sum()), st, ms, runs
+        return int(it.sum()), st, ms, runs, tune
 
     def seq_leg(precision):
         tot = 0
@@ -572,31 +582,49 @@ def run_batched(args):
         e1.synchronize()
         return e0.elapsed_time(e1) / reps, out[-1]
 
+    def kern(kms, kruns):
+        return {"stream": float(kms[0] / max(kruns[0], 1)), "link": float(kms[1] / max(kruns[1], 1)),
+                "launches": int(kruns[0])}
+
     for _ in range(args.warmup):
-        batch_leg()
+        batch_leg("autotune")
     seq_leg(0)
-    t_b, (it_b, st_b, kms, kruns) = timed_leg(batch_leg, args.steps)
+    t_a, (it_a, st_a, kms_a, kruns_a, tune) = timed_leg(lambda: batch_leg("autotune"), args.steps)
+    chosen, trials = tune
+    t_d, (it_d, st_d, kms_d, kruns_d, _) = timed_leg(lambda: batch_leg("default"), args.steps)
+    t_f, (it_f, st_f, kms_f, kruns_f, _) = timed_leg(lambda: batch_leg("pinned", chosen), args.steps)
     t_s, it_s = timed_leg(lambda: seq_leg(0), 1)
     t_p, it_p = timed_leg(lambda: seq_leg(2), 1)
     n_tot = int(sum(t["n"] for t in insts))
     nnz_tot = int(sum(int(t["route_ptr"][-1]) for t in insts))
+    st1, st2 = trials[:5], trials[5:]
     line = {"metric": "batched PMP: 256 instances to eps_abs 1e-4, aggregate iterations/s",
-            "value": it_b / (t_b / 1e3), "unit": "iterations/s", "n_gpus": 1,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_b,
+            "value": it_f / (t_f / 1e3), "unit": "iterations/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_f,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": "c4: 256 instances, n log-uniform in [1e3, 1e5], m = n/10, "
                                    "routes U{2..8}, c ~ U[1,10] x U[0.3,1], 70% log, box [0,20]",
                        "total_n": n_tot, "total_nnz": nnz_tot,
-                       "step": "num_batch_create (host arrays) + num_batch_solve + num_batch_get"},
-            "converged": int(np.sum(st_b == 0)), "batch_ms": t_b,
+                       "step": "num_batch_create (host arrays) + num_batch_set_schedule "
+                               "(the autotuned partition) + num_batch_solve + num_batch_get"},
+            "converged": int(np.sum(st_f == 0)), "batch_ms": t_f,
+            "with_autotune_ms": t_a, "autotune_ms": t_a - t_f,
+            "autotune": {"chosen": {"stream_item": int(chosen[0]), "link_item": int(chosen[1]),
+                                    "link_lanes": int(chosen[2])},
+                         "trial_iters": args.tune_iters, "candidates": int(len(trials)),
+                         "stream_kernel_ms": {f"{int(r[0])}": round(float(r[3]), 4) for r in st1},
+                         "link_kernel_ms_best": float(st2[:, 3].min()),
+                         "link_kernel_ms_worst": float(st2[:, 3].max())},
+            "default_partition_ms": t_d, "pinned_tuned_partition_ms": t_f,
             "sequential_fp32_ms": t_s, "sequential_plain_fp64_ms": t_p,
-            "speedup_vs_sequential_fp32": t_s / t_b, "speedup_vs_sequential_plain_fp64": t_p / t_b,
-            "iterations": {"batch": it_b, "sequential_fp32": int(it_s),
+            "speedup_vs_sequential_fp32": t_s / t_f, "speedup_vs_sequential_plain_fp64": t_p / t_f,
+            "iterations": {"batch": it_f, "batch_default_partition": it_d,
+                           "batch_with_autotune": it_a, "sequential_fp32": int(it_s),
                            "sequential_plain_fp64": int(it_p)},
-            "kernels_ms_per_launch": {"stream": float(kms[0] / max(kruns[0], 1)),
-                                      "link": float(kms[1] / max(kruns[1], 1))},
-            "kernel_launches": {"stream": int(kruns[0]), "link": int(kruns[1])}}
+            "kernels_ms_per_launch": {"autotuned": kern(kms_a, kruns_a),
+                                      "default_partition": kern(kms_d, kruns_d),
+                                      "pinned": kern(kms_f, kruns_f)}}
     print(json.dumps(line), flush=True)
 
 

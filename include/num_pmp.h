@@ -321,6 +321,45 @@ NUM_API int num_batch_create(num_batch** out, int32_t count, const int64_t* stre
  * decision of instance i at its q-th update point (-1, 0, +1; host array, copied). */
 NUM_API int num_batch_set_rho_schedules(num_batch* b, const int8_t* decisions, int64_t len);
 
+/* Work partition of a batch's two kernels.  Every instance's streams are cut into work
+ * items of stream_item consecutive streams and its links into items of link_item
+ * consecutive links; a block takes one item at a time; in the link kernel link_lanes
+ * lanes sum R x of one link.  The default is {2048, 256, 8}.  The partition does not
+ * change the arithmetic of a stream or a link, except that link_lanes fixes the order of
+ * the additions of (R x)_l; the residual norms are summed per item, so their last bits
+ * follow the partition as well. */
+typedef struct {
+    int32_t stream_item; /* power of two in [256, 65536] */
+    int32_t link_item;   /* power of two in [32, 8192] */
+    int32_t link_lanes;  /* 4, 8, 16 or 32 */
+} num_batch_schedule;
+
+/* The partition in use (HOST struct). */
+NUM_API int num_batch_get_schedule(const num_batch* b, num_batch_schedule* out);
+
+/* Use partition *s from the next solve on (NUM_ERR_INVALID outside the ranges above).  The
+ * iterates are kept; a captured graph is rebuilt.  Synchronizes the stream. */
+NUM_API int num_batch_set_schedule(num_batch* b, const num_batch_schedule* s);
+
+/* Autotuner of the partition: times candidate partitions on this batch and keeps the
+ * fastest.  Stage 1 tries stream_item in {512, 1024, 2048, 4096, 8192} with the link side
+ * unchanged and keeps the one with the least stream-kernel time; stage 2 tries link_item
+ * in {64, 128, 256, 512, 1024} times link_lanes in {4, 8, 16, 32} and keeps the least
+ * link-kernel time (ties: the earlier candidate).  Each candidate runs 2 untimed and
+ * trial_iters (1 .. 500) timed iterations of every instance without a stopping test;
+ * kernel times are CUDA events around each kernel.  Afterwards the chosen partition is in
+ * use and the batch is RESET (state zero, iteration counts zero, rho = rho0, history
+ * cleared): call it after num_batch_create and before solving.  *chosen (HOST, may be
+ * NULL) receives the partition.  trial_ms (HOST, 4 * max_trials doubles, may be NULL with
+ * max_trials = 0) receives, per candidate in the order tried, (stream_item, link_item,
+ * link_lanes, milliseconds of the kernel that stage compares); *ntrials (may be NULL) the
+ * number of candidates tried (25).  Synchronizes the stream.  The choice follows measured
+ * times, so two calls can choose differently, and with a different link_lanes the
+ * results differ in the last bits (see num_batch_schedule); pass the chosen partition to
+ * num_batch_set_schedule to reproduce a run. */
+NUM_API int num_batch_autotune(num_batch* b, int32_t trial_iters, num_batch_schedule* chosen,
+                               double* trial_ms, int32_t max_trials, int32_t* ntrials);
+
 /* Run at most max_iters further iterations of every instance (eps_abs as in num_solve,
  * with eps_tol = eps_abs sqrt(J_i) per instance).  iters_done[count] and status[count]
  * (host arrays, may be NULL) receive each instance's iterations and NUM_OK /

@@ -56,6 +56,15 @@ class num_params(ctypes.Structure):
                 ("allocator", ctypes.POINTER(num_allocator))]
 
 
+class BatchSchedule(ctypes.Structure):
+    """num_batch_schedule: work partition of a batch's kernels."""
+    _fields_ = [("stream_item", ctypes.c_int32), ("link_item", ctypes.c_int32),
+                ("link_lanes", ctypes.c_int32)]
+
+    def as_tuple(self):
+        return (self.stream_item, self.link_item, self.link_lanes)
+
+
 class NumError(RuntimeError):
     def __init__(self, code, message):
         super().__init__(f"{num_strerror(code)} ({code}): {message}")
@@ -97,6 +106,10 @@ def _load():
         "num_batch_solve": (ctypes.c_int, [P, i64, d, P, P]),
         "num_batch_get": (ctypes.c_int, [P, P, P, P]),
         "num_batch_get_kernel_times": (ctypes.c_int, [P, P, P, i32, ctypes.POINTER(i32)]),
+        "num_batch_get_schedule": (ctypes.c_int, [P, ctypes.POINTER(BatchSchedule)]),
+        "num_batch_set_schedule": (ctypes.c_int, [P, ctypes.POINTER(BatchSchedule)]),
+        "num_batch_autotune": (ctypes.c_int, [P, i32, ctypes.POINTER(BatchSchedule), P, i32,
+                                              ctypes.POINTER(i32)]),
         "num_batch_destroy": (None, [P]),
         "num_destroy": (None, [P]),
         "num_strerror": (ctypes.c_char_p, [ctypes.c_int]),
@@ -118,7 +131,8 @@ EXPORTED = ("num_default_params", "num_create", "num_create_device", "num_set_rh
             "num_objective_noalloc", "num_measure_gather_rate", "num_destroy", "num_strerror",
             "num_last_error",
             "num_batch_create", "num_batch_set_rho_schedules", "num_batch_solve",
-            "num_batch_get", "num_batch_get_kernel_times", "num_batch_destroy")
+            "num_batch_get", "num_batch_get_kernel_times", "num_batch_get_schedule",
+            "num_batch_set_schedule", "num_batch_autotune", "num_batch_destroy")
 
 
 def library():
@@ -413,6 +427,26 @@ class Batch:
         nk = ctypes.c_int32(0)
         _check(_lib.num_batch_get_kernel_times(self.h, _hptr(ms), _hptr(cnt), 2, ctypes.byref(nk)))
         return ms, cnt
+
+    def schedule(self):
+        """(stream_item, link_item, link_lanes) in use."""
+        out = BatchSchedule()
+        _check(_lib.num_batch_get_schedule(self.h, ctypes.byref(out)))
+        return out.as_tuple()
+
+    def set_schedule(self, stream_item, link_item, link_lanes):
+        s = BatchSchedule(int(stream_item), int(link_item), int(link_lanes))
+        _check(_lib.num_batch_set_schedule(self.h, ctypes.byref(s)))
+
+    def autotune(self, trial_iters=20):
+        """Run the autotuner; returns (chosen (stream_item, link_item, link_lanes), trials)
+        with trials an array of rows (stream_item, link_item, link_lanes, ms)."""
+        out = BatchSchedule()
+        trials = np.zeros((64, 4))
+        nt = ctypes.c_int32(0)
+        _check(_lib.num_batch_autotune(self.h, int(trial_iters), ctypes.byref(out), _hptr(trials),
+                                       64, ctypes.byref(nt)))
+        return out.as_tuple(), trials[:min(nt.value, 64)]
 
     def close(self):
         if getattr(self, "h", None) is not None:

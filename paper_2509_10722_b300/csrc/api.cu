@@ -217,7 +217,7 @@ View<T> make_view(const num_problem* h) {
 cudaError_t run_iterations(num_problem* h, int count) {
     const bool prof = h->prm.profile != 0;
     if (prof) {
-        cudaError_t e = cudaEventRecordWithFlags(h->evs[0], h->stream, cudaEventRecordExternal);
+        cudaError_t e = pmp::record_kernel_event(h->evs[0], h->stream);
         if (e != cudaSuccess) return e;
     }
     for (int i = 0; i < count; ++i) {
@@ -1218,12 +1218,28 @@ struct num_batch {
     double kernel_ms[2] = {0.0, 0.0};
     long long kernel_runs[2] = {0, 0};
     std::vector<double> J;  // terminals nnz_i + m_i of each instance
+    num_batch_schedule cfg{};          // the work partition in use
+    int cap_sitems = 0, cap_litems = 0;  // item capacity (the smallest item sizes)
+    unsigned int* arrive = nullptr;    // [count] per-instance link-item arrivals
 };
 
 namespace {
 
-constexpr int kBatchStreamItem = 2048;  // streams per work item
-constexpr int kBatchLinkItem = 256;     // links per work item
+// Work partition of a batch: defaults, limits and the autotuner's candidates.
+constexpr num_batch_schedule kBatchDefault = {2048, 256, 8};
+constexpr int kStreamItemMin = 256, kStreamItemMax = 65536;
+constexpr int kLinkItemMin = 32, kLinkItemMax = 8192;
+constexpr int kTuneStreamItems[] = {512, 1024, 2048, 4096, 8192};
+constexpr int kTuneLinkItems[] = {64, 128, 256, 512, 1024};
+constexpr int kTuneLanes[] = {4, 8, 16, 32};
+
+bool pow2_in(int v, int lo, int hi) { return v >= lo && v <= hi && (v & (v - 1)) == 0; }
+
+bool valid_schedule(const num_batch_schedule& c) {
+    return pow2_in(c.stream_item, kStreamItemMin, kStreamItemMax) &&
+           pow2_in(c.link_item, kLinkItemMin, kLinkItemMax) &&
+           (c.link_lanes == 4 || c.link_lanes == 8 || c.link_lanes == 16 || c.link_lanes == 32);
+}
 
 template <typename T>
 pmp::BatchView<T> make_batch_view(const num_batch* b) {
@@ -1244,6 +1260,8 @@ pmp::BatchView<T> make_batch_view(const num_batch* b) {
     v.hist = b->hist;
     v.sched = b->sched;
     v.sched_stride = b->sched_stride;
+    v.arrive = b->arrive;
+    v.lanes = b->cfg.link_lanes;
     return v;
 }
 
@@ -1251,7 +1269,7 @@ cudaError_t batch_run(num_batch* b, int count) {
     num_problem* h = b->p;
     const bool prof = h->prm.profile != 0;
     if (prof) {
-        cudaError_t e = cudaEventRecordWithFlags(h->evs[0], h->stream, cudaEventRecordExternal);
+        cudaError_t e = pmp::record_kernel_event(h->evs[0], h->stream);
         if (e != cudaSuccess) return e;
     }
     for (int i = 0; i < count; ++i) {
@@ -1281,7 +1299,97 @@ int batch_reset_all(num_batch* b) {
     const num_params& q = b->p->prm;
     cudaError_t e = pmp::batch_reset(b->ctls, b->glob, b->count, q.rho0, q.alpha, q.mu, q.gamma,
                                      q.rho_period, q.history, 0, b->p->stream);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(b->arrive, 0, sizeof(unsigned int) * (size_t)b->count, b->p->stream);
     if (e != cudaSuccess) return cuda_fail(e, "resetting the instances");
+    return NUM_OK;
+}
+
+// Build the work items of schedule `cfg` (instance, first row, end row) and size the grids;
+// a captured graph of the old partition is dropped.  Streams keep their instance's range
+// after the first-link ordering because an instance's links are a contiguous id range.
+int batch_apply_schedule(num_batch* b, const num_batch_schedule& cfg) {
+    num_problem* h = b->p;
+    cudaStream_t st = h->stream;
+    std::vector<int4> si, li;
+    std::vector<int> so(b->count + 1), lo_(b->count + 1);
+    for (int i = 0; i < b->count; ++i) {
+        so[i] = (int)si.size();
+        for (int64_t r = b->soff[i]; r < b->soff[i + 1]; r += cfg.stream_item)
+            si.push_back(make_int4(i, (int)r, (int)std::min<int64_t>(r + cfg.stream_item,
+                                                                     b->soff[i + 1]), 0));
+        lo_[i] = (int)li.size();
+        for (int64_t r = b->loff[i]; r < b->loff[i + 1]; r += cfg.link_item)
+            li.push_back(make_int4(i, (int)r, (int)std::min<int64_t>(r + cfg.link_item,
+                                                                     b->loff[i + 1]), 0));
+    }
+    so[b->count] = (int)si.size();
+    lo_[b->count] = (int)li.size();
+    if ((int)si.size() > b->cap_sitems || (int)li.size() > b->cap_litems)
+        return fail(NUM_ERR_STATE, "work items exceed their capacity");
+    cudaError_t e = cudaStreamSynchronize(st);  // no kernel may still read the old items
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->sitems, si.data(), sizeof(int4) * si.size(), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->litems, li.data(), sizeof(int4) * li.size(), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->sitem_off, so.data(), sizeof(int) * (b->count + 1),
+                            cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->litem_off, lo_.data(), sizeof(int) * (b->count + 1),
+                            cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // the host vectors go out of scope
+    if (e != cudaSuccess) return cuda_fail(e, "copying the work items");
+    b->nsitems = (int)si.size();
+    b->nlitems = (int)li.size();
+    e = pmp::batch_grids(h->prec == NUM_FUSED_FP32 ? 0 : 1, cfg.link_lanes, b->nsitems,
+                         b->nlitems, &b->grid_s, &b->grid_l, &b->grid_e);
+    if (e != cudaSuccess) return cuda_fail(e, "sizing the batch grids");
+    b->cfg = cfg;
+    if (b->graph_exec) cudaGraphExecDestroy(b->graph_exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->graph_exec = nullptr;
+    b->graph = nullptr;
+    return NUM_OK;
+}
+
+// Device time of the stream kernel and of the link kernel, summed over `iters` iterations
+// of schedule `cfg` (after two untimed ones), with no stopping test.
+int batch_time_schedule(num_batch* b, const num_batch_schedule& cfg, int iters, double* ms_s,
+                        double* ms_l) {
+    int rc = batch_apply_schedule(b, cfg);
+    if (rc != NUM_OK) return rc;
+    num_problem* h = b->p;
+    cudaStream_t st = h->stream;
+    cudaError_t e = pmp::batch_arm(b->ctls, b->glob, b->count, (long long)iters + 2, 0.0,
+                                   b->eps_scale, st);
+    if (e != cudaSuccess) return cuda_fail(e, "arming the instances");
+    std::vector<cudaEvent_t> ev(2 * (size_t)iters + 1, nullptr);
+    for (auto& x : ev)
+        if (e == cudaSuccess) e = cudaEventCreate(&x);
+    auto run = [&](cudaEvent_t* evs) {
+        return h->prec == NUM_FUSED_FP32
+                   ? pmp::batch_iteration<float>(make_batch_view<float>(b), b->grid_s, b->grid_l, st, evs)
+                   : pmp::batch_iteration<double>(make_batch_view<double>(b), b->grid_s, b->grid_l, st, evs);
+    };
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = run(nullptr);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[0], st);
+    for (int i = 0; i < iters && e == cudaSuccess; ++i) e = run(ev.data() + 1 + 2 * (size_t)i);
+    pmp::note_launches(2 * ((long long)iters + 2));
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    double ts = 0.0, tl = 0.0;
+    for (int i = 0; i < iters && e == cudaSuccess; ++i) {
+        float a = 0.f, c = 0.f;
+        e = cudaEventElapsedTime(&a, ev[2 * i], ev[2 * i + 1]);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&c, ev[2 * i + 1], ev[2 * i + 2]);
+        ts += a;
+        tl += c;
+    }
+    for (auto x : ev)
+        if (x) cudaEventDestroy(x);
+    if (e != cudaSuccess) return cuda_fail(e, "timing a schedule");
+    *ms_s = ts;
+    *ms_l = tl;
     return NUM_OK;
 }
 
@@ -1327,42 +1435,37 @@ int num_batch_create(num_batch** out, int32_t count, const int64_t* stream_off,
         return rc;
     }
     num_problem* h = b->p;
-    // work items (instance, first row, end row): streams keep their instance's range after
-    // the first-link ordering because an instance's links are a contiguous id range
-    std::vector<int4> si, li;
-    std::vector<int> so(count + 1), lo_(count + 1);
+    // work items are built by batch_apply_schedule; room for the smallest item sizes
     std::vector<double> scale(count);
+    int64_t cap_s = 0, cap_l = 0;
     for (int i = 0; i < count; ++i) {
-        so[i] = (int)si.size();
-        for (int64_t r = stream_off[i]; r < stream_off[i + 1]; r += kBatchStreamItem)
-            si.push_back(make_int4(i, (int)r, (int)std::min<int64_t>(r + kBatchStreamItem,
-                                                                     stream_off[i + 1]), 0));
-        lo_[i] = (int)li.size();
-        for (int64_t r = link_off[i]; r < link_off[i + 1]; r += kBatchLinkItem)
-            li.push_back(make_int4(i, (int)r, (int)std::min<int64_t>(r + kBatchLinkItem,
-                                                                     link_off[i + 1]), 0));
+        cap_s += (stream_off[i + 1] - stream_off[i] + kStreamItemMin - 1) / kStreamItemMin;
+        cap_l += (link_off[i + 1] - link_off[i] + kLinkItemMin - 1) / kLinkItemMin;
         const int64_t nnz_i = route_ptr[stream_off[i + 1]] - route_ptr[stream_off[i]];
         b->J.push_back((double)(nnz_i + link_off[i + 1] - link_off[i]));
         scale[i] = std::sqrt(b->J.back());
     }
-    so[count] = (int)si.size();
-    lo_[count] = (int)li.size();
-    b->nsitems = (int)si.size();
-    b->nlitems = (int)li.size();
+    if (cap_s > INT32_MAX / 4 || cap_l > INT32_MAX / 4) {
+        batch_destroy(b);
+        return fail(NUM_ERR_INVALID, "too many work items");
+    }
+    b->cap_sitems = (int)cap_s;
+    b->cap_litems = (int)cap_l;
     const int H = prm.history > 0 ? prm.history : 1;
     b->ctls = (pmp::Ctl*)dev_alloc(h, sizeof(pmp::Ctl) * count);
     b->glob = (pmp::BatchGlobal*)dev_alloc(h, sizeof(pmp::BatchGlobal));
-    b->sitems = (int4*)dev_alloc(h, sizeof(int4) * si.size());
-    b->litems = (int4*)dev_alloc(h, sizeof(int4) * li.size());
+    b->sitems = (int4*)dev_alloc(h, sizeof(int4) * (size_t)cap_s);
+    b->litems = (int4*)dev_alloc(h, sizeof(int4) * (size_t)cap_l);
     b->sitem_off = (int*)dev_alloc(h, sizeof(int) * (count + 1));
     b->litem_off = (int*)dev_alloc(h, sizeof(int) * (count + 1));
-    b->part_s = (double*)dev_alloc(h, sizeof(double) * si.size());
-    b->part_l = (double*)dev_alloc(h, sizeof(double) * 2 * li.size());
-    b->part_e = (double*)dev_alloc(h, sizeof(double) * si.size());
+    b->part_s = (double*)dev_alloc(h, sizeof(double) * (size_t)cap_s);
+    b->part_l = (double*)dev_alloc(h, sizeof(double) * 2 * (size_t)cap_l);
+    b->part_e = (double*)dev_alloc(h, sizeof(double) * (size_t)cap_s);
+    b->arrive = (unsigned int*)dev_alloc(h, sizeof(unsigned int) * (size_t)count);
     b->hist = (double*)dev_alloc(h, sizeof(double) * 3 * (size_t)H * count);
     b->eps_scale = (double*)dev_alloc(h, sizeof(double) * count);
     if (!b->ctls || !b->glob || !b->sitems || !b->litems || !b->sitem_off || !b->litem_off ||
-        !b->part_s || !b->part_l || !b->part_e || !b->hist || !b->eps_scale) {
+        !b->part_s || !b->part_l || !b->part_e || !b->hist || !b->eps_scale || !b->arrive) {
         batch_destroy(b);
         return fail(NUM_ERR_OOM, "device allocation failed");
     }
@@ -1380,19 +1483,14 @@ int num_batch_create(num_batch** out, int32_t count, const int64_t* stream_off,
        "cudaHostAlloc");
     BK(cudaHostAlloc((void**)&b->glob_host, sizeof(pmp::BatchGlobal), cudaHostAllocDefault),
        "cudaHostAlloc");
-    BK(cudaMemcpyAsync(b->sitems, si.data(), sizeof(int4) * si.size(), cudaMemcpyHostToDevice, st),
-       "copy items");
-    BK(cudaMemcpyAsync(b->litems, li.data(), sizeof(int4) * li.size(), cudaMemcpyHostToDevice, st),
-       "copy items");
-    BK(cudaMemcpyAsync(b->sitem_off, so.data(), sizeof(int) * (count + 1), cudaMemcpyHostToDevice,
-                       st), "copy items");
-    BK(cudaMemcpyAsync(b->litem_off, lo_.data(), sizeof(int) * (count + 1),
-                       cudaMemcpyHostToDevice, st), "copy items");
     BK(cudaMemcpyAsync(b->eps_scale, scale.data(), sizeof(double) * count, cudaMemcpyHostToDevice,
                        st), "copy scales");
     BK(cudaMemsetAsync(b->hist, 0, sizeof(double) * 3 * (size_t)H * count, st), "memset");
-    BK(pmp::batch_grids(h->prec == NUM_FUSED_FP32 ? 0 : 1, b->nsitems, b->nlitems, &b->grid_s,
-                        &b->grid_l, &b->grid_e), "sizing the batch grids");
+    rc = batch_apply_schedule(b, kBatchDefault);
+    if (rc != NUM_OK) {
+        batch_destroy(b);
+        return rc;
+    }
     rc = batch_reset_all(b);
     if (rc != NUM_OK) {
         batch_destroy(b);
@@ -1584,6 +1682,97 @@ int num_batch_get_kernel_times(const num_batch* b, double* ms, int64_t* launches
         ms[q] = b->kernel_ms[q];
         launches[q] = b->kernel_runs[q];
     }
+    return NUM_OK;
+}
+
+int num_batch_get_schedule(const num_batch* b, num_batch_schedule* out) {
+    g_last_error.clear();
+    if (!b || !out) return fail(NUM_ERR_INVALID, "batch or out is NULL");
+    *out = b->cfg;
+    return NUM_OK;
+}
+
+int num_batch_set_schedule(num_batch* b, const num_batch_schedule* cfg) {
+    g_last_error.clear();
+    if (!b || !cfg) return fail(NUM_ERR_INVALID, "batch or schedule is NULL");
+    if (!valid_schedule(*cfg))
+        return fail(NUM_ERR_INVALID, "stream_item must be a power of two in [256, 65536], "
+                                     "link_item a power of two in [32, 8192], link_lanes 4, 8, "
+                                     "16 or 32");
+    cudaError_t e = order_after_legacy(b->p);
+    if (e != cudaSuccess) return cuda_fail(e, "ordering");
+    return batch_apply_schedule(b, *cfg);
+}
+
+int num_batch_autotune(num_batch* b, int32_t trial_iters, num_batch_schedule* chosen,
+                       double* trial_ms, int32_t max_trials, int32_t* ntrials) {
+    g_last_error.clear();
+    if (!b) return fail(NUM_ERR_INVALID, "batch is NULL");
+    if (trial_iters < 1 || trial_iters > 500)
+        return fail(NUM_ERR_INVALID, "trial_iters must be in [1, 500]");
+    if (max_trials < 0 || (max_trials > 0 && !trial_ms))
+        return fail(NUM_ERR_INVALID, "bad trial buffer");
+    num_problem* h = b->p;
+    cudaError_t e = order_after_legacy(h);
+    if (e != cudaSuccess) return cuda_fail(e, "ordering");
+    num_batch_schedule best = b->cfg;
+    int t = 0;
+    auto record = [&](const num_batch_schedule& c, double ms) {
+        if (t < max_trials) {
+            trial_ms[4 * t] = c.stream_item;
+            trial_ms[4 * t + 1] = c.link_item;
+            trial_ms[4 * t + 2] = c.link_lanes;
+            trial_ms[4 * t + 3] = ms;
+        }
+        ++t;
+    };
+    // stage 1: streams per stream item (the stream kernel's time), link side as it is
+    double best_s = 0.0;
+    for (int si : kTuneStreamItems) {
+        num_batch_schedule c{si, best.link_item, best.link_lanes};
+        double ts = 0.0, tl = 0.0;
+        const int rc = batch_time_schedule(b, c, trial_iters, &ts, &tl);
+        if (rc != NUM_OK) return rc;
+        record(c, ts);
+        if (si == kTuneStreamItems[0] || ts < best_s) {
+            best_s = ts;
+            best.stream_item = si;
+        }
+    }
+    // stage 2: links per link item and lanes per link (the link kernel's time)
+    double best_l = 0.0;
+    bool first = true;
+    const int stream_item = best.stream_item;
+    for (int li : kTuneLinkItems)
+        for (int ln : kTuneLanes) {
+            num_batch_schedule c{stream_item, li, ln};
+            double ts = 0.0, tl = 0.0;
+            const int rc = batch_time_schedule(b, c, trial_iters, &ts, &tl);
+            if (rc != NUM_OK) return rc;
+            record(c, tl);
+            if (first || tl < best_l) {
+                best_l = tl;
+                best.link_item = li;
+                best.link_lanes = ln;
+                first = false;
+            }
+        }
+    int rc = batch_apply_schedule(b, best);
+    if (rc != NUM_OK) return rc;
+    // the trials moved the iterates: start over from zero
+    e = zero_state(h);
+    if (e != cudaSuccess) return cuda_fail(e, "zeroing the state");
+    rc = batch_reset_all(b);
+    if (rc != NUM_OK) return rc;
+    e = cudaMemsetAsync(b->hist, 0,
+                        sizeof(double) * 3 * (size_t)(h->prm.history > 0 ? h->prm.history : 1) *
+                            b->count, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "resetting after the trials");
+    b->kernel_ms[0] = b->kernel_ms[1] = 0.0;
+    b->kernel_runs[0] = b->kernel_runs[1] = 0;
+    if (chosen) *chosen = best;
+    if (ntrials) *ntrials = t;
     return NUM_OK;
 }
 

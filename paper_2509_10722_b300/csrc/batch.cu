@@ -9,10 +9,15 @@
 //     a block takes an item, runs the rows of it (a thread per stream / 8 lanes per link,
 //     exactly the row-kernel arithmetic) unless that instance has stopped, and writes the
 //     item's residual partial sums to the item's own slot;
-//   - the last block of the link kernel finishes the iteration of every running instance
-//     (one thread per instance: FP64 sums of its item slots in item order, norms, stopping
-//     test, rho), and counts the instances still running (the host stops replaying when
-//     none is).
+//   - the block that finishes the last link item of an instance (a per-instance arrival
+//     count) finishes that instance's iteration: FP64 sums of its item slots in a fixed
+//     order by the whole block, norms, stopping test, rho; an instance that stops takes
+//     itself off the count of running instances (the host stops replaying at zero).
+//     Instances are finished as their items complete, in parallel with the rest.
+// The work partition (streams per stream item, links per link item, lanes per link) is a
+// runtime schedule, chosen by the caller or by the autotuner in api.cu; the arithmetic of
+// a stream or a link does not depend on it except through the lanes per link, which fix
+// the order of the additions of R x.
 // No block waits on another; sums are in a fixed order, so runs are deterministic.
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
@@ -29,7 +34,6 @@ namespace {
 
 constexpr int kTh = 256;
 constexpr int kWarps = kTh / 32;
-constexpr int kGroup = 8;
 
 template <typename T>
 __global__ void __launch_bounds__(kTh) k_stream_batch(BatchView<T> b) {
@@ -57,26 +61,52 @@ __global__ void __launch_bounds__(kTh) k_stream_batch(BatchView<T> b) {
     }
 }
 
+// End of iteration of instance i, by the whole block: FP64 sums of its stream-item and
+// link-item slots (thread-strided, then the block tree: a fixed order), then the single-
+// thread step of Sec. III-F / III-G.
 template <typename T>
+__device__ void finish_instance(const BatchView<T>& b, int i, double* red) {
+    double ss = 0.0, rr = 0.0, sl = 0.0;
+    const int s0 = b.sitem_off[i], s1 = b.sitem_off[i + 1];
+    const int q0 = b.litem_off[i], q1 = b.litem_off[i + 1];
+    for (int q = s0 + threadIdx.x; q < s1; q += kTh) ss += __ldcg(b.part_s + q);
+    for (int q = q0 + threadIdx.x; q < q1; q += kTh) {
+        rr += __ldcg(b.part_l + 2 * q);
+        sl += __ldcg(b.part_l + 2 * q + 1);
+    }
+    ss = block_sum(ss, red);
+    rr = block_sum(rr, red);
+    sl = block_sum(sl, red);
+    if (threadIdx.x == 0) {
+        Ctl* c = b.ctls + i;
+        finalize_iteration(c, rr, ss + sl,
+                           b.hist + (size_t)i * 3 * (c->hist_len > 0 ? c->hist_len : 1),
+                           b.sched + (size_t)i * b.sched_stride);
+        b.arrive[i] = 0;
+        if (c->stop != RUNNING) atomicSub(&b.glob->running, 1);
+    }
+}
+
+template <typename T, int G>
 __global__ void __launch_bounds__(kTh) k_link_batch(BatchView<T> b) {
     __shared__ double red[kWarps];
-    __shared__ int last;
+    __shared__ int fin;
     if (b.glob->running == 0) return;
     const View<T>& v = b.v;
-    auto g = cg::tiled_partition<kGroup>(cg::this_thread_block());
+    auto g = cg::tiled_partition<G>(cg::this_thread_block());
     const bool leader = g.thread_rank() == 0;
-    constexpr int kGroups = kTh / kGroup;
+    constexpr int kGroups = kTh / G;
     for (int it = blockIdx.x; it < b.nlitems; it += gridDim.x) {
         const int4 item = __ldg(b.litems + it);
         const Ctl* c = b.ctls + item.x;
         if (c->stop) continue;  // block-uniform
         const T alpha = (T)c->alpha, rho = (T)c->rho, inv_rho = (T)(1.0 / c->rho);
         Acc<T> r2, s2;
-        for (int l = item.y + (int)(threadIdx.x / kGroup); l < item.z; l += kGroups) {
+        for (int l = item.y + (int)(threadIdx.x / G); l < item.z; l += kGroups) {
             const int p0 = __ldg(v.row_ptr + l), p1 = __ldg(v.row_ptr + l + 1);
             LinkState<T> st;
             if (leader) st = load_link(v, l);
-            const T s = group_gather_sum<kGroup>(g, v.col_idx, v.x, p0, p1);
+            const T s = group_gather_sum<G>(g, v.col_idx, v.x, p0, p1);
             if (leader) link_epilogue(v, l, st, s, p1 - p0, alpha, rho, inv_rho, r2, s2);
         }
         const double R2 = block_sum(r2.value(), red);
@@ -84,35 +114,15 @@ __global__ void __launch_bounds__(kTh) k_link_batch(BatchView<T> b) {
         if (threadIdx.x == 0) {
             b.part_l[2 * it] = R2;
             b.part_l[2 * it + 1] = S2;
+            __threadfence();
+            const int nit = b.litem_off[item.x + 1] - b.litem_off[item.x];
+            fin = atomicAdd(b.arrive + item.x, 1u) == (unsigned)(nit - 1);
         }
-    }
-    // the last block to get here finishes the iteration of every running instance
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        last = atomicAdd(&b.glob->ticket, 1u) == gridDim.x - 1;
-    }
-    __syncthreads();
-    if (!last) return;
-    __threadfence();
-    int running = 0;
-    for (int i = threadIdx.x; i < b.count; i += kTh) {
-        Ctl* c = b.ctls + i;
-        if (c->stop) continue;
-        double ss = 0.0, rr = 0.0, sl = 0.0;
-        for (int q = b.sitem_off[i]; q < b.sitem_off[i + 1]; ++q) ss += __ldcg(b.part_s + q);
-        for (int q = b.litem_off[i]; q < b.litem_off[i + 1]; ++q) {
-            rr += __ldcg(b.part_l + 2 * q);
-            sl += __ldcg(b.part_l + 2 * q + 1);
+        __syncthreads();
+        if (fin) {  // every link item of this instance is in
+            __threadfence();
+            finish_instance(b, item.x, red);
         }
-        finalize_iteration(c, rr, ss + sl, b.hist + (size_t)i * 3 * (c->hist_len > 0 ? c->hist_len : 1),
-                           b.sched + (size_t)i * b.sched_stride);
-        running += c->stop == RUNNING;
-    }
-    const int total = __syncthreads_count(running > 0) ? 1 : 0;
-    if (threadIdx.x == 0) {
-        b.glob->ticket = 0;
-        b.glob->running = total;
     }
 }
 
@@ -194,7 +204,7 @@ __global__ void k_batch_arm(Ctl* ctls, BatchGlobal* glob, int count, long long m
         c->stop = RUNNING;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-        glob->running = count > 0 && max_iters > 0 ? 1 : 0;
+        glob->running = max_iters > 0 ? count : 0;  // instances still running
         glob->ticket = 0;
     }
 }
@@ -221,10 +231,21 @@ __global__ void k_batch_reset(Ctl* ctls, BatchGlobal* glob, int count, double rh
 }
 
 template <typename T>
-cudaError_t batch_occupancy(int* occ_s, int* occ_l, int* occ_e) {
+cudaError_t link_occupancy(int lanes, int* occ) {
+    switch (lanes) {
+        case 4: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_link_batch<T, 4>, kTh, 0);
+        case 8: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_link_batch<T, 8>, kTh, 0);
+        case 16: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_link_batch<T, 16>, kTh, 0);
+        case 32: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_link_batch<T, 32>, kTh, 0);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <typename T>
+cudaError_t batch_occupancy(int lanes, int* occ_s, int* occ_l, int* occ_e) {
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ_s, k_stream_batch<T>, kTh, 0);
     if (e != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ_l, k_link_batch<T>, kTh, 0);
+    e = link_occupancy<T>(lanes, occ_l);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ_e, k_export_batch<T>, kTh, 0);
 }
@@ -236,14 +257,15 @@ int blocks_for(long long count) {
 
 }  // namespace
 
-cudaError_t batch_grids(int precision, int nsitems, int nlitems, int* grid_s, int* grid_l,
-                        int* grid_e) {
+cudaError_t batch_grids(int precision, int lanes, int nsitems, int nlitems, int* grid_s,
+                        int* grid_l, int* grid_e) {
     int dev = 0, sms = 0, os = 0, ol = 0, oe = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
-    e = precision == 0 ? batch_occupancy<float>(&os, &ol, &oe) : batch_occupancy<double>(&os, &ol, &oe);
+    e = precision == 0 ? batch_occupancy<float>(lanes, &os, &ol, &oe)
+                       : batch_occupancy<double>(lanes, &os, &ol, &oe);
     if (e != cudaSuccess) return e;
     if (os < 1 || ol < 1 || oe < 1) return cudaErrorInvalidConfiguration;
     const long long gs = (long long)os * sms, gl = (long long)ol * sms, ge = (long long)oe * sms;
@@ -266,9 +288,15 @@ template <typename T>
 cudaError_t batch_iteration(const BatchView<T>& b, int grid_s, int grid_l, cudaStream_t st,
                             cudaEvent_t* evs) {
     k_stream_batch<T><<<grid_s, kTh, 0, st>>>(b);
-    if (evs) cudaEventRecordWithFlags(evs[0], st, cudaEventRecordExternal);
-    k_link_batch<T><<<grid_l, kTh, 0, st>>>(b);
-    if (evs) cudaEventRecordWithFlags(evs[1], st, cudaEventRecordExternal);
+    if (evs) record_kernel_event(evs[0], st);
+    switch (b.lanes) {
+        case 4: k_link_batch<T, 4><<<grid_l, kTh, 0, st>>>(b); break;
+        case 8: k_link_batch<T, 8><<<grid_l, kTh, 0, st>>>(b); break;
+        case 16: k_link_batch<T, 16><<<grid_l, kTh, 0, st>>>(b); break;
+        case 32: k_link_batch<T, 32><<<grid_l, kTh, 0, st>>>(b); break;
+        default: return cudaErrorInvalidValue;
+    }
+    if (evs) record_kernel_event(evs[1], st);
     return cudaGetLastError();
 }
 template cudaError_t batch_iteration<float>(const BatchView<float>&, int, int, cudaStream_t,

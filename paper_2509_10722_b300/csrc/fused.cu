@@ -411,9 +411,9 @@ size_t smem_link(int tile) {
 template <typename T, int IS, int IL>
 cudaError_t launch_fixed(const View<T>& v, cudaStream_t st, cudaEvent_t* evs) {
     k_stream<T, IS><<<v.grid_s, kTh, smem_stream<T>(kTh * IS), st>>>(v);
-    if (evs) cudaEventRecordWithFlags(evs[0], st, cudaEventRecordExternal);
+    if (evs) record_kernel_event(evs[0], st);
     k_link<T, IL><<<v.grid_l, kTh, smem_link<T>(kTh * IL), st>>>(v);
-    if (evs) cudaEventRecordWithFlags(evs[1], st, cudaEventRecordExternal);
+    if (evs) record_kernel_event(evs[1], st);
     return cudaGetLastError();
 }
 

@@ -129,7 +129,7 @@ cudaError_t plain_iteration(const View<double>& v, int nb, cudaStream_t st, cuda
     double* partL = v.part_l + nb;
     int q = 0;
     auto mark = [&]() {
-        if (evs) cudaEventRecordWithFlags(evs[q], st, cudaEventRecordExternal);
+        if (evs) record_kernel_event(evs[q], st);
         ++q;
     };
     k_plain_spmvT<<<blocks(v.n, 1 << 16), kTh, 0, st>>>(v);

@@ -120,8 +120,8 @@ constexpr int kFusedKernelsPerIter = 2;
 
 // ---- batched kernels (batch.cu) ---------------------------------------------------------------
 struct BatchGlobal {
-    unsigned int ticket;  // last-block-done counter
-    int running;          // 1 while any instance is running
+    unsigned int ticket;  // last-block-done counter of the export kernel
+    int running;          // number of instances still running
 };
 
 // Work items are (instance, first row, end row, 0); item ranges of instance i are
@@ -142,10 +142,23 @@ struct BatchView {
     double* hist;    // [count][max(hist_len, 1)][3]
     const signed char* sched;  // [count][sched_stride]
     int sched_stride;
+    unsigned int* arrive;  // [count] link items of the instance done in this iteration
+    int lanes;             // lanes per link in the link kernel: 4, 8, 16 or 32
 };
 
-cudaError_t batch_grids(int precision, int nsitems, int nlitems, int* grid_s, int* grid_l,
-                        int* grid_e);
+// Profiling event after a kernel: an external event node while the stream is being
+// captured into a graph (so that replays record it), a plain record otherwise.
+inline cudaError_t record_kernel_event(cudaEvent_t ev, cudaStream_t st) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(st, &cs);
+    if (e != cudaSuccess) return e;
+    return cs == cudaStreamCaptureStatusActive
+               ? cudaEventRecordWithFlags(ev, st, cudaEventRecordExternal)
+               : cudaEventRecord(ev, st);
+}
+
+cudaError_t batch_grids(int precision, int lanes, int nsitems, int nlitems, int* grid_s,
+                        int* grid_l, int* grid_e);
 cudaError_t check_blocks(int count, const int64_t* stream_off, const int64_t* link_off,
                          long long n, const int64_t* route_ptr, const int* route_links, int* err,
                          cudaStream_t st);

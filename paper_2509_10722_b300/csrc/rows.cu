@@ -174,9 +174,9 @@ cudaError_t rows_grids(int precision, int n, int m, int nchunks, int* grid_s, in
 template <typename T>
 cudaError_t rows_iteration(const View<T>& v, cudaStream_t st, cudaEvent_t* evs) {
     k_stream_rows<T><<<v.grid_s, kTh, stream_smem<T>(), st>>>(v);
-    if (evs) cudaEventRecordWithFlags(evs[0], st, cudaEventRecordExternal);
+    if (evs) record_kernel_event(evs[0], st);
     k_link_rows<T><<<v.grid_l, kTh, 0, st>>>(v);
-    if (evs) cudaEventRecordWithFlags(evs[1], st, cudaEventRecordExternal);
+    if (evs) record_kernel_event(evs[1], st);
     return cudaGetLastError();
 }
 template cudaError_t rows_iteration<float>(const View<float>&, cudaStream_t, cudaEvent_t*);

@@ -125,3 +125,80 @@ def test_c4_recipe_batch_converges():
         ref = oracle_run(insts[i], 100_000, eps=1e-4)
         u = kkt.utility(insts[i], ref["x"])
         assert abs(g["info"][i]["objective"] - u) <= 1e-5 * abs(u), i
+
+
+# ---- the work partition and its autotuner ---------------------------------------------------
+
+PARTITIONS = [(256, 32, 4), (512, 64, 8), (2048, 256, 16), (65536, 8192, 32), (1024, 1024, 8)]
+
+
+@pytest.mark.parametrize("part", PARTITIONS, ids=[f"{a}-{b}-{c}" for a, b, c in PARTITIONS])
+def test_every_partition_matches_oracle(batch, part):
+    from paper_2509_10722_b300 import capi
+    iters = 120
+    with capi.Batch(batch, precision=1, history=64) as b:
+        b.set_schedule(*part)
+        assert b.schedule() == part
+        b.solve(iters, 0.0)
+        xs, ps, _ = b.get()
+    for i, inst in enumerate(batch):
+        ref = oracle_run(inst, iters)
+        assert rel(xs[i], ref["x"]) <= 1e-10, (part, i)
+        assert rel(ps[i], ref["lam"]) <= 1e-10, (part, i)
+
+
+def test_item_sizes_do_not_change_the_iterates(batch):
+    """With the lanes per link fixed and the rho decisions replayed, the FP32 iterates are
+    bit-identical for every item size: the partition only regroups the residual sums."""
+    from paper_2509_10722_b300 import capi
+    iters = 200
+    sched = np.zeros((len(batch), iters // 50), dtype=np.int8)
+    for i, inst in enumerate(batch):
+        d = oracle_run(inst, iters)["decisions"]
+        sched[i, :d.size] = d
+    out = []
+    for part in [(2048, 256, 8), (256, 32, 8), (65536, 8192, 8)]:
+        with capi.Batch(batch, precision=0, history=64) as b:
+            b.set_schedule(*part)
+            b.set_rho_schedules(sched)
+            b.solve(iters, 0.0)
+            xs, ps, _ = b.get()
+        out.append((np.concatenate(xs), np.concatenate(ps)))
+    for x, p in out[1:]:
+        assert np.array_equal(x, out[0][0]) and np.array_equal(p, out[0][1])
+
+
+def test_autotune_chooses_a_partition_and_resets(batch):
+    from paper_2509_10722_b300 import capi
+    iters = 150
+    with capi.Batch(batch, precision=0, history=64) as b:
+        chosen, trials = b.autotune(trial_iters=5)
+        assert trials.shape == (25, 4) and np.all(trials[:, 3] > 0)
+        assert b.schedule() == chosen
+        # stage 1 varied stream_item only, stage 2 link_item and lanes
+        assert sorted(set(trials[:5, 0])) == [512, 1024, 2048, 4096, 8192]
+        assert len(set(map(tuple, trials[5:, 1:3]))) == 20
+        assert chosen[0] == trials[:5][np.argmin(trials[:5, 3]), 0]
+        rc, it, _ = b.solve(iters, 0.0)
+        assert list(it) == [iters] * len(batch)  # reset: counts start from zero
+        xs, ps, infos = b.get()
+        assert all(inf["iters"] == iters for inf in infos)
+    with capi.Batch(batch, precision=0, history=64) as b2:
+        b2.set_schedule(*chosen)
+        b2.solve(iters, 0.0)
+        xs2, ps2, _ = b2.get()
+    for a, c in zip(xs, xs2):
+        assert np.array_equal(a, c)
+    for a, c in zip(ps, ps2):
+        assert np.array_equal(a, c)
+
+
+@pytest.mark.parametrize("bad", [(128, 256, 8), (3000, 256, 8), (2048, 16, 8), (2048, 16384, 8),
+                                 (2048, 256, 2), (2048, 256, 64), (2048, 100, 8)])
+def test_bad_partitions_are_rejected(bad):
+    from paper_2509_10722_b300 import capi
+    with capi.Batch([W.random_instance(50, 10, 1, 3, seed=1)], precision=0) as b:
+        with pytest.raises(capi.NumError) as e:
+            b.set_schedule(*bad)
+        assert e.value.code == capi.NUM_ERR_INVALID
+        assert b.schedule() == (2048, 256, 8)

@@ -260,3 +260,20 @@ def test_profile_times_and_launch_count(c1):
         p.solve(30, 0.0)
         ms, runs = p.kernel_times()
     assert list(runs) == [30] * 8 and np.all(ms > 0)
+
+
+@pytest.mark.parametrize("precision,schedule,nk", [(0, 1, 2), (1, 2, 2), (2, 1, 8)])
+def test_profile_without_graphs(c1, precision, schedule, nk):
+    """Per-kernel times with plain launches (use_graph = 0): the events are recorded on the
+    stream directly rather than as graph nodes, and the iterates equal the graph path's."""
+    from paper_2509_10722_b300 import capi
+    out = []
+    for g in (0, 1):
+        with capi.Problem(c1, precision=precision, schedule=schedule, profile=1,
+                          use_graph=g, check_every=10) as p:
+            status, done = p.solve(40, 0.0)
+            ms, runs = p.kernel_times()
+            x, lam, _ = p.get()
+        assert done == 40 and list(runs) == [40] * nk and np.all(ms > 0)
+        out.append(x)
+    assert np.array_equal(out[0], out[1])
