@@ -69,6 +69,8 @@ def parse():
     ap.add_argument("--scenario", choices=["none", "warmstart", "adjoint"], default="none",
                     help="warmstart: degradation and failure re-solves of Sec. V-D; "
                          "adjoint: gradients of 500 unrolled iterations on c5")
+    ap.add_argument("--no-seq", action="store_true",
+                    help="c4: skip the two sequential legs (for profiling the batch kernels)")
     ap.add_argument("--tune-iters", type=int, default=10,
                     help="c4: timed iterations per candidate partition of the autotuner")
     ap.add_argument("--record-traffic", metavar="CSV", default=None,
@@ -588,13 +590,18 @@ def run_batched(args):
 
     for _ in range(args.warmup):
         batch_leg("autotune")
-    seq_leg(0)
+    if not args.no_seq:
+        seq_leg(0)
     t_a, (it_a, st_a, kms_a, kruns_a, tune) = timed_leg(lambda: batch_leg("autotune"), args.steps)
     chosen, trials = tune
     t_d, (it_d, st_d, kms_d, kruns_d, _) = timed_leg(lambda: batch_leg("default"), args.steps)
     t_f, (it_f, st_f, kms_f, kruns_f, _) = timed_leg(lambda: batch_leg("pinned", chosen), args.steps)
-    t_s, it_s = timed_leg(lambda: seq_leg(0), 1)
-    t_p, it_p = timed_leg(lambda: seq_leg(2), 1)
+    if args.no_seq:
+        t_s = t_p = float("nan")
+        it_s = it_p = 0
+    else:
+        t_s, it_s = timed_leg(lambda: seq_leg(0), 1)
+        t_p, it_p = timed_leg(lambda: seq_leg(2), 1)
     n_tot = int(sum(t["n"] for t in insts))
     nnz_tot = int(sum(int(t["route_ptr"][-1]) for t in insts))
     st1, st2 = trials[:5], trials[5:]

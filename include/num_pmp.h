@@ -92,8 +92,9 @@ typedef struct {
  *   history     length of the on-device ring buffer of (||r||, ||s||, rho) per iteration
  *               (default 4096; 0 = none)
  *   use_graph   1 (default): replay captured CUDA graphs; 0: plain launches
- *   schedule    0 (default) or NUM_SCHEDULE_ROWS: row-parallel fused kernels (a warp per
- *               32 streams, a warp per link, links above 2048 streams cut into chunks);
+ *   schedule    0 (default) or NUM_SCHEDULE_ROWS: row-parallel fused kernels (a thread
+ *               per stream, 8 lanes per link; a link of more than 256 streams is summed
+ *               by whole warps, in chunks of 2048 entries);
  *               NUM_SCHEDULE_TILES: merge-path tiles of tile_items items (any skew)
  *   reorder     1 (default): place streams in the order of the first link of their route
  *               (stable), so that streams sharing that link are adjacent and the gathers

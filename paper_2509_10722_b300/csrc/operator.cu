@@ -55,10 +55,40 @@ __global__ void k_validate_streams(int n, const int64_t* __restrict__ route_ptr,
     }
     if (bits) atomicOr(err, bits);
     if (alpha2) atomicOr(err + 1, 1);  // some stream has U = -w / x
-    atomicMin(box + 0, lo_min);
-    atomicMax(box + 1, lo_max);
-    atomicMin(box + 2, hi_min);
-    atomicMax(box + 3, hi_max);
+    // box extremes: warp shuffles, then the block, then one atomic per block and value
+    // (a global atomic per thread on four shared addresses serialises in L2)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long a = __shfl_xor_sync(0xffffffffu, lo_min, o);
+        const unsigned long long b = __shfl_xor_sync(0xffffffffu, lo_max, o);
+        const unsigned long long c = __shfl_xor_sync(0xffffffffu, hi_min, o);
+        const unsigned long long d = __shfl_xor_sync(0xffffffffu, hi_max, o);
+        lo_min = a < lo_min ? a : lo_min;
+        lo_max = b > lo_max ? b : lo_max;
+        hi_min = c < hi_min ? c : hi_min;
+        hi_max = d > hi_max ? d : hi_max;
+    }
+    __shared__ unsigned long long ext[4][kThreads / 32];
+    const int warp = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+        ext[0][warp] = lo_min;
+        ext[1][warp] = lo_max;
+        ext[2][warp] = hi_min;
+        ext[3][warp] = hi_max;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int q = 1; q < (int)(blockDim.x >> 5); ++q) {
+            lo_min = ext[0][q] < lo_min ? ext[0][q] : lo_min;
+            lo_max = ext[1][q] > lo_max ? ext[1][q] : lo_max;
+            hi_min = ext[2][q] < hi_min ? ext[2][q] : hi_min;
+            hi_max = ext[3][q] > hi_max ? ext[3][q] : hi_max;
+        }
+        atomicMin(box + 0, lo_min);
+        atomicMax(box + 1, lo_max);
+        atomicMin(box + 2, hi_min);
+        atomicMax(box + 3, hi_max);
+    }
 }
 
 __global__ void k_validate_links(int m, long long nnz, const int* __restrict__ route_links,

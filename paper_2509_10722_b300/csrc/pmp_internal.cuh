@@ -40,9 +40,10 @@ struct Ctl {
 
 enum Stop { RUNNING = 0, CONVERGED = 1, LIMIT = 2, NONFINITE = 3 };
 
-// Row kernels (rows.cu): a link with more than kLongRow streams is summed in chunks of
-// kChunk entries by separate warps; persistent grids are capped at kMaxRowsGrid blocks.
-constexpr int kLongRow = 2048;
+// Row kernels (rows.cu): a link with more than kLongRow streams is summed by whole warps
+// in chunks of kChunk entries (one chunk per warp; 256 and 2048 measured best on a
+// Zipf(1.1) instance); persistent grids are capped at kMaxRowsGrid blocks.
+constexpr int kLongRow = 256;
 constexpr int kChunk = 2048;
 constexpr int kMaxRowsGrid = 8192;
 

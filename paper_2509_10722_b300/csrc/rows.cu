@@ -8,9 +8,10 @@
 //   link kernel: a group of G lanes per link (G = 32 / rows per warp), the link's own
 //     state loaded by the group leader before the gathers, R x summed by the group in a
 //     fixed order, the link epilogue by the leader; links with more than kLongRow streams
-//     are cut into fixed chunks of kChunk entries, each chunk summed by one group into its
-//     own slot, and the group that brings the row's arrival count to the number of chunks
-//     sums the slots in chunk order and runs the epilogue (no waiting, deterministic);
+//     are cut into fixed chunks of kChunk entries, each chunk summed by one warp (four
+//     gathers in flight per lane) into its own slot, and the warp that brings the row's
+//     arrival count to the number of chunks sums the slots in a fixed order and runs the
+//     epilogue (no waiting, deterministic);
 //   the last block of the link kernel finishes the iteration (FP64 residual sums, stopping
 //   test, rho), as in the tile engine.
 // Per-thread residual partial sums are compensated sums in the iteration precision; block
@@ -63,6 +64,43 @@ size_t stream_smem() {
 
 // ---- link kernel ---------------------------------------------------------------------------------
 
+// Sum of x over entries [e0, e1) by one warp: lane k takes e0 + k, e0 + k + 32, ... four
+// at a time, then a shuffle tree (a fixed order).
+template <typename T>
+__device__ __forceinline__ T warp_gather_sum(const int* __restrict__ col_idx,
+                                             const T* __restrict__ x, int e0, int e1, int lane) {
+    T s = T(0);
+    for (int e = e0 + lane; e < e1; e += 128) {
+        const int i0 = __ldg(col_idx + e);
+        const int i1 = e + 32 < e1 ? __ldg(col_idx + e + 32) : -1;
+        const int i2 = e + 64 < e1 ? __ldg(col_idx + e + 64) : -1;
+        const int i3 = e + 96 < e1 ? __ldg(col_idx + e + 96) : -1;
+        const T a = __ldg(x + i0);
+        const T b = i1 >= 0 ? __ldg(x + i1) : T(0);
+        const T c = i2 >= 0 ? __ldg(x + i2) : T(0);
+        const T d = i3 >= 0 ? __ldg(x + i3) : T(0);
+        s += (a + b) + (c + d);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    return s;
+}
+
+// Sum of the n chunk slots of one row by one warp, in a fixed order; the slots were
+// written by other blocks of this launch, so they are read from L2.
+template <typename T>
+__device__ __forceinline__ T warp_sum_slots(const T* slots, int n, int lane) {
+    T s = T(0);
+    int q = lane;
+    for (; q + 96 < n; q += 128)
+        s += (__ldcg(slots + q) + __ldcg(slots + q + 32)) +
+             (__ldcg(slots + q + 64) + __ldcg(slots + q + 96));
+    for (; q < n; q += 32) s += __ldcg(slots + q);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    return s;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kTh) k_link_rows(View<T> v) {
     __shared__ double red[kWarps];
@@ -77,42 +115,42 @@ __global__ void __launch_bounds__(kTh) k_link_rows(View<T> v) {
     const int* __restrict__ col_idx = v.col_idx;
     const T* __restrict__ x = v.x;
     Acc<T> r2, s2;
-    const int items = m + v.nchunks;
+    // links of up to kLongRow streams: one group each
     constexpr int kGroups = kTh / kGroup;
-    const int gstride = gridDim.x * kGroups;
-    for (int it = blockIdx.x * kGroups + (int)(threadIdx.x / kGroup); it < items; it += gstride) {
-        if (it < m) {
-            const int p0 = __ldg(row_ptr + it), p1 = __ldg(row_ptr + it + 1);
-            if (p1 - p0 > kLongRow) continue;  // done by its chunks
-            LinkState<T> st;
-            if (leader) st = load_link(v, it);
-            const T s = group_gather_sum<kGroup>(g, col_idx, x, p0, p1);
-            if (leader) link_epilogue(v, it, st, s, p1 - p0, alpha, rho, inv_rho, r2, s2);
-        } else {
-            const int4 ch = __ldg(v.chunks + (it - m));  // (row, first entry, end entry, first chunk)
-            const T s = group_gather_sum<kGroup>(g, col_idx, x, ch.y, ch.z);
-            int fin = 0;
-            if (leader) {
-                v.carry_l[it - m] = s;
-                __threadfence();
-                const int p0 = __ldg(row_ptr + ch.x), p1 = __ldg(row_ptr + ch.x + 1);
-                const int nch = (p1 - p0 + kChunk - 1) / kChunk;
-                fin = atomicAdd(v.arrive_l + ch.w, 1) == nch - 1;
-            }
-            fin = g.shfl(fin, 0);
-            if (fin) {  // every chunk of the row is in: sum the slots in chunk order
-                __threadfence();
-                const int p0 = __ldg(row_ptr + ch.x), p1 = __ldg(row_ptr + ch.x + 1);
-                const int nch = (p1 - p0 + kChunk - 1) / kChunk;
-                T t = T(0);
-                for (int q = g.thread_rank(); q < nch; q += kGroup) t += __ldcg(v.carry_l + ch.w + q);
-#pragma unroll
-                for (int o = kGroup / 2; o > 0; o >>= 1) t += g.shfl_down(t, o);
-                if (leader) {
-                    v.arrive_l[ch.w] = 0;
-                    const LinkState<T> st = load_link(v, ch.x);
-                    link_epilogue(v, ch.x, st, t, p1 - p0, alpha, rho, inv_rho, r2, s2);
-                }
+    for (int l = blockIdx.x * kGroups + (int)(threadIdx.x / kGroup); l < m;
+         l += gridDim.x * kGroups) {
+        const int p0 = __ldg(row_ptr + l), p1 = __ldg(row_ptr + l + 1);
+        if (p1 - p0 > kLongRow) continue;  // done by its chunks
+        LinkState<T> st;
+        if (leader) st = load_link(v, l);
+        const T s = group_gather_sum<kGroup>(g, col_idx, x, p0, p1);
+        if (leader) link_epilogue(v, l, st, s, p1 - p0, alpha, rho, inv_rho, r2, s2);
+    }
+    // chunks of the longer links: one warp each (four gathers in flight per lane), so that
+    // a chunk is a short chain of round trips and the chunks balance across warps
+    const int lane = threadIdx.x & 31;
+    for (int q = blockIdx.x * kWarps + (int)(threadIdx.x >> 5); q < v.nchunks;
+         q += gridDim.x * kWarps) {
+        const int4 ch = __ldg(v.chunks + q);  // (row, first entry, end entry, first chunk)
+        const T s = warp_gather_sum(col_idx, x, ch.y, ch.z, lane);
+        int fin = 0;
+        if (lane == 0) {
+            v.carry_l[q] = s;
+            __threadfence();
+            const int p0 = __ldg(row_ptr + ch.x), p1 = __ldg(row_ptr + ch.x + 1);
+            const int nch = (p1 - p0 + kChunk - 1) / kChunk;
+            fin = atomicAdd(v.arrive_l + ch.w, 1) == nch - 1;
+        }
+        fin = __shfl_sync(0xffffffffu, fin, 0);
+        if (fin) {  // every chunk of the row is in: sum the slots in a fixed order
+            __threadfence();
+            const int p0 = __ldg(row_ptr + ch.x), p1 = __ldg(row_ptr + ch.x + 1);
+            const int nch = (p1 - p0 + kChunk - 1) / kChunk;
+            const T t = warp_sum_slots(v.carry_l + ch.w, nch, lane);
+            if (lane == 0) {
+                v.arrive_l[ch.w] = 0;
+                const LinkState<T> st = load_link(v, ch.x);
+                link_epilogue(v, ch.x, st, t, p1 - p0, alpha, rho, inv_rho, r2, s2);
             }
         }
     }

@@ -80,8 +80,8 @@ def test_c3_scaled_matches_oracle(c3_small, precision, tol):
 
 
 def test_c3_full_size_fp32_tracks_fp64():
-    """Full c3 (1.4e8 entries; 3,906 links above 2,048 streams are cut into chunks, the
-    hottest has 1.1e7 streams): FP32 on the FP64 run's rho schedule stays within 1e-4 of
+    """Full c3 (1.4e8 entries; every link above 256 streams is summed by warps in chunks of
+    2,048 entries, the hottest has 1.1e7 streams): FP32 on the FP64 run's rho schedule stays within 1e-4 of
     it after 300 iterations."""
     c3 = W.workload("c3")
     f64 = run_gpu(c3, 300, "fp64", history=300)
