@@ -555,9 +555,9 @@ def run_batched(args):
     stream = torch.cuda.Stream()
     sp = stream.cuda_stream
 
-    def batch_leg(mode="default", part=None):
+    def batch_leg(mode="default", part=None, precision=0, keep=None):
         tune = None
-        with capi.Batch(insts, stream=sp, precision=0, profile=1) as b:
+        with capi.Batch(insts, stream=sp, precision=precision, profile=1) as b:
             if mode == "autotune":
                 tune = b.autotune(trial_iters=args.tune_iters)
             elif mode == "pinned":
@@ -565,6 +565,9 @@ def run_batched(args):
             rc, it, st = b.solve(args.max_iters, args.eps)
             xs, ps, infos = b.get()
             ms, runs = b.kernel_times()
+            if keep is not None:
+                keep["x"] = [x.copy() for x in xs]
+                keep["obj"] = np.array([inf["objective"] for inf in infos])
         return int(it.sum()), st, ms, runs, tune
 
     def seq_leg(precision):
@@ -596,6 +599,13 @@ def run_batched(args):
     chosen, trials = tune
     t_d, (it_d, st_d, kms_d, kruns_d, _) = timed_leg(lambda: batch_leg("default"), args.steps)
     t_f, (it_f, st_f, kms_f, kruns_f, _) = timed_leg(lambda: batch_leg("pinned", chosen), args.steps)
+    # precision: the same batch in FP64 (default partition, untimed) against the FP32 run
+    r32, r64 = {}, {}
+    batch_leg("pinned", chosen, 0, r32)
+    batch_leg("default", None, 1, r64)
+    obj_rel = np.abs(r32["obj"] - r64["obj"]) / np.maximum(np.abs(r64["obj"]), 1e-300)
+    x_rel = [float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+             for a, b in zip(r32["x"], r64["x"])]
     if args.no_seq:
         t_s = t_p = float("nan")
         it_s = it_p = 0
@@ -629,6 +639,11 @@ def run_batched(args):
             "iterations": {"batch": it_f, "batch_default_partition": it_d,
                            "batch_with_autotune": it_a, "sequential_fp32": int(it_s),
                            "sequential_plain_fp64": int(it_p)},
+            "fp32_vs_fp64_batch": {"objective_rel_max": float(obj_rel.max()),
+                                   "objective_rel_median": float(np.median(obj_rel)),
+                                   "x_rel_max": float(max(x_rel)),
+                                   "note": "per instance, both stopped by the same test at "
+                                           "eps_abs 1e-4"},
             "kernels_ms_per_launch": {"autotuned": kern(kms_a, kruns_a),
                                       "default_partition": kern(kms_d, kruns_d),
                                       "pinned": kern(kms_f, kruns_f)}}
