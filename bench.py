@@ -69,6 +69,8 @@ def parse():
     ap.add_argument("--scenario", choices=["none", "warmstart", "adjoint"], default="none",
                     help="warmstart: degradation and failure re-solves of Sec. V-D; "
                          "adjoint: gradients of 500 unrolled iterations on c5")
+    ap.add_argument("--congested", action="store_true",
+                    help="c4: Zipf(1.1) link choice in every instance (congestion scenario)")
     ap.add_argument("--no-seq", action="store_true",
                     help="c4: skip the two sequential legs (for profiling the batch kernels)")
     ap.add_argument("--tune-iters", type=int, default=10,
@@ -551,7 +553,7 @@ def run_batched(args):
 
     import torch
     from paper_2509_10722_b300 import capi
-    insts = W.batched_instances(256, seed=0)
+    insts = W.batched_instances(256, seed=0, congested=args.congested)
     stream = torch.cuda.Stream()
     sp = stream.cuda_stream
 
@@ -621,7 +623,9 @@ def run_batched(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": "c4: 256 instances, n log-uniform in [1e3, 1e5], m = n/10, "
-                                   "routes U{2..8}, c ~ U[1,10] x U[0.3,1], 70% log, box [0,20]",
+                                   "routes U{2..8}, c ~ U[1,10] x U[0.3,1], 70% log, box [0,20]"
+                                   + (", Zipf(1.1) link choice (congested)" if args.congested
+                                      else ", uniform links"),
                        "total_n": n_tot, "total_nnz": nnz_tot,
                        "step": "num_batch_create (host arrays) + num_batch_set_schedule "
                                "(the autotuned partition) + num_batch_solve + num_batch_get"},

@@ -1220,7 +1220,11 @@ struct num_batch {
     std::vector<double> J;  // terminals nnz_i + m_i of each instance
     num_batch_schedule cfg{};          // the work partition in use
     int cap_sitems = 0, cap_litems = 0;  // item capacity (the smallest item sizes)
-    unsigned int* arrive = nullptr;    // [count] per-instance link-item arrivals
+    unsigned int* arrive = nullptr;    // [count] per-instance arrivals of finished parts
+    int* chunk_inst = nullptr;         // [nchunks] instance of each long-link chunk
+    int* coff = nullptr;               // [count + 1] chunk range of each instance
+    int* crows = nullptr;              // [count] chunked links of each instance
+    double* part_c = nullptr;          // [2 nchunks] residual terms of chunked links
 };
 
 namespace {
@@ -1262,6 +1266,15 @@ pmp::BatchView<T> make_batch_view(const num_batch* b) {
     v.sched_stride = b->sched_stride;
     v.arrive = b->arrive;
     v.lanes = b->cfg.link_lanes;
+    const num_problem* h = b->p;
+    v.chunks = h->chunks;
+    v.nchunks = h->nchunks;
+    v.chunk_inst = b->chunk_inst;
+    v.coff = b->coff;
+    v.crows = b->crows;
+    v.carry = (T*)h->carry_l;
+    v.arrive_c = h->arrive_l;
+    v.part_c = b->part_c;
     return v;
 }
 
@@ -1343,13 +1356,57 @@ int batch_apply_schedule(num_batch* b, const num_batch_schedule& cfg) {
     b->nsitems = (int)si.size();
     b->nlitems = (int)li.size();
     e = pmp::batch_grids(h->prec == NUM_FUSED_FP32 ? 0 : 1, cfg.link_lanes, b->nsitems,
-                         b->nlitems, &b->grid_s, &b->grid_l, &b->grid_e);
+                         b->nlitems, h->nchunks, &b->grid_s, &b->grid_l, &b->grid_e);
     if (e != cudaSuccess) return cuda_fail(e, "sizing the batch grids");
     b->cfg = cfg;
     if (b->graph_exec) cudaGraphExecDestroy(b->graph_exec);
     if (b->graph) cudaGraphDestroy(b->graph);
     b->graph_exec = nullptr;
     b->graph = nullptr;
+    return NUM_OK;
+}
+
+// The instance of every long-link chunk of the stacked problem, each instance's chunk range
+// and number of chunked links, and zeroed residual slots for the chunked links.  Chunks are
+// in link order and an instance's links are a contiguous id range, so an instance's chunks
+// are contiguous.
+int batch_chunk_tables(num_batch* b) {
+    num_problem* h = b->p;
+    const int nc = h->nchunks;
+    if (nc <= 0) return NUM_OK;
+    cudaStream_t st = h->stream;
+    std::vector<int4> ch((size_t)nc);
+    cudaError_t e = cudaMemcpyAsync(ch.data(), h->chunks, sizeof(int4) * (size_t)nc,
+                                    cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "reading the chunk table");
+    std::vector<int> inst((size_t)nc), coff(b->count + 1, 0), crows(b->count, 0);
+    for (int q = 0; q < nc; ++q) {
+        const int64_t link = ch[q].x;
+        const int i = (int)(std::upper_bound(b->loff.begin(), b->loff.end(), link) -
+                            b->loff.begin()) - 1;
+        inst[q] = i;
+        coff[i + 1] += 1;
+        if (ch[q].w == q) crows[i] += 1;
+    }
+    for (int i = 0; i < b->count; ++i) coff[i + 1] += coff[i];
+    b->chunk_inst = (int*)dev_alloc(h, sizeof(int) * (size_t)nc);
+    b->coff = (int*)dev_alloc(h, sizeof(int) * (size_t)(b->count + 1));
+    b->crows = (int*)dev_alloc(h, sizeof(int) * (size_t)b->count);
+    b->part_c = (double*)dev_alloc(h, sizeof(double) * 2 * (size_t)nc);
+    if (!b->chunk_inst || !b->coff || !b->crows || !b->part_c)
+        return fail(NUM_ERR_OOM, "device allocation failed");
+    e = cudaMemcpyAsync(b->chunk_inst, inst.data(), sizeof(int) * (size_t)nc,
+                        cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->coff, coff.data(), sizeof(int) * (size_t)(b->count + 1),
+                            cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->crows, crows.data(), sizeof(int) * (size_t)b->count,
+                            cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->part_c, 0, sizeof(double) * 2 * (size_t)nc, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // the host vectors go out of scope
+    if (e != cudaSuccess) return cuda_fail(e, "copying the chunk tables");
     return NUM_OK;
 }
 
@@ -1486,6 +1543,11 @@ int num_batch_create(num_batch** out, int32_t count, const int64_t* stream_off,
     BK(cudaMemcpyAsync(b->eps_scale, scale.data(), sizeof(double) * count, cudaMemcpyHostToDevice,
                        st), "copy scales");
     BK(cudaMemsetAsync(b->hist, 0, sizeof(double) * 3 * (size_t)H * count, st), "memset");
+    rc = batch_chunk_tables(b);
+    if (rc != NUM_OK) {
+        batch_destroy(b);
+        return rc;
+    }
     rc = batch_apply_schedule(b, kBatchDefault);
     if (rc != NUM_OK) {
         batch_destroy(b);

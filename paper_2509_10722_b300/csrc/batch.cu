@@ -19,6 +19,8 @@
 // a stream or a link does not depend on it except through the lanes per link, which fix
 // the order of the additions of R x.
 // No block waits on another; sums are in a fixed order, so runs are deterministic.
+#include <algorithm>
+
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
@@ -61,23 +63,28 @@ __global__ void __launch_bounds__(kTh) k_stream_batch(BatchView<T> b) {
     }
 }
 
-// End of iteration of instance i, by the whole block: FP64 sums of its stream-item and
-// link-item slots (thread-strided, then the block tree: a fixed order), then the single-
-// thread step of Sec. III-F / III-G.
+// End of iteration of instance i, by one warp: FP64 sums of its stream-item, link-item
+// and chunked-link slots (lane-strided, then the shuffle tree: a fixed order), then the
+// single-thread step of Sec. III-F / III-G.
 template <typename T>
-__device__ void finish_instance(const BatchView<T>& b, int i, double* red) {
+__device__ void finish_instance(const BatchView<T>& b, int i, int lane) {
     double ss = 0.0, rr = 0.0, sl = 0.0;
     const int s0 = b.sitem_off[i], s1 = b.sitem_off[i + 1];
     const int q0 = b.litem_off[i], q1 = b.litem_off[i + 1];
-    for (int q = s0 + threadIdx.x; q < s1; q += kTh) ss += __ldcg(b.part_s + q);
-    for (int q = q0 + threadIdx.x; q < q1; q += kTh) {
+    for (int q = s0 + lane; q < s1; q += 32) ss += __ldcg(b.part_s + q);
+    for (int q = q0 + lane; q < q1; q += 32) {
         rr += __ldcg(b.part_l + 2 * q);
         sl += __ldcg(b.part_l + 2 * q + 1);
     }
-    ss = block_sum(ss, red);
-    rr = block_sum(rr, red);
-    sl = block_sum(sl, red);
-    if (threadIdx.x == 0) {
+    if (b.nchunks > 0)
+        for (int q = b.coff[i] + lane; q < b.coff[i + 1]; q += 32) {
+            rr += __ldcg(b.part_c + 2 * q);  // zero except at a link's first chunk
+            sl += __ldcg(b.part_c + 2 * q + 1);
+        }
+    ss = warp_sum(ss);
+    rr = warp_sum(rr);
+    sl = warp_sum(sl);
+    if (lane == 0) {
         Ctl* c = b.ctls + i;
         finalize_iteration(c, rr, ss + sl,
                            b.hist + (size_t)i * 3 * (c->hist_len > 0 ? c->hist_len : 1),
@@ -85,6 +92,14 @@ __device__ void finish_instance(const BatchView<T>& b, int i, double* red) {
         b.arrive[i] = 0;
         if (c->stop != RUNNING) atomicSub(&b.glob->running, 1);
     }
+}
+
+// Count one finished part (a link item or a chunked link) of instance i; true for the
+// part that completes the instance.  Single thread.
+template <typename T>
+__device__ __forceinline__ bool instance_done(const BatchView<T>& b, int i) {
+    const int parts = b.litem_off[i + 1] - b.litem_off[i] + (b.nchunks > 0 ? b.crows[i] : 0);
+    return atomicAdd(b.arrive + i, 1u) == (unsigned)(parts - 1);
 }
 
 template <typename T, int G>
@@ -95,6 +110,7 @@ __global__ void __launch_bounds__(kTh) k_link_batch(BatchView<T> b) {
     const View<T>& v = b.v;
     auto g = cg::tiled_partition<G>(cg::this_thread_block());
     const bool leader = g.thread_rank() == 0;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     constexpr int kGroups = kTh / G;
     for (int it = blockIdx.x; it < b.nlitems; it += gridDim.x) {
         const int4 item = __ldg(b.litems + it);
@@ -104,6 +120,7 @@ __global__ void __launch_bounds__(kTh) k_link_batch(BatchView<T> b) {
         Acc<T> r2, s2;
         for (int l = item.y + (int)(threadIdx.x / G); l < item.z; l += kGroups) {
             const int p0 = __ldg(v.row_ptr + l), p1 = __ldg(v.row_ptr + l + 1);
+            if (b.nchunks > 0 && p1 - p0 > kLongRow) continue;  // done by its chunks
             LinkState<T> st;
             if (leader) st = load_link(v, l);
             const T s = group_gather_sum<G>(g, v.col_idx, v.x, p0, p1);
@@ -115,13 +132,51 @@ __global__ void __launch_bounds__(kTh) k_link_batch(BatchView<T> b) {
             b.part_l[2 * it] = R2;
             b.part_l[2 * it + 1] = S2;
             __threadfence();
-            const int nit = b.litem_off[item.x + 1] - b.litem_off[item.x];
-            fin = atomicAdd(b.arrive + item.x, 1u) == (unsigned)(nit - 1);
+            fin = instance_done(b, item.x);
         }
         __syncthreads();
-        if (fin) {  // every link item of this instance is in
+        if (fin && warp == 0) {  // every part of this instance is in
             __threadfence();
-            finish_instance(b, item.x, red);
+            finish_instance(b, item.x, lane);
+        }
+    }
+    // chunks of the longer links: one warp each, as in the single-instance row kernel
+    for (int q = blockIdx.x * kWarps + warp; q < b.nchunks; q += gridDim.x * kWarps) {
+        const int i = __ldg(b.chunk_inst + q);
+        const Ctl* c = b.ctls + i;
+        if (c->stop) continue;  // warp-uniform
+        const int4 ch = __ldg(b.chunks + q);
+        const T s = warp_gather_sum(v.col_idx, v.x, ch.y, ch.z, lane);
+        int done = 0;
+        if (lane == 0) {
+            b.carry[q] = s;
+            __threadfence();
+            const int p0 = __ldg(v.row_ptr + ch.x), p1 = __ldg(v.row_ptr + ch.x + 1);
+            const int nch = (p1 - p0 + kChunk - 1) / kChunk;
+            done = atomicAdd(b.arrive_c + ch.w, 1) == nch - 1;
+        }
+        done = __shfl_sync(0xffffffffu, done, 0);
+        if (!done) continue;
+        __threadfence();
+        const int p0 = __ldg(v.row_ptr + ch.x), p1 = __ldg(v.row_ptr + ch.x + 1);
+        const int nch = (p1 - p0 + kChunk - 1) / kChunk;
+        const T t = warp_sum_slots(b.carry + ch.w, nch, lane);
+        int whole = 0;
+        if (lane == 0) {
+            const T alpha = (T)c->alpha, rho = (T)c->rho, inv_rho = (T)(1.0 / c->rho);
+            Acc<T> r2, s2;
+            b.arrive_c[ch.w] = 0;
+            const LinkState<T> st = load_link(v, ch.x);
+            link_epilogue(v, ch.x, st, t, p1 - p0, alpha, rho, inv_rho, r2, s2);
+            b.part_c[2 * ch.w] = r2.value();
+            b.part_c[2 * ch.w + 1] = s2.value();
+            __threadfence();
+            whole = instance_done(b, i);
+        }
+        whole = __shfl_sync(0xffffffffu, whole, 0);
+        if (whole) {
+            __threadfence();
+            finish_instance(b, i, lane);
         }
     }
 }
@@ -257,8 +312,8 @@ int blocks_for(long long count) {
 
 }  // namespace
 
-cudaError_t batch_grids(int precision, int lanes, int nsitems, int nlitems, int* grid_s,
-                        int* grid_l, int* grid_e) {
+cudaError_t batch_grids(int precision, int lanes, int nsitems, int nlitems, int nchunks,
+                        int* grid_s, int* grid_l, int* grid_e) {
     int dev = 0, sms = 0, os = 0, ol = 0, oe = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
@@ -270,7 +325,8 @@ cudaError_t batch_grids(int precision, int lanes, int nsitems, int nlitems, int*
     if (os < 1 || ol < 1 || oe < 1) return cudaErrorInvalidConfiguration;
     const long long gs = (long long)os * sms, gl = (long long)ol * sms, ge = (long long)oe * sms;
     *grid_s = (int)(gs < nsitems ? gs : nsitems);
-    *grid_l = (int)(gl < nlitems ? gl : nlitems);
+    const long long need_l = std::max<long long>(nlitems, ((long long)nchunks + kWarps - 1) / kWarps);
+    *grid_l = (int)(gl < need_l ? gl : need_l);
     *grid_e = (int)(ge < nsitems ? ge : nsitems);
     return cudaSuccess;
 }

@@ -143,8 +143,18 @@ struct BatchView {
     double* hist;    // [count][max(hist_len, 1)][3]
     const signed char* sched;  // [count][sched_stride]
     int sched_stride;
-    unsigned int* arrive;  // [count] link items of the instance done in this iteration
+    unsigned int* arrive;  // [count] link items (and chunked links) of the instance done
     int lanes;             // lanes per link in the link kernel: 4, 8, 16 or 32
+    // links of more than kLongRow streams, summed by whole warps in chunks (the stacked
+    // problem's chunk table; chunks never cross an instance)
+    const int4* chunks;    // [nchunks] (link, first entry, end entry, first chunk of link)
+    int nchunks;
+    const int* chunk_inst; // [nchunks] instance of each chunk
+    const int* coff;       // [count + 1] chunk range of each instance
+    const int* crows;      // [count] chunked links of each instance
+    T* carry;              // [nchunks] chunk sums
+    int* arrive_c;         // [nchunks] chunks of a link done (at its first chunk)
+    double* part_c;        // [2 nchunks] residual terms of a chunked link (at its first chunk)
 };
 
 // Profiling event after a kernel: an external event node while the stream is being
@@ -158,8 +168,8 @@ inline cudaError_t record_kernel_event(cudaEvent_t ev, cudaStream_t st) {
                : cudaEventRecord(ev, st);
 }
 
-cudaError_t batch_grids(int precision, int lanes, int nsitems, int nlitems, int* grid_s,
-                        int* grid_l, int* grid_e);
+cudaError_t batch_grids(int precision, int lanes, int nsitems, int nlitems, int nchunks,
+                        int* grid_s, int* grid_l, int* grid_e);
 cudaError_t check_blocks(int count, const int64_t* stream_off, const int64_t* link_off,
                          long long n, const int64_t* route_ptr, const int* route_links, int* err,
                          cudaStream_t st);

@@ -124,4 +124,41 @@ __device__ __forceinline__ T group_gather_sum(const Group& g, const int* __restr
     return s;
 }
 
+// Sum of x over entries [e0, e1) by one warp: lane k takes e0 + k, e0 + k + 32, ... four
+// at a time, then a shuffle tree (a fixed order).
+template <typename T>
+__device__ __forceinline__ T warp_gather_sum(const int* __restrict__ col_idx,
+                                             const T* __restrict__ x, int e0, int e1, int lane) {
+    T s = T(0);
+    for (int e = e0 + lane; e < e1; e += 128) {
+        const int i0 = __ldg(col_idx + e);
+        const int i1 = e + 32 < e1 ? __ldg(col_idx + e + 32) : -1;
+        const int i2 = e + 64 < e1 ? __ldg(col_idx + e + 64) : -1;
+        const int i3 = e + 96 < e1 ? __ldg(col_idx + e + 96) : -1;
+        const T a = __ldg(x + i0);
+        const T b = i1 >= 0 ? __ldg(x + i1) : T(0);
+        const T c = i2 >= 0 ? __ldg(x + i2) : T(0);
+        const T d = i3 >= 0 ? __ldg(x + i3) : T(0);
+        s += (a + b) + (c + d);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    return s;
+}
+
+// Sum of the n chunk slots of one row by one warp, in a fixed order; the slots were
+// written by other blocks of this launch, so they are read from L2.
+template <typename T>
+__device__ __forceinline__ T warp_sum_slots(const T* slots, int n, int lane) {
+    T s = T(0);
+    int q = lane;
+    for (; q + 96 < n; q += 128)
+        s += (__ldcg(slots + q) + __ldcg(slots + q + 32)) +
+             (__ldcg(slots + q + 64) + __ldcg(slots + q + 96));
+    for (; q < n; q += 32) s += __ldcg(slots + q);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    return s;
+}
+
 }  // namespace pmp

@@ -188,10 +188,12 @@ def workload(name, seed=None, scale=None):
     return random_instance(n, m, lo, hi, **spec)
 
 
-def batched_instances(count=256, seed=0):
+def batched_instances(count=256, seed=0, congested=False):
     """Batched-solve recipe: `count` independent instances, n log-uniform in [1e3, 1e5],
     m = n/10, routes of 2..8 uniform links, capacities U[1,10] times a per-link U[0.3,1]
-    degradation factor, 70% log utilities, box [0, 20]."""
+    degradation factor, 70% log utilities, box [0, 20].  congested=True draws the links of
+    every route from a truncated Zipf(1.1) instead (a few links carry most streams), the
+    congestion scenario of the batched recipe."""
     rng = np.random.default_rng(seed)
     ns = np.exp(rng.uniform(np.log(1e3), np.log(1e5), size=count)).astype(np.int64)
     seeds = rng.integers(0, 2**31 - 1, size=count)
@@ -199,7 +201,8 @@ def batched_instances(count=256, seed=0):
     for n, s in zip(ns, seeds):
         m = max(8, int(n) // 10)
         out.append(random_instance(int(n), m, 2, 8, seed=int(s), frac_log=0.7,
-                                   box=(0.0, 20.0), degrade=(0.3, 1.0)))
+                                   box=(0.0, 20.0), degrade=(0.3, 1.0),
+                                   link_dist="zipf" if congested else "uniform"))
     return out
 
 

@@ -82,18 +82,16 @@ def test_batch_instances_stop_independently(batch):
 
 
 def test_batch_equals_single_solves(batch):
-    """Same rows, same arithmetic: bit-identical to solving each instance alone, except
-    where the single-instance kernels sum a link above 256 streams by whole warps in
-    chunks (the Zipf instance), which changes the FP32 summation order of that link."""
+    """Same rows, same arithmetic: bit-identical to solving each instance alone, including
+    the Zipf instance, whose links above 256 streams are summed by whole warps in chunks
+    of 2,048 entries on both paths (8 lanes per shorter link, the default partition)."""
     from paper_2509_10722_b300 import capi
+    assert np.bincount(batch[-1]["route_links"], minlength=batch[-1]["m"]).max() > 2 * 2048
     g = _run_batch(batch, 200, 0)
     for i, inst in enumerate(batch):
         with capi.Problem(inst, precision=0, history=64) as p:
             p.solve(200, 0.0)
             x, lam, info = p.get()
-        if np.bincount(inst["route_links"], minlength=inst["m"]).max() > 256:
-            assert rel(g["x"][i], x) <= 1e-5 and rel(g["lam"][i], lam) <= 1e-5, i
-            continue
         assert np.array_equal(g["x"][i], x), i
         assert np.array_equal(g["lam"][i], lam), i
         assert abs(g["info"][i]["objective"] - info["objective"]) <= 1e-12 * max(1.0, abs(info["objective"]))
