@@ -22,6 +22,8 @@
 // dx/dS = x / sqrt(D), dx/dw = 1 / (rho sqrt(D)); unclipped linear stream, dx/dS = 1/L,
 // dx/dw = 1 / (rho L); a stream at a bound of its box, 0.  Only x_k and ps_k of every
 // iteration are needed; they are recomputed segment by segment from checkpoints.
+// Links of more than kLongRow streams (row schedule) are summed by whole warps in chunks,
+// as in the forward row kernel.
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
@@ -38,6 +40,23 @@ namespace {
 constexpr int kTh = 256;
 constexpr int kGroup = 8;
 
+// Transpose of the link step of one link, given sa = (R Abar)_l and sb = (R Bbar)_l.
+template <typename T>
+__device__ __forceinline__ void adj_link_epilogue(const AdjView<T>& a, int l, T sa, T sb, int deg,
+                                                  T alpha, T rho, const T* __restrict__ ps_k) {
+    const View<T>& v = a.v;
+    const T yb = a.yb[l] + sb;
+    const T zsb = a.zsb[l];
+    const T deg1 = (T)(deg + 1);
+    const T t = sa + alpha * rho * yb - alpha * zsb;
+    const T psb = t / deg1 + alpha * zsb;
+    a.Rxb[l] = t / deg1;
+    const bool open = ps_k[l] > -v.c[l];  // slack prox not at its bound
+    a.zsb[l] = (T(1) - alpha) * zsb + (open ? psb : T(0));
+    a.yb[l] = yb - (open ? psb / rho : T(0));
+    if (!open) a.cb[l] -= psb;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kTh) k_adj_link(AdjView<T> a, const T* __restrict__ ps_k,
                                                  const double* __restrict__ rho_ptr) {
@@ -50,6 +69,7 @@ __global__ void __launch_bounds__(kTh) k_adj_link(AdjView<T> a, const T* __restr
     for (int l = blockIdx.x * kGroups + (int)(threadIdx.x / kGroup); l < v.m;
          l += gridDim.x * kGroups) {
         const int p0 = __ldg(v.row_ptr + l), p1 = __ldg(v.row_ptr + l + 1);
+        if (a.abc && p1 - p0 > kLongRow) continue;  // done by its chunks
         T sa = T(0), sb = T(0);  // R Abar, R Bbar: fixed order over the link's streams
         for (int e = p0 + g.thread_rank(); e < p1; e += kGroup) {
             const T2 ab = a.ab[__ldg(v.col_idx + e)];
@@ -61,17 +81,53 @@ __global__ void __launch_bounds__(kTh) k_adj_link(AdjView<T> a, const T* __restr
             sa += g.shfl_down(sa, o);
             sb += g.shfl_down(sb, o);
         }
-        if (!leader) continue;
-        const T yb = a.yb[l] + sb;
-        const T zsb = a.zsb[l];
-        const T deg1 = (T)(p1 - p0 + 1);
-        const T t = sa + alpha * rho * yb - alpha * zsb;
-        const T psb = t / deg1 + alpha * zsb;
-        a.Rxb[l] = t / deg1;
-        const bool open = ps_k[l] > -v.c[l];  // slack prox not at its bound
-        a.zsb[l] = (T(1) - alpha) * zsb + (open ? psb : T(0));
-        a.yb[l] = yb - (open ? psb / rho : T(0));
-        if (!open) a.cb[l] -= psb;
+        if (leader) adj_link_epilogue(a, l, sa, sb, p1 - p0, alpha, rho, ps_k);
+    }
+    if (!a.abc) return;
+    // chunks of the longer links: one warp each; the warp that completes a link sums its
+    // chunk slots in a fixed order and runs the link's transpose step
+    const int lane = threadIdx.x & 31;
+    for (int q = blockIdx.x * (kTh / 32) + (int)(threadIdx.x >> 5); q < v.nchunks;
+         q += gridDim.x * (kTh / 32)) {
+        const int4 ch = __ldg(v.chunks + q);  // (link, first entry, end entry, first chunk)
+        T sa = T(0), sb = T(0);
+        for (int e = ch.y + lane; e < ch.z; e += 64) {
+            const T2 u = a.ab[__ldg(v.col_idx + e)];
+            const T2 w = e + 32 < ch.z ? a.ab[__ldg(v.col_idx + e + 32)] : T2{T(0), T(0)};
+            sa += u.x + w.x;
+            sb += u.y + w.y;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            sa += __shfl_down_sync(0xffffffffu, sa, o);
+            sb += __shfl_down_sync(0xffffffffu, sb, o);
+        }
+        const int p0 = __ldg(v.row_ptr + ch.x), p1 = __ldg(v.row_ptr + ch.x + 1);
+        const int nch = (p1 - p0 + kChunk - 1) / kChunk;
+        int done = 0;
+        if (lane == 0) {
+            a.abc[q] = T2{sa, sb};
+            __threadfence();
+            done = atomicAdd(v.arrive_l + ch.w, 1) == nch - 1;
+        }
+        done = __shfl_sync(0xffffffffu, done, 0);
+        if (!done) continue;
+        __threadfence();
+        T ta = T(0), tb = T(0);
+        for (int k = lane; k < nch; k += 32) {
+            const T2 u = __ldcg(a.abc + ch.w + k);
+            ta += u.x;
+            tb += u.y;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            ta += __shfl_down_sync(0xffffffffu, ta, o);
+            tb += __shfl_down_sync(0xffffffffu, tb, o);
+        }
+        if (lane == 0) {
+            v.arrive_l[ch.w] = 0;
+            adj_link_epilogue(a, ch.x, ta, tb, p1 - p0, alpha, rho, ps_k);
+        }
     }
 }
 

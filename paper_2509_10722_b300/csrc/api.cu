@@ -1041,6 +1041,7 @@ int adjoint_impl(num_problem* h, int64_t K, int64_t Kc, const double* xbar, int 
     a.zsb = (T*)A(sizeof(T) * M);
     a.Rxb = (T*)A(sizeof(T) * M);
     a.cb = (T*)A(sizeof(T) * M);
+    if (h->chunks && h->nchunks > 0) a.abc = (T2*)A(sizeof(T2) * (size_t)h->nchunks);
     T* tape_x = (T*)A(sizeof(T) * N * (size_t)Kc);
     T* tape_ps = (T*)A(sizeof(T) * M * (size_t)Kc);
     double* tape_rho = (double*)A(sizeof(double) * (size_t)Kc);

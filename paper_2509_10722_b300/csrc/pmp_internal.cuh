@@ -198,6 +198,7 @@ struct AdjView {
     T* Rxb;                       // Rx_bar [m]
     T* cb;                        // dJ/dc [m]
     T* wb;                        // dJ/dw [n]
+    typename Pair<T>::type* abc;  // [v.nchunks] chunk sums of (Abar, Bbar) of long links
 };
 template <typename T>
 cudaError_t adjoint_init(const AdjView<T>& a, const double* xbar, int objective, cudaStream_t st);

@@ -57,6 +57,27 @@ def test_alpha2_adjoint_equals_reference(small_a2, precision, tol):
     assert rel(gc, rc) <= tol and rel(gw, rw) <= tol
 
 
+@pytest.fixture(scope="module")
+def skewed():
+    """Zipf link choice: the hottest link has 3,342 streams (two chunks of 2,048 entries)
+    and 14 links have more than 256, so the backward link pass takes its chunk path."""
+    inst = W.random_instance(6000, 30, 1, 4, seed=43, link_dist="zipf", frac_log=0.7,
+                             box=(0.0, 20.0))
+    deg = np.bincount(inst["route_links"], minlength=inst["m"])
+    assert deg.max() > 2048 and (deg > 256).sum() > 5
+    return inst
+
+
+@pytest.mark.parametrize("precision,tol", [(1, 1e-9), (0, 1e-3)])
+def test_skewed_adjoint_equals_reference(skewed, precision, tol):
+    iters = 120
+    dec = oracle_run(skewed, iters)["decisions"]
+    gc, gw, J = _gpu_adjoint(skewed, iters, precision, sched=dec)
+    rc, rw, rJ = adjoint_ref.gradients(skewed, iters, dec)
+    assert abs(J - rJ) <= max(tol, 1e-12) * abs(rJ)
+    assert rel(gc, rc) <= tol and rel(gw, rw) <= tol
+
+
 def test_vjp_equals_reference(small):
     iters = 120
     dec = oracle_run(small, iters)["decisions"]
