@@ -731,6 +731,12 @@ def run_adjoint(args):
             e1.record(stream)
             e1.synchronize()
             t_adj = e0.elapsed_time(e1)
+            # one segment (checkpoint_every = 0): the forward run tapes every iteration
+            e0.record(stream)
+            cg1, wg1, J1 = p.adjoint(iters, 0)
+            e1.record(stream)
+            e1.synchronize()
+            t_one = e0.elapsed_time(e1)
             p.reset()
             e0.record(stream)
             p.solve(iters, 0.0)
@@ -739,7 +745,10 @@ def run_adjoint(args):
             t_fwd = e0.elapsed_time(e1)
         grads[name] = (cg, wg)
         out[name] = {"adjoint_ms": t_adj, "forward_ms": t_fwd, "ratio": t_adj / t_fwd,
-                     "objective": J}
+                     "objective": J, "one_segment_ms": t_one,
+                     "one_segment_ratio": t_one / t_fwd,
+                     "one_segment_equal": bool(np.array_equal(cg, cg1) and
+                                               np.array_equal(wg, wg1))}
     rel = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))
     line = {"metric": "adjoint of 500 unrolled PMP iterations (dJ/dc, dJ/dw), c5",
             "value": out["fp32"]["adjoint_ms"], "unit": "ms", "higher_is_better": False,

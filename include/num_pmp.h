@@ -231,9 +231,11 @@ NUM_API int num_set_weights(num_problem* h, const double* w);
  * NULL).  The derivative runs the adjoint of every step backwards: transposed gathers over
  * R and the Jacobians of the stream prox (zero at the box bounds) and of the slack prox.
  * It keeps the full iterate every checkpoint_every iterations (0: only at the start) and
- * recomputes each segment (the iteration is deterministic), storing x and the slack flow
- * of each iteration of the segment: device memory about
- * checkpoint_every * (n + m) values + (iters / checkpoint_every) iterates.  A set rho
+ * recomputes each segment but the last (the iteration is deterministic; the last one is
+ * recorded by the forward run itself), storing x and the slack flow of each iteration of
+ * the segment: device memory about checkpoint_every * (n + m) values +
+ * (iters / checkpoint_every) iterates.  checkpoint_every = 0 (one segment) recomputes
+ * nothing, at the cost of iters * (n + m) stored values.  A set rho
  * schedule applies to the forward run.  The handle is left at the forward result. */
 NUM_API int num_adjoint(num_problem* h, int64_t iters, int32_t checkpoint_every,
                         const double* xbar, int32_t objective, double* c_grad, double* w_grad,

@@ -1066,14 +1066,35 @@ int adjoint_impl(num_problem* h, int64_t K, int64_t Kc, const double* xbar, int 
     } while (0)
     AK(order_after_legacy(h), "ordering");
     if (xbar) AK(cudaMemcpyAsync(xbar_dev, xbar, 8 * N, cudaMemcpyHostToDevice, st), "copy xbar");
-    // forward K iterations from the zero state, keeping the state at every segment start
+    // run `cnt` iterations one at a time, keeping rho, x and the slack flow of each
+    auto tape_segment = [&](int64_t cnt) -> cudaError_t {
+        for (int64_t i = 0; i < cnt; ++i) {
+            cudaError_t r = pmp::record_rho(h->ctl, tape_rho + i, st);
+            if (r == cudaSuccess) r = run_iterations(h, 1);
+            pmp::note_launches(h->kpi);
+            if (r == cudaSuccess)
+                r = cudaMemcpyAsync(tape_x + N * (size_t)i, h->x, sizeof(T) * N,
+                                    cudaMemcpyDeviceToDevice, st);
+            if (r == cudaSuccess)
+                r = cudaMemcpyAsync(tape_ps + M * (size_t)i, h->ps, sizeof(T) * M,
+                                    cudaMemcpyDeviceToDevice, st);
+            if (r != cudaSuccess) return r;
+        }
+        return cudaSuccess;
+    };
+    // forward K iterations from the zero state, keeping the state at every segment start;
+    // the last segment is taped on the way, so the backward sweep starts without a recompute
     AK(zero_state(h), "zeroing the state");
     for (int64_t s = 0; s < nseg; ++s) {
         const int64_t cnt = std::min<int64_t>(Kc, K - s * Kc);
         AK(copy_state(h, ckpt + sb * (size_t)s, true), "checkpoint");
         AK(pmp::ctl_arm(h->ctl, s * Kc + cnt, 0.0, st), "arming");
-        AK(run_iterations(h, (int)cnt), "forward iterations");
-        pmp::note_launches(cnt * h->kpi);
+        if (s < nseg - 1) {
+            AK(run_iterations(h, (int)cnt), "forward iterations");
+            pmp::note_launches(cnt * h->kpi);
+        } else {
+            AK(tape_segment(cnt), "forward iterations of the last segment");
+        }
     }
     if (objective_out) {
         AK(h->prec == NUM_FUSED_FP32
@@ -1087,19 +1108,14 @@ int adjoint_impl(num_problem* h, int64_t K, int64_t Kc, const double* xbar, int 
     AK(copy_state(h, ckpt + sb * (size_t)nseg, true), "final state");
     a.v = make_view<T>(h);
     AK(pmp::adjoint_init<T>(a, xbar_dev, objective, st), "adjoint init");
-    // backward, one segment at a time: recompute its iterates (deterministic), then sweep
+    // backward, one segment at a time: recompute its iterates (deterministic; the last
+    // segment's are taped already), then sweep
     for (int64_t s = nseg - 1; s >= 0; --s) {
         const int64_t cnt = std::min<int64_t>(Kc, K - s * Kc);
-        AK(copy_state(h, ckpt + sb * (size_t)s, false), "restore checkpoint");
-        AK(pmp::ctl_arm(h->ctl, s * Kc + cnt, 0.0, st), "arming");
-        for (int64_t i = 0; i < cnt; ++i) {
-            AK(pmp::record_rho(h->ctl, tape_rho + i, st), "recording rho");
-            AK(run_iterations(h, 1), "recomputing an iteration");
-            pmp::note_launches(h->kpi);
-            AK(cudaMemcpyAsync(tape_x + N * (size_t)i, h->x, sizeof(T) * N,
-                               cudaMemcpyDeviceToDevice, st), "tape x");
-            AK(cudaMemcpyAsync(tape_ps + M * (size_t)i, h->ps, sizeof(T) * M,
-                               cudaMemcpyDeviceToDevice, st), "tape ps");
+        if (s < nseg - 1) {
+            AK(copy_state(h, ckpt + sb * (size_t)s, false), "restore checkpoint");
+            AK(pmp::ctl_arm(h->ctl, s * Kc + cnt, 0.0, st), "arming");
+            AK(tape_segment(cnt), "recomputing a segment");
         }
         for (int64_t i = cnt - 1; i >= 0; --i)
             AK(pmp::adjoint_step<T>(a, tape_x + N * (size_t)i, tape_ps + M * (size_t)i,
