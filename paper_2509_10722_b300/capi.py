@@ -360,19 +360,28 @@ def num_destroy(h):
 
 def stack_instances(insts):
     """Stack instance dicts block-diagonally: returns (stream_off, link_off, stacked dict)
-    with global link ids (pure index bookkeeping for num_batch_create)."""
-    so = np.zeros(len(insts) + 1, dtype=np.int64)
-    lo = np.zeros(len(insts) + 1, dtype=np.int64)
+    with global link ids (pure index bookkeeping for num_batch_create).  Each output array
+    is allocated once and filled slice by slice."""
+    k = len(insts)
+    so = np.zeros(k + 1, dtype=np.int64)
+    lo = np.zeros(k + 1, dtype=np.int64)
+    eo = np.zeros(k + 1, dtype=np.int64)
     for i, t in enumerate(insts):
         so[i + 1] = so[i] + int(t["n"])
         lo[i + 1] = lo[i] + int(t["m"])
-    nnz_off = np.cumsum([0] + [int(t["route_ptr"][-1]) for t in insts])
-    route_ptr = np.concatenate([[0]] + [np.asarray(t["route_ptr"][1:], np.int64) + nnz_off[i]
-                                        for i, t in enumerate(insts)]).astype(np.int64)
-    route_links = np.concatenate([np.asarray(t["route_links"], np.int64) + lo[i]
-                                  for i, t in enumerate(insts)]).astype(np.int32)
-    cat = {k: np.concatenate([np.asarray(t[k]) for t in insts])
-           for k in ("c", "utype", "w", "lo", "hi")}
+        eo[i + 1] = eo[i] + int(t["route_ptr"][-1])
+    if lo[-1] >= 2**31:
+        raise ValueError("the stacked problem has 2^31 or more links")
+    route_ptr = np.empty(int(so[-1]) + 1, dtype=np.int64)
+    route_ptr[0] = 0
+    route_links = np.empty(int(eo[-1]), dtype=np.int32)
+    for i, t in enumerate(insts):
+        np.add(np.asarray(t["route_ptr"][1:], np.int64), eo[i],
+               out=route_ptr[so[i] + 1:so[i + 1] + 1])
+        np.add(np.asarray(t["route_links"], np.int32), np.int32(lo[i]),
+               out=route_links[eo[i]:eo[i + 1]])
+    cat = {key: np.concatenate([np.asarray(t[key]) for t in insts])
+           for key in ("c", "utype", "w", "lo", "hi")}
     stacked = dict(n=int(so[-1]), m=int(lo[-1]), route_ptr=route_ptr, route_links=route_links,
                    **cat)
     return so, lo, stacked
