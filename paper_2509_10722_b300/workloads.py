@@ -173,8 +173,9 @@ WORKLOAD_ITERS = {"c1": 2000}
 
 
 def workload(name, seed=None, scale=None):
-    """Instance for a named workload.  `scale` (0 < scale <= 1) shrinks n and m together,
-    keeping route lengths and distributions, for the CPU-sized stand-ins of a large case."""
+    """Instance for a named workload.  `scale` (> 0) multiplies n and m together, keeping
+    route lengths and distributions: below 1 for CPU-sized stand-ins of a large case, above
+    1 for larger instances of the same recipe."""
     spec = dict(WORKLOADS[name])
     if seed is not None:
         spec["seed"] = seed
