@@ -1,0 +1,160 @@
+// Host-side internals shared by the C-ABI sources (api.cu, adjoint_api.cu, batch_api.cu):
+// the problem handle, error reporting, device allocation through the handle, the view of a
+// handle's arrays that the kernels take, and handle creation.  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstring>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "num_pmp.h"
+#include "pmp_internal.cuh"
+
+struct num_problem {
+    int64_t n = 0, m = 0, nnz = 0;
+    int Js = 0, Jl = 0;
+    num_params prm{};
+    num_allocator alloc{};
+    bool custom_alloc = false;
+    cudaStream_t user_stream = nullptr;
+    cudaStream_t stream = nullptr;  // where the work goes
+    bool own_stream = false;
+    cudaEvent_t legacy_ev = nullptr;
+    int device = 0;
+    int prec = 0;
+    std::vector<std::pair<void*, size_t>> blocks;
+
+    int *col_ptr = nullptr, *row_idx = nullptr, *row_ptr = nullptr, *col_idx = nullptr;
+    int2 *tiles_s = nullptr, *tiles_l = nullptr;
+    int ntiles_s = 0, ntiles_l = 0, tile_s = 0, tile_l = 0, grid_s = 0, grid_l = 0;
+    int sched_kind = NUM_SCHEDULE_ROWS;  // fused paths: row kernels or merge-path tiles
+    int* perm = nullptr;                 // caller's index of the stream at each position
+    uint8_t* ut = nullptr;               // utility types, only if some stream has U = -w / x
+    int4* chunks = nullptr;              // row kernels: chunks of the long links
+    int nchunks = 0;
+    int narrive_l = 0;                   // entries of arrive_l
+    void *wt = nullptr, *lo = nullptr, *hi = nullptr, *c = nullptr;
+    void *x = nullptr, *Z = nullptr, *pby = nullptr, *zs = nullptr, *Rx = nullptr, *ps = nullptr;
+    void *carry_s = nullptr, *carry_l = nullptr;
+    int *arrive_s = nullptr, *arrive_l = nullptr;
+    double *part_s = nullptr, *part_l = nullptr;
+    int plain_nb = 0;
+    void *A = nullptr, *B = nullptr, *tS = nullptr, *tR = nullptr, *tL = nullptr, *RxN = nullptr,
+         *pbar = nullptr, *y = nullptr;
+    pmp::Ctl* ctl = nullptr;
+    pmp::Ctl* ctl_host = nullptr;  // pinned
+    double* hist = nullptr;
+    signed char* sched = nullptr;
+    int sched_len = 0;
+    double* x64 = nullptr;
+    double* y64 = nullptr;
+    double* part_exp = nullptr;
+    int exp_blocks = 0;
+    int box_uniform = 0;
+    double lo_u = 0.0, hi_u = 0.0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    double last_eps_tol = 0.0;
+    // profiling: evs[0] before the first kernel of a batch of iterations, then one event
+    // after every kernel; per-kernel totals
+    std::vector<cudaEvent_t> evs;
+    double kernel_ms[pmp::kPlainKernelsPerIter] = {};
+    long long kernel_runs[pmp::kPlainKernelsPerIter] = {};
+    int kpi = 0;  // kernels per iteration
+};
+
+namespace pmp {
+namespace host {
+
+extern thread_local std::string g_last_error;  // the message num_last_error() returns
+
+int fail(int code, const std::string& msg);           // sets the message, returns code
+int cuda_fail(cudaError_t e, const char* what);        // NUM_ERR_CUDA with the CUDA error
+int finish_cuda(cudaError_t e, const char* what);      // NUM_OK or cuda_fail
+
+constexpr int kMaxGrid = 8192;
+constexpr int kExportBlocksMax = 1024;
+
+void* dev_alloc(num_problem* h, size_t bytes);  // through the handle's allocator; NULL on failure
+void dev_free(num_problem* h, void* p);
+void destroy_handle(num_problem* h);
+cudaError_t order_after_legacy(num_problem* h);  // order the handle's stream after the legacy one
+cudaError_t run_iterations(num_problem* h, int count);
+cudaError_t zero_state(num_problem* h);
+
+template <typename T>
+View<T> make_view(const num_problem* h) {
+    View<T> v;
+    std::memset(&v, 0, sizeof(v));
+    v.n = (int)h->n;
+    v.m = (int)h->m;
+    v.nnz = (int)h->nnz;
+    v.Js = h->Js;
+    v.Jl = h->Jl;
+    v.col_ptr = h->col_ptr;
+    v.row_idx = h->row_idx;
+    v.row_ptr = h->row_ptr;
+    v.col_idx = h->col_idx;
+    v.tiles_s = h->tiles_s;
+    v.tiles_l = h->tiles_l;
+    v.ntiles_s = h->ntiles_s;
+    v.ntiles_l = h->ntiles_l;
+    v.tile_s = h->tile_s;
+    v.tile_l = h->tile_l;
+    v.wt = (const T*)h->wt;
+    v.lo = (const T*)h->lo;
+    v.hi = (const T*)h->hi;
+    v.lo_u = (T)h->lo_u;
+    v.hi_u = (T)h->hi_u;
+    v.box_uniform = h->box_uniform;
+    v.c = (const T*)h->c;
+    v.x = (T*)h->x;
+    v.Z = (T*)h->Z;
+    v.pby = (typename View<T>::T2*)h->pby;
+    v.zs = (T*)h->zs;
+    v.Rx = (T*)h->Rx;
+    v.ps = (T*)h->ps;
+    v.carry_s = (typename View<T>::T2*)h->carry_s;
+    v.carry_l = (T*)h->carry_l;
+    v.arrive_s = h->arrive_s;
+    v.arrive_l = h->arrive_l;
+    v.part_s = h->part_s;
+    v.part_l = h->part_l;
+    v.grid_s = h->grid_s;
+    v.grid_l = h->grid_l;
+    v.chunks = h->chunks;
+    v.nchunks = h->nchunks;
+    v.perm = h->perm;
+    v.ut = h->ut;
+    v.ctl = h->ctl;
+    v.hist = h->hist;
+    v.sched = h->sched;
+    v.A = (T*)h->A;
+    v.B = (T*)h->B;
+    v.tS = (T*)h->tS;
+    v.tR = (T*)h->tR;
+    v.tL = (T*)h->tL;
+    v.RxN = (T*)h->RxN;
+    v.pbar = (T*)h->pbar;
+    v.y = (T*)h->y;
+    return v;
+}
+
+// Instances of a batch: host arrays of count + 1 offsets into the stacked numbering.
+struct BatchSpec {
+    int count;
+    const int64_t* stream_off;
+    const int64_t* link_off;
+};
+
+int create_impl(num_problem** out, int64_t n, int64_t m, const int64_t* route_ptr,
+                const int32_t* route_links, const double* c, const uint8_t* utype,
+                const double* w, const double* lo, const double* hi, const num_params* p,
+                void* cuda_stream, bool on_device, const BatchSpec* batch = nullptr);
+
+}  // namespace host
+}  // namespace pmp
