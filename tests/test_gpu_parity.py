@@ -108,6 +108,16 @@ def _cases():
         return lo, lo + rng.uniform(0.1, 3.0, n)
     yield "per_stream_box", W.random_instance(3000, 200, 1, 6, seed=10, box=box), {}
 
+    def fixed(rng, n):
+        lo = rng.uniform(0.0, 0.3, n)
+        hi = lo + rng.uniform(0.1, 3.0, n)
+        pin = rng.random(n) < 0.2  # a fifth of the streams have a fixed rate (lo = hi)
+        hi[pin] = lo[pin] + 0.05 * (lo[pin] == 0)  # log streams need hi > 0
+        lo[pin] = hi[pin]
+        return lo, hi
+    yield "fixed_rates", W.random_instance(3000, 300, 1, 6, seed=11, frac_log=0.5,
+                                           frac_alpha2=0.2, box=fixed), {}
+
 
 CASES = list(_cases())
 
