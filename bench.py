@@ -287,15 +287,23 @@ class Solver:
         self.kernel_ms = None
         self.kernel_runs = None
         self.bytes = None
+        self.phase_ms = np.zeros(3)  # create, solve, get (CUDA events on the stream)
 
     def step(self):
-        c, d = self.capi, self.d
+        c, d, torch = self.capi, self.d, self.torch
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        ev[0].record(self.stream)
         h = c.num_create_device(self.n, self.m, d["route_ptr"], d["route_links"], d["c"],
                                 d["utype"], d["w"], d["lo"], d["hi"], self.params,
                                 self.stream.cuda_stream)
         try:
+            ev[1].record(self.stream)
             status, iters = c.num_solve(h, self.max_iters, self.eps)
+            ev[2].record(self.stream)
             info = c.num_get_device(h, self.x, self.p)
+            ev[3].record(self.stream)
+            ev[3].synchronize()
+            self.phase_ms += [ev[q].elapsed_time(ev[q + 1]) for q in range(3)]
             ms, runs = c.num_get_kernel_times(h)
             if self.kernel_ms is None:
                 self.kernel_ms, self.kernel_runs = np.zeros_like(ms), np.zeros_like(runs)
@@ -309,6 +317,7 @@ class Solver:
     def reset_kernel_times(self):
         self.kernel_ms = None
         self.kernel_runs = None
+        self.phase_ms = np.zeros(3)
 
 
 def timed(solver, torch, steps):
@@ -477,6 +486,11 @@ def run_ours(args, dist):
                        "precision": "FP32 iterates, FP64 residuals / stopping test / rho",
                        "schedule": args.schedule},
             "time_to_tol_s": ms_max / args.steps / 1e3,
+            "phases_ms_per_step": {
+                "create (validation, stream ordering, CSR build, tables)":
+                    float(fp32.phase_ms[0] / args.steps),
+                "solve (num_solve to the stopping test)": float(fp32.phase_ms[1] / args.steps),
+                "get (FP64 export, objective)": float(fp32.phase_ms[2] / args.steps)},
             "iters_to_tol": it_per_solve[-1], "converged": all(s == 0 for s in statuses),
             "final_residuals": {"primal": info["primal"], "dual": info["dual"],
                                 "eps_tol": info["eps_tol"]},
