@@ -70,6 +70,9 @@ static double clip(double v, double lo, double hi) {
 /* argmin_x  -w log x + (rho/2) sum_t (x - zeta_t)^2 over the box, with S = sum_t zeta_t and
  * L = number of terminals: the positive root of rho L x^2 - rho S x - w = 0, clipped. */
 double oracle_prox_log(double S, double L, double w, double rho, double lo, double hi) {
+#if ORACLE_PLANT == 18
+    L = 1.0;
+#endif
     double D = S * S + 4.0 * w * L / rho;
     double x;
 #if ORACLE_PLANT == 1
@@ -118,7 +121,13 @@ double oracle_prox_alpha2(double S, double L, double w, double rho, double lo, d
         else
             a = mid;
     }
+#if ORACLE_PLANT == 17
+    (void)lo;
+    (void)hi;
+    return 0.5 * (a + b);
+#else
     return clip(0.5 * (a + b), lo, hi);
+#endif
 }
 
 /* argmin_p  I{p + c >= 0} + (rho/2)(p - zeta)^2 = max(zeta, -c). */
@@ -266,7 +275,11 @@ int oracle_solve(int64_t n, int64_t m, const int64_t* route_ptr, const int32_t* 
         }
         for (int64_t t = 0; t < J; ++t) {
             int64_t l = link_of[t];
+#if ORACLE_PLANT == 15
+            double d = p[t] - pbar[l];
+#else
             double d = (p[t] - pbar[l]) - (p_prev[t] - pbar_prev[l]);
+#endif
             s2 += d * d;
         }
         double rnorm = sqrt(r2);
@@ -307,7 +320,11 @@ int oracle_solve(int64_t n, int64_t m, const int64_t* route_ptr, const int32_t* 
             break;
         }
         /* 8. residual balancing every `period` iterations, then the dual rescale */
+#if ORACLE_PLANT == 16
+        if (prm->period > 0 && k > 1 && (k - 1) % prm->period == 0) {
+#else
         if (prm->period > 0 && k % prm->period == 0) {
+#endif
             int8_t dec;
             if (rho_replay && n_updates < rho_replay_len) {
                 dec = rho_replay[n_updates];

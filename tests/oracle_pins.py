@@ -465,4 +465,8 @@ PLANTS = {
     12: "z projection averages over traffic terminals only",
     13: "log prox not clipped to the box",
     14: "alpha = 2 prox with the wrong sign of the S x^2 term",
+    15: "dual residual without the previous iterate (p - pbar, not its change)",
+    16: "rho updated one iteration late",
+    17: "alpha = 2 prox not clipped to the box",
+    18: "log prox ignoring the number of terminals of the stream",
 }
