@@ -88,3 +88,25 @@ def test_pruned_warm_start(inst):
     ref = oracle_run(pr, 100_000, eps=eps)
     u = kkt.utility(pr, ref["x"])
     assert abs(iw["objective"] - u) <= 1e-5 * abs(u) and abs(ic["objective"] - u) <= 1e-5 * abs(u)
+
+
+def test_fp32_then_fp64_reaches_a_tolerance_fp32_cannot():
+    """Precision escalation through the state API: FP32 iterates down to eps_abs = 1e-7,
+    the state moved into an FP64 handle (num_get_state / num_set_state carry FP64 values
+    whatever the handle's precision), then FP64 to 1e-10.  The result passes the same
+    stopping test as a solve in FP64 from zero and agrees with the oracle's solution at
+    that tolerance."""
+    from paper_2509_10722_b300 import capi
+    inst = W.workload("c1")
+    with capi.Problem(inst, precision=capi.NUM_FUSED_FP32) as p32, \
+            capi.Problem(inst, precision=capi.NUM_FUSED_FP64) as p64:
+        st, it32 = p32.solve(100_000, 1e-7)
+        assert st == 0
+        p64.set_state(p32.get_state())
+        st, it64 = p64.solve(100_000, 1e-10)
+        assert st == 0
+        x, lam, info = p64.get()
+    assert info["primal"] < info["eps_tol"] and info["dual"] < info["eps_tol"]
+    ref = oracle_run(inst, 100_000, eps=1e-10)
+    assert ref["converged"]
+    assert rel(x, ref["x"]) <= 1e-6 and rel(lam, ref["lam"]) <= 1e-6
