@@ -472,8 +472,9 @@ cudaError_t occupancy(int tile_s, int tile_l, int* occ_s, int* occ_l) {
 
 }  // namespace
 
-int fused_tile_items_stream(int precision) { return precision == 0 ? 2048 : 2048; }
-int fused_tile_items_link(int precision) { return precision == 0 ? 4096 : 4096; }
+// Default tile sizes (items = nonzeros + rows per tile); the same for both precisions.
+int fused_tile_items_stream(int /*precision*/) { return 2048; }
+int fused_tile_items_link(int /*precision*/) { return 4096; }
 
 size_t fused_smem_stream(int precision, int tile) {
     return precision == 0 ? smem_stream<float>(tile) : smem_stream<double>(tile);

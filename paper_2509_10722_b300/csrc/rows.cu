@@ -7,11 +7,11 @@
 //     route entries four at a time (four independent gathers of (pbar, y) in flight);
 //   link kernel: a group of G lanes per link (G = 32 / rows per warp), the link's own
 //     state loaded by the group leader before the gathers, R x summed by the group in a
-//     fixed order, the link epilogue by the leader; links with more than kLongRow streams
-//     are cut into fixed chunks of kChunk entries, each chunk summed by one warp (four
-//     gathers in flight per lane) into its own slot, and the warp that brings the row's
-//     arrival count to the number of chunks sums the slots in a fixed order and runs the
-//     epilogue (no waiting, deterministic);
+//     fixed order, the link epilogue by the leader; links with more than kLongRow (256)
+//     streams are cut into fixed chunks of kChunk (2048) entries, each chunk summed by one
+//     warp (four gathers in flight per lane) into its own slot, and the warp that brings
+//     the row's arrival count to the number of chunks sums the slots in a fixed order and
+//     runs the epilogue (no waiting, deterministic);
 //   the last block of the link kernel finishes the iteration (FP64 residual sums, stopping
 //   test, rho), as in the tile engine.
 // Per-thread residual partial sums are compensated sums in the iteration precision; block
@@ -57,11 +57,6 @@ __global__ void __launch_bounds__(kTh) k_stream_rows(View<T> v) {
     const double s = block_sum(acc.value(), red);
     if (threadIdx.x == 0) v.part_s[blockIdx.x] = s;
 }
-template <typename T>
-size_t stream_smem() {
-    return 0;
-}
-
 // ---- link kernel ---------------------------------------------------------------------------------
 
 template <typename T>
@@ -140,13 +135,7 @@ __global__ void __launch_bounds__(kTh) k_link_rows(View<T> v) {
 
 template <typename T>
 cudaError_t rows_occupancy(int* occ_s, int* occ_l) {
-    cudaError_t e = cudaSuccess;
-    if (stream_smem<T>() > 48 * 1024)
-        e = cudaFuncSetAttribute(k_stream_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)stream_smem<T>());
-    if (e != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ_s, k_stream_rows<T>, kTh,
-                                                      stream_smem<T>());
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ_s, k_stream_rows<T>, kTh, 0);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ_l, k_link_rows<T>, kTh, 0);
 }
@@ -174,7 +163,7 @@ cudaError_t rows_grids(int precision, int n, int m, int nchunks, int* grid_s, in
 
 template <typename T>
 cudaError_t rows_iteration(const View<T>& v, cudaStream_t st, cudaEvent_t* evs) {
-    k_stream_rows<T><<<v.grid_s, kTh, stream_smem<T>(), st>>>(v);
+    k_stream_rows<T><<<v.grid_s, kTh, 0, st>>>(v);
     if (evs) record_kernel_event(evs[0], st);
     k_link_rows<T><<<v.grid_l, kTh, 0, st>>>(v);
     if (evs) record_kernel_event(evs[1], st);
