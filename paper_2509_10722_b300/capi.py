@@ -12,7 +12,10 @@ import os
 
 import numpy as np
 
-_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "lib", "libnum_pmp.so")
+# the in-tree library; NUM_PMP_LIBRARY may name another build of it (the debug build,
+# lib/libnum_pmp_debug.so, whose kernels check every gathered index)
+_LIB_PATH = os.environ.get("NUM_PMP_LIBRARY") or os.path.join(
+    os.path.dirname(os.path.abspath(__file__)), "lib", "libnum_pmp.so")
 
 NUM_OK = 0
 NUM_NOT_CONVERGED = 1

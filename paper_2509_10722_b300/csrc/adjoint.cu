@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(kTh) k_adj_link(AdjView<T> a, const T* __restr
         if (a.abc && p1 - p0 > kLongRow) continue;  // done by its chunks
         T sa = T(0), sb = T(0);  // R Abar, R Bbar: fixed order over the link's streams
         for (int e = p0 + g.thread_rank(); e < p1; e += kGroup) {
-            const T2 ab = a.ab[__ldg(v.col_idx + e)];
+            const T2 ab = a.ab[checked_index(__ldg(v.col_idx + e), v.n, v.dbg)];
             sa += ab.x;
             sb += ab.y;
         }
@@ -92,8 +92,9 @@ __global__ void __launch_bounds__(kTh) k_adj_link(AdjView<T> a, const T* __restr
         const int4 ch = __ldg(v.chunks + q);  // (link, first entry, end entry, first chunk)
         T sa = T(0), sb = T(0);
         for (int e = ch.y + lane; e < ch.z; e += 64) {
-            const T2 u = a.ab[__ldg(v.col_idx + e)];
-            const T2 w = e + 32 < ch.z ? a.ab[__ldg(v.col_idx + e + 32)] : T2{T(0), T(0)};
+            const T2 u = a.ab[checked_index(__ldg(v.col_idx + e), v.n, v.dbg)];
+            const T2 w = e + 32 < ch.z ? a.ab[checked_index(__ldg(v.col_idx + e + 32), v.n, v.dbg)]
+                                       : T2{T(0), T(0)};
             sa += u.x + w.x;
             sb += u.y + w.y;
         }
@@ -140,7 +141,7 @@ __global__ void __launch_bounds__(kTh) k_adj_stream(AdjView<T> a, const T* __res
     for (int j = blockIdx.x * kTh + threadIdx.x; j < v.n; j += gridDim.x * kTh) {
         const int p = __ldg(v.col_ptr + j), pn = __ldg(v.col_ptr + j + 1);
         T r = T(0);
-        for (int e = p; e < pn; ++e) r += a.Rxb[__ldg(v.row_idx + e)];
+        for (int e = p; e < pn; ++e) r += a.Rxb[checked_index(__ldg(v.row_idx + e), v.m, v.dbg)];
         const T xbk = a.xb[j] + r;
         const T x = x_k[j], L = (T)(pn - p), wt = v.wt[j];
         const T lo = v.box_uniform ? v.lo_u : v.lo[j];

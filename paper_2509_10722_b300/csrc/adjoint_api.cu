@@ -184,6 +184,11 @@ int adjoint_impl(num_problem* h, int64_t K, int64_t Kc, const double* xbar, int 
     AK(cudaStreamSynchronize(st), "adjoint");
 #undef AK
     if (objective_out) *objective_out = h->ctl_host->objective;
+    const int dbg_rc = check_debug_flag(h);
+    if (dbg_rc != NUM_OK) {
+        release();
+        return dbg_rc;
+    }
     release();
     return NUM_OK;
 }
@@ -194,6 +199,7 @@ extern "C" {
 
 int num_adjoint(num_problem* h, int64_t iters, int32_t checkpoint_every, const double* xbar,
                 int32_t objective, double* c_grad, double* w_grad, double* objective_out) {
+    TraceRange trace("num_adjoint");
     g_last_error.clear();
     if (!h) return fail(NUM_ERR_INVALID, "handle is NULL");
     if (iters < 1) return fail(NUM_ERR_INVALID, "iters must be >= 1");

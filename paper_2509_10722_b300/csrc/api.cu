@@ -155,6 +155,7 @@ cudaError_t zero_state(num_problem* h) {
     auto z = [&](void* p, size_t bytes) {
         if (p && e == cudaSuccess) e = cudaMemsetAsync(p, 0, bytes, st);
     };
+    z(h->dbg, sizeof(unsigned int));
     z(h->x, ts * h->n);
     z(h->Z, ts * h->n);
     z(h->pby, 2 * ts * h->m);
@@ -327,6 +328,7 @@ int create_impl(num_problem** out, int64_t n, int64_t m, const int64_t* route_pt
     h->part_s = (double*)A(sizeof(double) * npart);
     h->part_l = (double*)A(sizeof(double) * 2 * npart);
     h->ctl = (Ctl*)A(sizeof(Ctl));
+    h->dbg = (unsigned int*)A(sizeof(unsigned int));
     h->hist = (double*)A(sizeof(double) * 3 * (size_t)(prm.history > 0 ? prm.history : 1));
     h->x64 = (double*)A(8 * N);
     h->y64 = (double*)A(8 * M);
@@ -518,6 +520,20 @@ int create_impl(num_problem** out, int64_t n, int64_t m, const int64_t* route_pt
     return NUM_OK;
 }
 
+int check_debug_flag(num_problem* h) {
+#ifdef PMP_DEBUG_BOUNDS
+    unsigned int flag = 0;
+    cudaError_t e = cudaMemcpyAsync(&flag, h->dbg, sizeof(flag), cudaMemcpyDeviceToHost,
+                                    h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "reading the debug flag");
+    if (flag) return fail(NUM_ERR_STATE, "debug build: a kernel gathered at an index out of range");
+#else
+    (void)h;
+#endif
+    return NUM_OK;
+}
+
 int finish_cuda(cudaError_t e, const char* what) {
     if (e != cudaSuccess) return cuda_fail(e, what);
     return NUM_OK;
@@ -551,6 +567,7 @@ int num_create(num_problem** out, int64_t n, int64_t m, const int64_t* route_ptr
                const int32_t* route_links, const double* c, const uint8_t* utype,
                const double* w, const double* lo, const double* hi, const num_params* p,
                void* cuda_stream) {
+    TraceRange trace("num_create");
     return create_impl(out, n, m, route_ptr, route_links, c, utype, w, lo, hi, p, cuda_stream,
                        false);
 }
@@ -559,6 +576,7 @@ int num_create_device(num_problem** out, int64_t n, int64_t m, const int64_t* ro
                       const int32_t* route_links, const double* c, const uint8_t* utype,
                       const double* w, const double* lo, const double* hi,
                       const num_params* p, void* cuda_stream) {
+    TraceRange trace("num_create_device");
     return create_impl(out, n, m, route_ptr, route_links, c, utype, w, lo, hi, p, cuda_stream,
                        true);
 }
@@ -601,6 +619,7 @@ int num_set_rho_schedule(num_problem* h, const int8_t* decisions, int64_t count)
 }
 
 int num_solve(num_problem* h, int64_t max_iters, double eps_abs, int64_t* iters_done) {
+    TraceRange trace("num_solve");
     g_last_error.clear();
     if (iters_done) *iters_done = 0;
     if (!h) return fail(NUM_ERR_INVALID, "handle is NULL");
@@ -633,6 +652,7 @@ int num_solve(num_problem* h, int64_t max_iters, double eps_abs, int64_t* iters_
     const long long max_launches = (max_iters + K - 1) / K + 1;
     for (long long it = 0;; ++it) {
         if (it >= max_launches) return fail(NUM_ERR_STATE, "the iteration limit was not honoured");
+        TraceRange replay("num_solve: replay of check_every iterations");
         const long long k_before = h->ctl_host->k;
         if (h->prm.use_graph)
             e = cudaGraphLaunch(h->graph_exec, st);
@@ -650,6 +670,8 @@ int num_solve(num_problem* h, int64_t max_iters, double eps_abs, int64_t* iters_
         if (h->ctl_host->stop != pmp::RUNNING) break;
     }
     if (iters_done) *iters_done = h->ctl_host->k - k0;
+    const int dbg_rc = check_debug_flag(h);
+    if (dbg_rc != NUM_OK) return dbg_rc;
     switch (h->ctl_host->stop) {
         case pmp::CONVERGED: return NUM_OK;
         case pmp::LIMIT: return NUM_NOT_CONVERGED;
@@ -658,6 +680,7 @@ int num_solve(num_problem* h, int64_t max_iters, double eps_abs, int64_t* iters_
 }
 
 static int get_impl(const num_problem* hc, double* x, double* prices, double* info, bool dev) {
+    TraceRange trace("num_get");
     g_last_error.clear();
     if (!hc) return fail(NUM_ERR_INVALID, "handle is NULL");
     num_problem* h = const_cast<num_problem*>(hc);

@@ -55,7 +55,7 @@ __global__ void __launch_bounds__(kTh) k_stream_batch(BatchView<T> b) {
             const T xo = v.x[j], Zo = v.Z[j], wt = __ldg(v.wt + j);
             const T lo = v.box_uniform ? v.lo_u : __ldg(v.lo + j);
             const T hi = v.box_uniform ? v.hi_u : __ldg(v.hi + j);
-            const V sum = route_sum<T>(v.row_idx, v.pby, p, pn);
+            const V sum = route_sum<T>(v.row_idx, v.pby, p, pn, v.m, v.dbg);
             stream_epilogue(v, j, sum, (T)(pn - p), xo, Zo, wt, lo, hi, alpha, inv_rho, acc);
         }
         const double s = block_sum(acc.value(), red);
@@ -123,7 +123,7 @@ __global__ void __launch_bounds__(kTh) k_link_batch(BatchView<T> b) {
             if (b.nchunks > 0 && p1 - p0 > kLongRow) continue;  // done by its chunks
             LinkState<T> st;
             if (leader) st = load_link(v, l);
-            const T s = group_gather_sum<G>(g, v.col_idx, v.x, p0, p1);
+            const T s = group_gather_sum<G>(g, v.col_idx, v.x, p0, p1, v.n, v.dbg);
             if (leader) link_epilogue(v, l, st, s, p1 - p0, alpha, rho, inv_rho, r2, s2);
         }
         const double R2 = block_sum(r2.value(), red);
@@ -146,7 +146,7 @@ __global__ void __launch_bounds__(kTh) k_link_batch(BatchView<T> b) {
         const Ctl* c = b.ctls + i;
         if (c->stop) continue;  // warp-uniform
         const int4 ch = __ldg(b.chunks + q);
-        const T s = warp_gather_sum(v.col_idx, v.x, ch.y, ch.z, lane);
+        const T s = warp_gather_sum(v.col_idx, v.x, ch.y, ch.z, lane, v.n, v.dbg);
         int done = 0;
         if (lane == 0) {
             b.carry[q] = s;

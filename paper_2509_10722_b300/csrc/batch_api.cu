@@ -281,6 +281,7 @@ int num_batch_create(num_batch** out, int32_t count, const int64_t* stream_off,
                      const int32_t* route_links, const double* c, const uint8_t* utype,
                      const double* w, const double* lo, const double* hi, const num_params* p,
                      void* cuda_stream) {
+    TraceRange trace("num_batch_create");
     g_last_error.clear();
     if (!out) return fail(NUM_ERR_INVALID, "out is NULL");
     *out = nullptr;
@@ -433,6 +434,7 @@ int num_batch_set_rho_schedules(num_batch* b, const int8_t* decisions, int64_t l
 
 int num_batch_solve(num_batch* b, int64_t max_iters, double eps_abs, int64_t* iters_done,
                     int32_t* status) {
+    TraceRange trace("num_batch_solve");
     g_last_error.clear();
     if (!b) return fail(NUM_ERR_INVALID, "batch is NULL");
     if (max_iters < 0) return fail(NUM_ERR_INVALID, "max_iters must be >= 0");
@@ -466,6 +468,7 @@ int num_batch_solve(num_batch* b, int64_t max_iters, double eps_abs, int64_t* it
         long long done_prev = 0;
         for (long long it = 0;; ++it) {
             if (it >= max_launches) return fail(NUM_ERR_STATE, "the iteration limit was not honoured");
+            TraceRange replay("num_batch_solve: replay of check_every iterations");
             e = h->prm.use_graph ? cudaGraphLaunch(b->graph_exec, st) : batch_run(b, K);
             if (e != cudaSuccess) return cuda_fail(e, "launching iterations");
             pmp::note_launches((long long)K * 2);
@@ -511,11 +514,14 @@ int num_batch_solve(num_batch* b, int64_t max_iters, double eps_abs, int64_t* it
         if (stt == pmp::NONFINITE) rc = NUM_ERR_NUMERIC;
         else if (stt != pmp::CONVERGED && rc == NUM_OK) rc = NUM_NOT_CONVERGED;
     }
+    const int dbg_rc = check_debug_flag(h);
+    if (dbg_rc != NUM_OK) return dbg_rc;
     if (rc == NUM_ERR_NUMERIC) return fail(rc, "a residual of some instance became non-finite");
     return rc;
 }
 
 int num_batch_get(const num_batch* bc, double* x, double* prices, double* info) {
+    TraceRange trace("num_batch_get");
     g_last_error.clear();
     if (!bc) return fail(NUM_ERR_INVALID, "batch is NULL");
     num_batch* b = const_cast<num_batch*>(bc);
@@ -590,6 +596,7 @@ int num_batch_set_schedule(num_batch* b, const num_batch_schedule* cfg) {
 
 int num_batch_autotune(num_batch* b, int32_t trial_iters, num_batch_schedule* chosen,
                        double* trial_ms, int32_t max_trials, int32_t* ntrials) {
+    TraceRange trace("num_batch_autotune");
     g_last_error.clear();
     if (!b) return fail(NUM_ERR_INVALID, "batch is NULL");
     if (trial_iters < 1 || trial_iters > 500)

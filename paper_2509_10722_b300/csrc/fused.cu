@@ -105,7 +105,7 @@ struct StreamPolicy {
     __device__ int ntiles() const { return v.ntiles_s; }
     __device__ V* carry() const { return v.carry_s; }
     __device__ int* arrive() const { return v.arrive_s; }
-    __device__ V gather(int l) const { return __ldg(v.pby + l); }
+    __device__ V gather(int l) const { return __ldg(v.pby + checked_index(l, v.m, v.dbg)); }
     // stream j: sum = (A_j, B_j), L = |j|
     __device__ void epilogue(int j, V sum, int L, T& acc0, T&) const {
         const T Lf = (T)L;
@@ -135,7 +135,7 @@ struct LinkPolicy {
     __device__ int ntiles() const { return v.ntiles_l; }
     __device__ V* carry() const { return v.carry_l; }
     __device__ int* arrive() const { return v.arrive_l; }
-    __device__ V gather(int j) const { return __ldg(v.x + j); }
+    __device__ V gather(int j) const { return __ldg(v.x + checked_index(j, v.n, v.dbg)); }
     // link l: sum = (R x)_l, deg = number of streams on l
     __device__ void epilogue(int l, V Rxn, int deg, T& acc0, T& acc1) const {
         const T2 py = v.pby[l];

@@ -11,6 +11,8 @@
 #include <utility>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "num_pmp.h"
 #include "pmp_internal.cuh"
 
@@ -46,7 +48,8 @@ struct num_problem {
     void *A = nullptr, *B = nullptr, *tS = nullptr, *tR = nullptr, *tL = nullptr, *RxN = nullptr,
          *pbar = nullptr, *y = nullptr;
     pmp::Ctl* ctl = nullptr;
-    pmp::Ctl* ctl_host = nullptr;  // pinned
+    pmp::Ctl* ctl_host = nullptr;
+    unsigned int* dbg = nullptr;  // out-of-range gather flag of debug builds (device)  // pinned
     double* hist = nullptr;
     signed char* sched = nullptr;
     int sched_len = 0;
@@ -76,6 +79,16 @@ int fail(int code, const std::string& msg);           // sets the message, retur
 int cuda_fail(cudaError_t e, const char* what);        // NUM_ERR_CUDA with the CUDA error
 int finish_cuda(cudaError_t e, const char* what);      // NUM_OK or cuda_fail
 
+// NVTX range for the life of a scope: names the library's phases (create, solve, each
+// replay of a graph of iterations, export, adjoint, batch calls) in profiler traces.  With
+// no tool attached a range costs a pointer check.
+struct TraceRange {
+    explicit TraceRange(const char* name) { nvtxRangePushA(name); }
+    ~TraceRange() { nvtxRangePop(); }
+    TraceRange(const TraceRange&) = delete;
+    TraceRange& operator=(const TraceRange&) = delete;
+};
+
 constexpr int kMaxGrid = 8192;
 constexpr int kExportBlocksMax = 1024;
 
@@ -85,6 +98,8 @@ void destroy_handle(num_problem* h);
 cudaError_t order_after_legacy(num_problem* h);  // order the handle's stream after the legacy one
 cudaError_t run_iterations(num_problem* h, int count);
 cudaError_t zero_state(num_problem* h);
+// NUM_OK, or in a debug build NUM_ERR_STATE if a kernel recorded an out-of-range gather
+int check_debug_flag(num_problem* h);
 
 template <typename T>
 View<T> make_view(const num_problem* h) {
@@ -131,6 +146,7 @@ View<T> make_view(const num_problem* h) {
     v.perm = h->perm;
     v.ut = h->ut;
     v.ctl = h->ctl;
+    v.dbg = h->dbg;
     v.hist = h->hist;
     v.sched = h->sched;
     v.A = (T*)h->A;

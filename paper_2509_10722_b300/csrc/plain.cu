@@ -21,7 +21,7 @@ __global__ void k_plain_spmvT(View<double> v) {
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < v.n; j += gridDim.x * blockDim.x) {
         double a = 0.0, b = 0.0;
         for (int e = v.col_ptr[j]; e < v.col_ptr[j + 1]; ++e) {
-            const int l = v.row_idx[e];
+            const int l = checked_index(v.row_idx[e], v.m, v.dbg);
             a += v.pbar[l];
             b += v.y[l];
         }
@@ -57,7 +57,8 @@ __global__ void k_plain_spmv(View<double> v) {
     const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
     for (long long l = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; l < v.m; l += warps) {
         double s = 0.0;
-        for (int e = v.row_ptr[l] + lane; e < v.row_ptr[l + 1]; e += 32) s += v.x[v.col_idx[e]];
+        for (int e = v.row_ptr[l] + lane; e < v.row_ptr[l + 1]; e += 32)
+            s += v.x[checked_index(v.col_idx[e], v.n, v.dbg)];
         s = warp_sum(s);
         if (lane == 0) v.RxN[l] = s;
     }

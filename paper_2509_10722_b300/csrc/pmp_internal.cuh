@@ -40,6 +40,23 @@ struct Ctl {
 
 enum Stop { RUNNING = 0, CONVERGED = 1, LIMIT = 2, NONFINITE = 3 };
 
+// Debug builds (-DPMP_DEBUG_BOUNDS, `build.py --debug`): every gathered index is checked
+// against the length of the vector it indexes; one out of range is recorded in *dbg (the
+// solve then returns NUM_ERR_STATE) and replaced by 0, so the access stays inside the
+// vector.  Release builds compile the check away.
+__device__ __forceinline__ int checked_index(int i, int bound, unsigned int* dbg) {
+#ifdef PMP_DEBUG_BOUNDS
+    if ((unsigned)i >= (unsigned)bound) {
+        atomicOr(dbg, 1u);
+        return 0;
+    }
+#else
+    (void)bound;
+    (void)dbg;
+#endif
+    return i;
+}
+
 // Row kernels (rows.cu): a link with more than kLongRow streams is summed by whole warps
 // in chunks of kChunk entries (one chunk per warp; 256 and 2048 measured best on a
 // Zipf(1.1) instance); persistent grids are capped at kMaxRowsGrid blocks.
@@ -99,6 +116,7 @@ struct View {
     T* RxN;                     // this iteration's R x
     T* pbar;                    // split arrays of the plain path
     T* y;
+    unsigned int* dbg;  // debug builds: set when a gathered index was out of range
 };
 
 // ---- launchers (fused.cu) -------------------------------------------------------------------

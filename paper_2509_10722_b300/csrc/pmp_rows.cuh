@@ -32,13 +32,15 @@ struct Acc<double> {
 template <typename T>
 __device__ __forceinline__ typename Pair<T>::type route_sum(const int* __restrict__ row_idx,
                                                            const typename Pair<T>::type* __restrict__ pby,
-                                                           int p, int pn) {
+                                                           int p, int pn, int m, unsigned int* dbg) {
     using V = typename Pair<T>::type;
     V sum = vzero(V());
     int e = p;
     for (; e + 4 <= pn; e += 4) {
-        const int l0 = __ldg(row_idx + e), l1 = __ldg(row_idx + e + 1);
-        const int l2 = __ldg(row_idx + e + 2), l3 = __ldg(row_idx + e + 3);
+        const int l0 = checked_index(__ldg(row_idx + e), m, dbg);
+        const int l1 = checked_index(__ldg(row_idx + e + 1), m, dbg);
+        const int l2 = checked_index(__ldg(row_idx + e + 2), m, dbg);
+        const int l3 = checked_index(__ldg(row_idx + e + 3), m, dbg);
         const V g0 = __ldg(pby + l0), g1 = __ldg(pby + l1);
         const V g2 = __ldg(pby + l2), g3 = __ldg(pby + l3);
         sum = vadd(sum, g0);
@@ -46,7 +48,7 @@ __device__ __forceinline__ typename Pair<T>::type route_sum(const int* __restric
         sum = vadd(sum, g2);
         sum = vadd(sum, g3);
     }
-    for (; e < pn; ++e) sum = vadd(sum, __ldg(pby + __ldg(row_idx + e)));
+    for (; e < pn; ++e) sum = vadd(sum, __ldg(pby + checked_index(__ldg(row_idx + e), m, dbg)));
     return sum;
 }
 
@@ -109,12 +111,13 @@ __device__ __forceinline__ void link_epilogue(const View<T>& v, int l, const Lin
 // in a fixed order (lane-strided, two loads in flight per lane, then a shuffle tree).
 template <int G, typename T, class Group>
 __device__ __forceinline__ T group_gather_sum(const Group& g, const int* __restrict__ col_idx,
-                                              const T* __restrict__ x, int e0, int e1) {
+                                              const T* __restrict__ x, int e0, int e1, int n,
+                                              unsigned int* dbg) {
     const int sl = g.thread_rank();
     T s = T(0);
     for (int e = e0 + sl; e < e1; e += 2 * G) {
-        const int i0 = __ldg(col_idx + e);
-        const int i1 = e + G < e1 ? __ldg(col_idx + e + G) : -1;
+        const int i0 = checked_index(__ldg(col_idx + e), n, dbg);
+        const int i1 = e + G < e1 ? checked_index(__ldg(col_idx + e + G), n, dbg) : -1;
         const T a = __ldg(x + i0);
         const T b = i1 >= 0 ? __ldg(x + i1) : T(0);
         s += a + b;
@@ -128,13 +131,14 @@ __device__ __forceinline__ T group_gather_sum(const Group& g, const int* __restr
 // at a time, then a shuffle tree (a fixed order).
 template <typename T>
 __device__ __forceinline__ T warp_gather_sum(const int* __restrict__ col_idx,
-                                             const T* __restrict__ x, int e0, int e1, int lane) {
+                                             const T* __restrict__ x, int e0, int e1, int lane,
+                                             int n, unsigned int* dbg) {
     T s = T(0);
     for (int e = e0 + lane; e < e1; e += 128) {
-        const int i0 = __ldg(col_idx + e);
-        const int i1 = e + 32 < e1 ? __ldg(col_idx + e + 32) : -1;
-        const int i2 = e + 64 < e1 ? __ldg(col_idx + e + 64) : -1;
-        const int i3 = e + 96 < e1 ? __ldg(col_idx + e + 96) : -1;
+        const int i0 = checked_index(__ldg(col_idx + e), n, dbg);
+        const int i1 = e + 32 < e1 ? checked_index(__ldg(col_idx + e + 32), n, dbg) : -1;
+        const int i2 = e + 64 < e1 ? checked_index(__ldg(col_idx + e + 64), n, dbg) : -1;
+        const int i3 = e + 96 < e1 ? checked_index(__ldg(col_idx + e + 96), n, dbg) : -1;
         const T a = __ldg(x + i0);
         const T b = i1 >= 0 ? __ldg(x + i1) : T(0);
         const T c = i2 >= 0 ? __ldg(x + i2) : T(0);

@@ -51,7 +51,7 @@ __global__ void __launch_bounds__(kTh) k_stream_rows(View<T> v) {
         const T xo = v.x[j], Zo = v.Z[j], wt = __ldg(v.wt + j);
         const T lo = v.box_uniform ? v.lo_u : __ldg(v.lo + j);
         const T hi = v.box_uniform ? v.hi_u : __ldg(v.hi + j);
-        const V sum = route_sum<T>(row_idx, pby, p, pn);
+        const V sum = route_sum<T>(row_idx, pby, p, pn, v.m, v.dbg);
         stream_epilogue(v, j, sum, (T)(pn - p), xo, Zo, wt, lo, hi, alpha, inv_rho, acc);
     }
     const double s = block_sum(acc.value(), red);
@@ -81,7 +81,7 @@ __global__ void __launch_bounds__(kTh) k_link_rows(View<T> v) {
         if (p1 - p0 > kLongRow) continue;  // done by its chunks
         LinkState<T> st;
         if (leader) st = load_link(v, l);
-        const T s = group_gather_sum<kGroup>(g, col_idx, x, p0, p1);
+        const T s = group_gather_sum<kGroup>(g, col_idx, x, p0, p1, v.n, v.dbg);
         if (leader) link_epilogue(v, l, st, s, p1 - p0, alpha, rho, inv_rho, r2, s2);
     }
     // chunks of the longer links: one warp each (four gathers in flight per lane), so that
@@ -90,7 +90,7 @@ __global__ void __launch_bounds__(kTh) k_link_rows(View<T> v) {
     for (int q = blockIdx.x * kWarps + (int)(threadIdx.x >> 5); q < v.nchunks;
          q += gridDim.x * kWarps) {
         const int4 ch = __ldg(v.chunks + q);  // (row, first entry, end entry, first chunk)
-        const T s = warp_gather_sum(col_idx, x, ch.y, ch.z, lane);
+        const T s = warp_gather_sum(col_idx, x, ch.y, ch.z, lane, v.n, v.dbg);
         int fin = 0;
         if (lane == 0) {
             v.carry_l[q] = s;

@@ -31,6 +31,14 @@ def test_every_declared_symbol_is_exported(capi):
     assert set(names) == set(capi.EXPORTED)
 
 
+def test_debug_build_exports_the_same_symbols(capi):
+    """The debug build (gather bounds checks compiled in) has the same C ABI."""
+    path = B.build(debug=True)
+    lib = ctypes.CDLL(path)
+    for name in _declared():
+        assert hasattr(lib, name), name
+
+
 def test_strerror_and_defaults(capi):
     assert capi.num_strerror(0) == "ok"
     assert "invalid" in capi.num_strerror(-1)
