@@ -66,7 +66,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-iters", type=int, default=3)
     ap.add_argument("--ref-iters", type=int, default=1, help="oracle iterations per reference step")
-    ap.add_argument("--scenario", choices=["none", "warmstart", "adjoint"], default="none",
+    ap.add_argument("--scenario", choices=["none", "warmstart", "adjoint", "congestion"],
+                    default="none",
                     help="warmstart: degradation and failure re-solves of Sec. V-D; "
                          "adjoint: gradients of 500 unrolled iterations on c5")
     ap.add_argument("--congested", action="store_true",
@@ -668,6 +669,46 @@ def run_batched(args):
     print(json.dumps(line), flush=True)
 
 
+def run_congestion(args):
+    """The congestion experiment of Sec. V-C: the same network without and with 0.1% of its
+    links each added to 10% of the streams (m = 1e6 links, n = 5e5 streams, routes of
+    U{5..15} links), solved to eps_abs = 1e-4 in FP32 from zero.  The paper reports about
+    1,000 iterations uncongested and a few hundred more congested."""
+    import torch
+    from paper_2509_10722_b300 import capi
+    base, cong, hot = W.congestion_pair(scale=args.scale or 1.0)
+    stream = torch.cuda.Stream()
+    sp = stream.cuda_stream
+    out = {}
+    for name, inst in (("uncongested", base), ("congested", cong)):
+        deg = np.bincount(inst["route_links"], minlength=inst["m"])
+        with capi.Problem(inst, stream=sp, precision=0) as p:
+            p.solve(args.max_iters, args.eps)  # warm-up run of the same solve
+            p.reset()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st, it = p.solve(args.max_iters, args.eps)
+            e1.record(stream)
+            e1.synchronize()
+            x, lam, info = p.get()
+        out[name] = {"iterations": int(it), "converged": st == 0,
+                     "solve_ms": e0.elapsed_time(e1),
+                     "ms_per_iteration": e0.elapsed_time(e1) / max(int(it), 1),
+                     "nnz": int(inst["route_ptr"][-1]), "max_link_degree": int(deg.max()),
+                     "objective": info["objective"]}
+    u, c = out["uncongested"], out["congested"]
+    line = {"metric": "iterations to eps_abs 1e-4 with and without congestion (Sec. V-C)",
+            "value": c["iterations"] - u["iterations"], "unit": "extra iterations",
+            "higher_is_better": False, "n_gpus": 1, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "m = 1e6 links, n = 5e5 streams, routes U{5..15} uniform "
+                                   "links, c ~ U[1,10], 70% log, box [0,50]; congested: "
+                                   "0.1% of links each on 10% of the streams",
+                       "eps_abs": args.eps, "scale": args.scale},
+            "paper": "about 1,000 iterations uncongested, a few hundred more congested",
+            **out}
+    print(json.dumps(line), flush=True)
+
+
 def run_warmstart(args):
     """Re-solves after the perturbations of Sec. V-D on the solved c2 instance, FP32:
     degradation (each link has a 25% chance of a 50% capacity cut), warm (continue from the
@@ -790,6 +831,9 @@ def main():
         return
     if args.scenario == "warmstart":
         run_warmstart(args)
+        return
+    if args.scenario == "congestion":
+        run_congestion(args)
         return
     if args.workload == "c4":
         run_batched(args)

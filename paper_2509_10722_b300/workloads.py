@@ -150,6 +150,58 @@ def random_instance(n, m, len_lo, len_hi, *, seed=0, link_dist="uniform", zipf_s
                 utype=utype, w=w, lo=lo, hi=hi)
 
 
+def add_hot_links(inst, frac_links=0.001, frac_streams=0.10, seed=1):
+    """The congestion model of Sec. V-C on top of an instance: pick round(frac_links * m)
+    links at random and add each of them to the routes of round(frac_streams * n) streams
+    drawn at random (a stream that already uses the link is left as it is).  Every original
+    route stays the prefix of its new route; the hot links follow in the order they were
+    drawn.  Returns a new instance dict with its own route arrays (the rest is shared) and
+    the hot link ids."""
+    rng = np.random.default_rng(seed)
+    n, m = int(inst["n"]), int(inst["m"])
+    route_ptr = np.asarray(inst["route_ptr"], dtype=np.int64)
+    links = np.asarray(inst["route_links"], dtype=np.int32)
+    k = max(1, int(round(frac_links * m)))
+    s = max(1, int(round(frac_streams * n)))
+    hot = rng.choice(m, size=k, replace=False).astype(np.int32)
+    pair_s = np.concatenate([rng.choice(n, size=s, replace=False) for _ in range(k)])
+    pair_l = np.repeat(hot, s)
+    lengths = np.diff(route_ptr)
+    owner = np.repeat(np.arange(n, dtype=np.int64), lengths)
+    is_hot = np.zeros(m, dtype=bool)
+    is_hot[hot] = True
+    sel = is_hot[links]
+    if sel.any():  # (stream, link) pairs the routes already have
+        have = owner[sel] * m + links[sel].astype(np.int64)
+        keep = ~np.isin(pair_s.astype(np.int64) * m + pair_l, have)
+        pair_s, pair_l = pair_s[keep], pair_l[keep]
+    order = np.argsort(pair_s, kind="stable")
+    ps, pl = pair_s[order].astype(np.int64), pair_l[order]
+    extra = np.bincount(ps, minlength=n)
+    new_ptr = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(lengths + extra, out=new_ptr[1:])
+    out = np.empty(int(new_ptr[-1]), dtype=np.int32)
+    out[new_ptr[owner] + (np.arange(links.size, dtype=np.int64) - route_ptr[owner])] = links
+    rank = np.arange(ps.size, dtype=np.int64) - np.searchsorted(ps, ps, side="left")
+    out[new_ptr[ps] + lengths[ps] + rank] = pl
+    cong = dict(inst)
+    cong["route_ptr"] = new_ptr
+    cong["route_links"] = out
+    return cong, hot
+
+
+def congestion_pair(scale=1.0, seed=0):
+    """The uncongested and congested networks of Sec. V-C at the size of its degree
+    histograms (m = 1e6 links, n = 5e5 streams): routes of U{5..15} uniform links (mean
+    10), c ~ U[1,10], 70% log / 30% linear, w ~ U[0.5,2], box [0, 50]; the congested one
+    adds 0.1% of the links to 10% of the streams each.  `scale` shrinks n and m together."""
+    n = max(1, int(round(500_000 * scale)))
+    m = max(1, int(round(1_000_000 * scale)))
+    base = random_instance(n, m, 5, 15, seed=seed, frac_log=0.7, box=(0.0, 50.0))
+    cong, hot = add_hot_links(base, 0.001, 0.10, seed=seed + 1)
+    return base, cong, hot
+
+
 # ---------------------------------------------------------------------------------------------
 # The named workloads.  Sizes, distributions and boxes are the ones the instance recipes state;
 # C4 (batched) and C5 (differentiation) are listed for completeness of the recipe table.

@@ -98,3 +98,28 @@ def test_degrade_and_prune_bookkeeping():
     for old_j in np.setdiff1d(np.arange(inst["n"]), ks):
         old = inst["route_links"][inst["route_ptr"][old_j]:inst["route_ptr"][old_j + 1]]
         assert failed[old].any()
+
+
+def test_hot_links_follow_the_congestion_model():
+    """add_hot_links (Sec. V-C): 0.1% of the links each join 10% of the routes; original
+    routes stay prefixes, no route repeats a link, the rest of the instance is unchanged."""
+    base = W.random_instance(20_000, 5_000, 2, 6, seed=3)
+    cong, hot = W.add_hot_links(base, 0.001, 0.10, seed=4)
+    assert hot.size == 5 and len(set(hot.tolist())) == 5
+    rp0, rl0 = base["route_ptr"], base["route_links"]
+    rp1, rl1 = cong["route_ptr"], cong["route_links"]
+    assert rp1.size == rp0.size and np.all(np.diff(rp1) >= np.diff(rp0))
+    for j in range(base["n"]):
+        r0 = rl0[rp0[j]:rp0[j + 1]]
+        r1 = rl1[rp1[j]:rp1[j + 1]]
+        assert np.array_equal(r1[:r0.size], r0)
+        assert len(set(r1.tolist())) == r1.size
+        assert set(r1[r0.size:].tolist()) <= set(hot.tolist())
+    deg0 = np.bincount(rl0, minlength=base["m"])
+    deg1 = np.bincount(rl1, minlength=base["m"])
+    # each hot link reaches 10% of the streams (fewer only where a route already had it)
+    assert np.all(deg1[hot] >= 2_000) and np.all(deg1[hot] <= 2_000 + deg0[hot])
+    others = np.setdiff1d(np.arange(base["m"]), hot)
+    assert np.array_equal(deg1[others], deg0[others])
+    for k in ("c", "utype", "w", "lo", "hi"):
+        assert cong[k] is base[k]
