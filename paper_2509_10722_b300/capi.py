@@ -240,10 +240,15 @@ def num_solve(h, max_iters, eps_abs=-1.0):
     return rc, int(it.value)
 
 
-def num_get(h, n, m, x=True, prices=True):
-    """Host copies: returns (x[n] or None, prices[m] or None, info dict)."""
-    xa = np.empty(n) if x else None
-    pa = np.empty(m) if prices else None
+def num_get(h, n, m, x=True, prices=True, out_x=None, out_prices=None):
+    """Host copies: returns (x[n] or None, prices[m] or None, info dict).  out_x / out_prices
+    (float64 numpy arrays of n / m values, e.g. views of pinned memory) receive the copies
+    instead of new arrays."""
+    xa = (out_x if out_x is not None else np.empty(n)) if x else None
+    pa = (out_prices if out_prices is not None else np.empty(m)) if prices else None
+    for a, k, name in ((xa, n, "out_x"), (pa, m, "out_prices")):
+        if a is not None and (a.dtype != np.float64 or a.size != k or not a.flags.c_contiguous):
+            raise ValueError(f"{name} must be a contiguous float64 array of {k} values")
     info = np.zeros(NUM_INFO_LEN)
     _check(_lib.num_get(h, _hptr(xa), _hptr(pa), _hptr(info)))
     return xa, pa, {k: float(info[i]) for k, i in INFO.items()}
