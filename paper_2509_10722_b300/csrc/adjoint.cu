@@ -23,7 +23,7 @@
 // dx/dw = 1 / (rho L); a stream at a bound of its box, 0.  Only x_k and ps_k of every
 // iteration are needed; they are recomputed segment by segment from checkpoints.
 // Links of more than kLongRow streams (row schedule) are summed by whole warps in chunks,
-// as in the forward row kernel.
+// and streams with more than kLongRoute links by one warp each, as in the forward kernels.
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
@@ -132,46 +132,69 @@ __global__ void __launch_bounds__(kTh) k_adj_link(AdjView<T> a, const T* __restr
     }
 }
 
+// Transpose of the stream step of stream j, given r = (R' Rx_bar)_j.
+template <typename T>
+__device__ __forceinline__ void adj_stream_epilogue(const AdjView<T>& a, int j, T r, int len,
+                                                    const T* __restrict__ x_k, T alpha, T rho) {
+    using T2 = typename Pair<T>::type;
+    const View<T>& v = a.v;
+    const T xbk = a.xb[j] + r;
+    const T x = x_k[j], L = (T)len, wt = v.wt[j];
+    const T lo = v.box_uniform ? v.lo_u : v.lo[j];
+    const T hi = v.box_uniform ? v.hi_u : v.hi[j];
+    T dS = T(0), dw = T(0);
+    if (x > lo && x < hi) {
+        if (v.ut && v.ut[j] == 2) {
+            // rho L x^3 - rho S x^2 - w = 0 with S = L x - w / (rho x^2):
+            // f_x = rho L x^2 + 2 w / x, dx/dS = rho x^2 / f_x, dx/dw = 1 / f_x
+            const T fx = rho * L * x * x + T(2) * wt / x;
+            dS = rho * x * x / fx;
+            dw = T(1) / fx;
+        } else if (wt > T(0)) {
+            const T sqD = L * x + wt / (rho * x);
+            dS = x / sqD;
+            dw = T(1) / (rho * sqD);
+        } else {
+            dS = T(1) / L;
+            dw = T(1) / (rho * L);
+        }
+    }
+    const T Sb = xbk * dS;
+    a.wb[j] += xbk * dw;
+    const T t = a.Zb[j] + Sb;
+    a.xb[j] = alpha * L * t;
+    a.Zb[j] = (T(1) - alpha) * t;
+    T2 ab;
+    ab.x = -alpha * t;
+    ab.y = -Sb / rho;
+    a.ab[j] = ab;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kTh) k_adj_stream(AdjView<T> a, const T* __restrict__ x_k,
                                                    const double* __restrict__ rho_ptr) {
-    using T2 = typename Pair<T>::type;
     const View<T>& v = a.v;
     const T alpha = (T)a.alpha, rho = (T)*rho_ptr;
+    const bool split = v.nlong > 0;
     for (int j = blockIdx.x * kTh + threadIdx.x; j < v.n; j += gridDim.x * kTh) {
         const int p = __ldg(v.col_ptr + j), pn = __ldg(v.col_ptr + j + 1);
+        if (split && pn - p > kLongRoute) continue;  // summed by a warp below
         T r = T(0);
         for (int e = p; e < pn; ++e) r += a.Rxb[checked_index(__ldg(v.row_idx + e), v.m, v.dbg)];
-        const T xbk = a.xb[j] + r;
-        const T x = x_k[j], L = (T)(pn - p), wt = v.wt[j];
-        const T lo = v.box_uniform ? v.lo_u : v.lo[j];
-        const T hi = v.box_uniform ? v.hi_u : v.hi[j];
-        T dS = T(0), dw = T(0);
-        if (x > lo && x < hi) {
-            if (v.ut && v.ut[j] == 2) {
-                // rho L x^3 - rho S x^2 - w = 0 with S = L x - w / (rho x^2):
-                // f_x = rho L x^2 + 2 w / x, dx/dS = rho x^2 / f_x, dx/dw = 1 / f_x
-                const T fx = rho * L * x * x + T(2) * wt / x;
-                dS = rho * x * x / fx;
-                dw = T(1) / fx;
-            } else if (wt > T(0)) {
-                const T sqD = L * x + wt / (rho * x);
-                dS = x / sqD;
-                dw = T(1) / (rho * sqD);
-            } else {
-                dS = T(1) / L;
-                dw = T(1) / (rho * L);
-            }
-        }
-        const T Sb = xbk * dS;
-        a.wb[j] += xbk * dw;
-        const T t = a.Zb[j] + Sb;
-        a.xb[j] = alpha * L * t;
-        a.Zb[j] = (T(1) - alpha) * t;
-        T2 ab;
-        ab.x = -alpha * t;
-        ab.y = -Sb / rho;
-        a.ab[j] = ab;
+        adj_stream_epilogue(a, j, r, pn - p, x_k, alpha, rho);
+    }
+    // streams with more than kLongRoute links: one warp each, as in the forward kernel
+    const int lane = threadIdx.x & 31;
+    for (int q = blockIdx.x * (kTh / 32) + (int)(threadIdx.x >> 5); q < v.nlong;
+         q += gridDim.x * (kTh / 32)) {
+        const int j = __ldg(v.long_routes + q);
+        const int p = __ldg(v.col_ptr + j), pn = __ldg(v.col_ptr + j + 1);
+        T r = T(0);
+        for (int e = p + lane; e < pn; e += 32)
+            r += a.Rxb[checked_index(__ldg(v.row_idx + e), v.m, v.dbg)];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) r += __shfl_down_sync(0xffffffffu, r, o);
+        if (lane == 0) adj_stream_epilogue(a, j, r, pn - p, x_k, alpha, rho);
     }
 }
 

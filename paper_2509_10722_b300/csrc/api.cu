@@ -367,9 +367,10 @@ int create_impl(num_problem** out, int64_t n, int64_t m, const int64_t* route_pt
     int* d_lens = reorder ? (int*)A(4 * (N + 1)) : nullptr;
     int* d_ptr32 = reorder ? (int*)A(4 * (N + 1)) : nullptr;
     int* d_ptmp = reorder ? (int*)A(4 * pmp::scan_tmp_len(N + 1)) : nullptr;
-    int* d_ccount = rowk ? (int*)A(4 * (M + 1)) : nullptr;
-    int* d_coff = rowk ? (int*)A(4 * (M + 1)) : nullptr;
-    int* d_ctmp = rowk ? (int*)A(4 * pmp::scan_tmp_len(M + 1)) : nullptr;
+    const size_t NM = (N > M ? N : M) + 1;  // the chunk and long-route tables share these
+    int* d_ccount = rowk ? (int*)A(4 * NM) : nullptr;
+    int* d_coff = rowk ? (int*)A(4 * NM) : nullptr;
+    int* d_ctmp = rowk ? (int*)A(4 * pmp::scan_tmp_len(NM)) : nullptr;
     if (!ok) {
         destroy_handle(h);
         return fail(NUM_ERR_OOM, "device allocation failed");
@@ -503,6 +504,16 @@ int create_impl(num_problem** out, int64_t n, int64_t m, const int64_t* route_pt
         }
         if (h->nchunks > 0)
             CK(pmp::fill_chunks(h->row_ptr, (int)m, d_coff, h->chunks, st), "long-link chunks");
+        CK(pmp::count_long_routes(h->col_ptr, (int)n, d_ccount, d_coff, d_ctmp, &h->nlong, st),
+           "counting long routes");
+        h->long_routes = (int*)dev_alloc(h, sizeof(int) * (size_t)(h->nlong > 0 ? h->nlong : 1));
+        if (!h->long_routes) {
+            destroy_handle(h);
+            return fail(NUM_ERR_OOM, "device allocation failed");
+        }
+        if (h->nlong > 0)
+            CK(pmp::fill_long_routes(h->col_ptr, (int)n, d_coff, h->long_routes, st),
+               "long routes");
         CK(pmp::rows_grids(fp32 ? 0 : 1, (int)n, (int)m, h->nchunks, &h->grid_s, &h->grid_l),
            "sizing the row-kernel grids");
     }

@@ -37,6 +37,8 @@ struct num_problem {
     int* perm = nullptr;                 // caller's index of the stream at each position
     uint8_t* ut = nullptr;               // utility types, only if some stream has U = -w / x
     int4* chunks = nullptr;              // row kernels: chunks of the long links
+    int* long_routes = nullptr;          // row kernels: streams with long routes
+    int nlong = 0;
     int nchunks = 0;
     int narrive_l = 0;                   // entries of arrive_l
     void *wt = nullptr, *lo = nullptr, *hi = nullptr, *c = nullptr;
@@ -147,6 +149,8 @@ View<T> make_view(const num_problem* h) {
     v.ut = h->ut;
     v.ctl = h->ctl;
     v.dbg = h->dbg;
+    v.long_routes = h->long_routes;
+    v.nlong = h->nlong;
     v.hist = h->hist;
     v.sched = h->sched;
     v.A = (T*)h->A;

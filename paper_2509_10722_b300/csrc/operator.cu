@@ -335,6 +335,18 @@ __global__ void k_chunk_counts(const int* __restrict__ row_ptr, int m, int* coun
     }
 }
 
+// flags[j] = 1 for a stream with more than kLongRoute links (j < n), 0 otherwise (j <= n)
+__global__ void k_long_route_flags(const int* __restrict__ col_ptr, int n, int* flags) {
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j <= n; j += gridDim.x * blockDim.x)
+        flags[j] = j < n && col_ptr[j + 1] - col_ptr[j] > kLongRoute ? 1 : 0;
+}
+
+__global__ void k_long_route_fill(const int* __restrict__ col_ptr, int n,
+                                  const int* __restrict__ offs, int* list) {
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x)
+        if (col_ptr[j + 1] - col_ptr[j] > kLongRoute) list[offs[j]] = j;
+}
+
 __global__ void k_chunk_fill(const int* __restrict__ row_ptr, int m, const int* __restrict__ offs,
                              int4* chunks) {
     for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < m; l += gridDim.x * blockDim.x) {
@@ -619,6 +631,26 @@ cudaError_t count_chunks(const int* row_ptr, int m, int* counts, int* offs, int*
     e = cudaMemcpyAsync(nchunks, offs + m, sizeof(int), cudaMemcpyDeviceToHost, st);
     if (e != cudaSuccess) return e;
     return cudaStreamSynchronize(st);
+}
+
+cudaError_t count_long_routes(const int* col_ptr, int n, int* flags, int* offs, int* tmp,
+                              int* nlong, cudaStream_t st) {
+    k_long_route_flags<<<blocks_for((long long)n + 1, kThreads, 65535), kThreads, 0, st>>>(
+        col_ptr, n, flags);
+    note_launches(1);
+    cudaError_t e = scan_exclusive(flags, offs, (size_t)n + 1, tmp, st);
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpyAsync(nlong, offs + n, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return e;
+    return cudaStreamSynchronize(st);
+}
+
+cudaError_t fill_long_routes(const int* col_ptr, int n, const int* offs, int* list,
+                             cudaStream_t st) {
+    k_long_route_fill<<<blocks_for(n, kThreads, 65535), kThreads, 0, st>>>(col_ptr, n, offs,
+                                                                           list);
+    note_launches(1);
+    return cudaGetLastError();
 }
 
 cudaError_t fill_chunks(const int* row_ptr, int m, const int* offs, int4* chunks,

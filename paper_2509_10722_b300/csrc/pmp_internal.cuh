@@ -62,6 +62,9 @@ __device__ __forceinline__ int checked_index(int i, int bound, unsigned int* dbg
 // Zipf(1.1) instance); persistent grids are capped at kMaxRowsGrid blocks.
 constexpr int kLongRow = 256;
 constexpr int kChunk = 2048;
+// Row kernels: a stream whose route has more than kLongRoute links is summed by a whole warp
+// (a list built at setup), so that a few long routes do not hold up the stream kernel.
+constexpr int kLongRoute = 32;
 constexpr int kMaxRowsGrid = 8192;
 
 template <typename T> struct Pair;
@@ -117,6 +120,8 @@ struct View {
     T* pbar;                    // split arrays of the plain path
     T* y;
     unsigned int* dbg;  // debug builds: set when a gathered index was out of range
+    const int* long_routes;  // row kernels: streams with more than kLongRoute links
+    int nlong;
 };
 
 // ---- launchers (fused.cu) -------------------------------------------------------------------
@@ -238,6 +243,10 @@ cudaError_t rows_iteration(const View<T>& v, cudaStream_t st, cudaEvent_t* evs);
 // number of chunks; chunks (may be NULL on the counting call) receives them.
 cudaError_t count_chunks(const int* row_ptr, int m, int* counts, int* offs, int* tmp,
                          int* nchunks, cudaStream_t st);
+cudaError_t count_long_routes(const int* col_ptr, int n, int* flags, int* offs, int* tmp,
+                              int* nlong, cudaStream_t st);
+cudaError_t fill_long_routes(const int* col_ptr, int n, const int* offs, int* list,
+                             cudaStream_t st);
 cudaError_t fill_chunks(const int* row_ptr, int m, const int* offs, int4* chunks,
                         cudaStream_t st);
 constexpr int kPlainKernelsPerIter = 8;

@@ -52,6 +52,34 @@ __device__ __forceinline__ typename Pair<T>::type route_sum(const int* __restric
     return sum;
 }
 
+// Sum of (pbar, y) over the route entries [p, pn) of one long route, by one warp: lane k
+// takes p + k, p + k + 32, ... four at a time, then a shuffle tree (a fixed order); the sum
+// is complete in lane 0.
+template <typename T>
+__device__ __forceinline__ typename Pair<T>::type warp_route_sum(
+    const int* __restrict__ row_idx, const typename Pair<T>::type* __restrict__ pby, int p, int pn,
+    int lane, int m, unsigned int* dbg) {
+    using V = typename Pair<T>::type;
+    V s = vzero(V());
+    for (int e = p + lane; e < pn; e += 128) {
+        const int l0 = checked_index(__ldg(row_idx + e), m, dbg);
+        const int l1 = e + 32 < pn ? checked_index(__ldg(row_idx + e + 32), m, dbg) : -1;
+        const int l2 = e + 64 < pn ? checked_index(__ldg(row_idx + e + 64), m, dbg) : -1;
+        const int l3 = e + 96 < pn ? checked_index(__ldg(row_idx + e + 96), m, dbg) : -1;
+        const V g0 = __ldg(pby + l0);
+        const V g1 = l1 >= 0 ? __ldg(pby + l1) : vzero(V());
+        const V g2 = l2 >= 0 ? __ldg(pby + l2) : vzero(V());
+        const V g3 = l3 >= 0 ? __ldg(pby + l3) : vzero(V());
+        s = vadd(s, vadd(vadd(g0, g1), vadd(g2, g3)));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        s.x += __shfl_down_sync(0xffffffffu, s.x, o);
+        s.y += __shfl_down_sync(0xffffffffu, s.y, o);
+    }
+    return s;
+}
+
 // ---- stream kernel -------------------------------------------------------------------------------
 
 template <typename T>

@@ -5,6 +5,7 @@
 //
 //   stream kernel: one thread per stream; the stream's state is loaded first, then its
 //     route entries four at a time (four independent gathers of (pbar, y) in flight);
+//     streams with more than kLongRoute (32) links are summed by one warp each instead;
 //   link kernel: a group of G lanes per link (G = 32 / rows per warp), the link's own
 //     state loaded by the group leader before the gathers, R x summed by the group in a
 //     fixed order, the link epilogue by the leader; links with more than kLongRow (256)
@@ -33,7 +34,9 @@ constexpr int kTh = 256;
 constexpr int kWarps = kTh / 32;
 constexpr int kGroup = 8;  // lanes per link (4 links per warp); 4 to 32 measured, 8 kept
 
-template <typename T>
+// kSplit: the instance has streams with long routes (v.nlong > 0); without them the kernel
+// is compiled without the warp phase, and the common loop without its length test.
+template <typename T, bool kSplit>
 __global__ void __launch_bounds__(kTh) k_stream_rows(View<T> v) {
     using V = typename Pair<T>::type;
     __shared__ double red[kWarps];
@@ -48,11 +51,26 @@ __global__ void __launch_bounds__(kTh) k_stream_rows(View<T> v) {
     Acc<T> acc;
     for (int j = blockIdx.x * kTh + threadIdx.x; j < n; j += gridDim.x * kTh) {
         const int p = __ldg(col_ptr + j), pn = __ldg(col_ptr + j + 1);
+        if (kSplit && pn - p > kLongRoute) continue;  // summed by a warp below
         const T xo = v.x[j], Zo = v.Z[j], wt = __ldg(v.wt + j);
         const T lo = v.box_uniform ? v.lo_u : __ldg(v.lo + j);
         const T hi = v.box_uniform ? v.hi_u : __ldg(v.hi + j);
         const V sum = route_sum<T>(row_idx, pby, p, pn, v.m, v.dbg);
         stream_epilogue(v, j, sum, (T)(pn - p), xo, Zo, wt, lo, hi, alpha, inv_rho, acc);
+    }
+    // streams with more than kLongRoute links: one warp each
+    const int lane = threadIdx.x & 31;
+    for (int q = blockIdx.x * kWarps + (int)(threadIdx.x >> 5); kSplit && q < v.nlong;
+         q += gridDim.x * kWarps) {
+        const int j = __ldg(v.long_routes + q);
+        const int p = __ldg(col_ptr + j), pn = __ldg(col_ptr + j + 1);
+        const V sum = warp_route_sum<T>(row_idx, pby, p, pn, lane, v.m, v.dbg);
+        if (lane == 0) {
+            const T xo = v.x[j], Zo = v.Z[j], wt = __ldg(v.wt + j);
+            const T lo = v.box_uniform ? v.lo_u : __ldg(v.lo + j);
+            const T hi = v.box_uniform ? v.hi_u : __ldg(v.hi + j);
+            stream_epilogue(v, j, sum, (T)(pn - p), xo, Zo, wt, lo, hi, alpha, inv_rho, acc);
+        }
     }
     const double s = block_sum(acc.value(), red);
     if (threadIdx.x == 0) v.part_s[blockIdx.x] = s;
@@ -135,7 +153,9 @@ __global__ void __launch_bounds__(kTh) k_link_rows(View<T> v) {
 
 template <typename T>
 cudaError_t rows_occupancy(int* occ_s, int* occ_l) {
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ_s, k_stream_rows<T>, kTh, 0);
+    // the variant with the warp phase uses at least as many registers
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ_s, k_stream_rows<T, true>,
+                                                                  kTh, 0);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ_l, k_link_rows<T>, kTh, 0);
 }
@@ -163,7 +183,10 @@ cudaError_t rows_grids(int precision, int n, int m, int nchunks, int* grid_s, in
 
 template <typename T>
 cudaError_t rows_iteration(const View<T>& v, cudaStream_t st, cudaEvent_t* evs) {
-    k_stream_rows<T><<<v.grid_s, kTh, 0, st>>>(v);
+    if (v.nlong > 0)
+        k_stream_rows<T, true><<<v.grid_s, kTh, 0, st>>>(v);
+    else
+        k_stream_rows<T, false><<<v.grid_s, kTh, 0, st>>>(v);
     if (evs) record_kernel_event(evs[0], st);
     k_link_rows<T><<<v.grid_l, kTh, 0, st>>>(v);
     if (evs) record_kernel_event(evs[1], st);

@@ -98,6 +98,21 @@ def _cases():
         60000, 2000, 2, 12, seed=6, link_dist="zipf", frac_log=1.0, c_scale=0.1,
         w_dist="lognormal", box=(0.0, 10.0)), {}
     yield "long_routes", W.random_instance(300, 200, 60, 150, seed=7), dict(tile_items=512)
+
+    def mix_long(seed):
+        """Short routes (1..6 links) with 2% of the streams on 33..400 links: the row stream
+        kernel sums those by warps in the same launch as the rest."""
+        short = W.random_instance(4000, 1200, 1, 6, seed=seed)
+        rng = np.random.default_rng(seed + 100)
+        n, m = short["n"], short["m"]
+        lens = np.diff(short["route_ptr"])
+        longs = rng.choice(n, size=n // 50, replace=False)
+        lens[longs] = rng.integers(33, 401, size=longs.size)
+        rp = np.zeros(n + 1, dtype=np.int64)
+        np.cumsum(lens, out=rp[1:])
+        rl = np.concatenate([rng.choice(m, size=int(k), replace=False) for k in lens])
+        return dict(short, route_ptr=rp, route_links=rl.astype(np.int32))
+    yield "mixed_long_routes", mix_long(13), {}
     yield "ragged_tail", W.random_instance(4097, 1025, 1, 10, seed=8), dict(tile_items=1024)
     yield "all_linear", W.random_instance(2000, 300, 1, 6, seed=9, frac_log=0.0), {}
     yield "alpha2_mixed", W.random_instance(3000, 400, 1, 6, seed=12, frac_log=0.4,
