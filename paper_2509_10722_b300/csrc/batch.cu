@@ -37,7 +37,9 @@ namespace {
 constexpr int kTh = 256;
 constexpr int kWarps = kTh / 32;
 
-template <typename T>
+// kSplit: some stream has a route of more than kLongRoute links (summed by a warp, as in
+// the single-instance stream kernel); otherwise compiled without that phase.
+template <typename T, bool kSplit>
 __global__ void __launch_bounds__(kTh) k_stream_batch(BatchView<T> b) {
     using V = typename Pair<T>::type;
     __shared__ double red[kWarps];
@@ -52,6 +54,7 @@ __global__ void __launch_bounds__(kTh) k_stream_batch(BatchView<T> b) {
         Acc<T> acc;
         for (int j = item.y + threadIdx.x; j < item.z; j += kTh) {
             const int p = __ldg(v.col_ptr + j), pn = __ldg(v.col_ptr + j + 1);
+            if (kSplit && pn - p > kLongRoute) continue;  // summed by a warp below
             const T xo = v.x[j], Zo = v.Z[j], wt = __ldg(v.wt + j);
             const T lo = v.box_uniform ? v.lo_u : __ldg(v.lo + j);
             const T hi = v.box_uniform ? v.hi_u : __ldg(v.hi + j);
@@ -60,6 +63,26 @@ __global__ void __launch_bounds__(kTh) k_stream_batch(BatchView<T> b) {
         }
         const double s = block_sum(acc.value(), red);
         if (threadIdx.x == 0) b.part_s[it] = s;
+    }
+    // streams with long routes: one warp each; the residual term goes to the stream's slot
+    const int lane = threadIdx.x & 31;
+    for (int q = blockIdx.x * kWarps + (int)(threadIdx.x >> 5); kSplit && q < v.nlong;
+         q += gridDim.x * kWarps) {
+        const Ctl* c = b.ctls + __ldg(b.lr_inst + q);
+        if (c->stop) continue;  // warp-uniform
+        const int j = __ldg(v.long_routes + q);
+        const int p = __ldg(v.col_ptr + j), pn = __ldg(v.col_ptr + j + 1);
+        const V sum = warp_route_sum<T>(v.row_idx, v.pby, p, pn, lane, v.m, v.dbg);
+        if (lane == 0) {
+            const T alpha = (T)c->alpha;
+            const T inv_rho = (T)(1.0 / c->rho);
+            const T xo = v.x[j], Zo = v.Z[j], wt = __ldg(v.wt + j);
+            const T lo = v.box_uniform ? v.lo_u : __ldg(v.lo + j);
+            const T hi = v.box_uniform ? v.hi_u : __ldg(v.hi + j);
+            Acc<T> acc;
+            stream_epilogue(v, j, sum, (T)(pn - p), xo, Zo, wt, lo, hi, alpha, inv_rho, acc);
+            b.part_r[q] = acc.value();
+        }
     }
 }
 
@@ -76,6 +99,8 @@ __device__ void finish_instance(const BatchView<T>& b, int i, int lane) {
         rr += __ldcg(b.part_l + 2 * q);
         sl += __ldcg(b.part_l + 2 * q + 1);
     }
+    if (b.v.nlong > 0)
+        for (int q = b.lroff[i] + lane; q < b.lroff[i + 1]; q += 32) ss += __ldcg(b.part_r + q);
     if (b.nchunks > 0)
         for (int q = b.coff[i] + lane; q < b.coff[i + 1]; q += 32) {
             rr += __ldcg(b.part_c + 2 * q);  // zero except at a link's first chunk
@@ -298,7 +323,8 @@ cudaError_t link_occupancy(int lanes, int* occ) {
 
 template <typename T>
 cudaError_t batch_occupancy(int lanes, int* occ_s, int* occ_l, int* occ_e) {
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ_s, k_stream_batch<T>, kTh, 0);
+    cudaError_t e =
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ_s, k_stream_batch<T, true>, kTh, 0);
     if (e != cudaSuccess) return e;
     e = link_occupancy<T>(lanes, occ_l);
     if (e != cudaSuccess) return e;
@@ -343,7 +369,10 @@ cudaError_t check_blocks(int count, const int64_t* stream_off, const int64_t* li
 template <typename T>
 cudaError_t batch_iteration(const BatchView<T>& b, int grid_s, int grid_l, cudaStream_t st,
                             cudaEvent_t* evs) {
-    k_stream_batch<T><<<grid_s, kTh, 0, st>>>(b);
+    if (b.v.nlong > 0)
+        k_stream_batch<T, true><<<grid_s, kTh, 0, st>>>(b);
+    else
+        k_stream_batch<T, false><<<grid_s, kTh, 0, st>>>(b);
     if (evs) record_kernel_event(evs[0], st);
     switch (b.lanes) {
         case 4: k_link_batch<T, 4><<<grid_l, kTh, 0, st>>>(b); break;

@@ -47,6 +47,9 @@ struct num_batch {
     int* coff = nullptr;               // [count + 1] chunk range of each instance
     int* crows = nullptr;              // [count] chunked links of each instance
     double* part_c = nullptr;          // [2 nchunks] residual terms of chunked links
+    int* lr_inst = nullptr;            // [nlong] instance of each long-route stream
+    int* lroff = nullptr;              // [count + 1] long-route range of each instance
+    double* part_r = nullptr;          // [nlong] residual terms of long-route streams
 };
 
 namespace {
@@ -97,6 +100,9 @@ pmp::BatchView<T> make_batch_view(const num_batch* b) {
     v.carry = (T*)h->carry_l;
     v.arrive_c = h->arrive_l;
     v.part_c = b->part_c;
+    v.lr_inst = b->lr_inst;
+    v.lroff = b->lroff;
+    v.part_r = b->part_r;
     return v;
 }
 
@@ -229,6 +235,43 @@ int batch_chunk_tables(num_batch* b) {
     if (e == cudaSuccess) e = cudaMemsetAsync(b->part_c, 0, sizeof(double) * 2 * (size_t)nc, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // the host vectors go out of scope
     if (e != cudaSuccess) return cuda_fail(e, "copying the chunk tables");
+    return NUM_OK;
+}
+
+// The instance of every long-route stream of the stacked problem (the list is in stream
+// order and an instance's streams are a contiguous range, so each instance has a contiguous
+// part of it), and zeroed residual slots for those streams.
+int batch_long_route_tables(num_batch* b) {
+    num_problem* h = b->p;
+    const int nl = h->nlong;
+    if (nl <= 0) return NUM_OK;
+    cudaStream_t st = h->stream;
+    std::vector<int> js((size_t)nl);
+    cudaError_t e = cudaMemcpyAsync(js.data(), h->long_routes, sizeof(int) * (size_t)nl,
+                                    cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "reading the long-route list");
+    std::vector<int> inst((size_t)nl), off(b->count + 1, 0);
+    for (int q = 0; q < nl; ++q) {
+        const int i = (int)(std::upper_bound(b->soff.begin(), b->soff.end(), (int64_t)js[q]) -
+                            b->soff.begin()) - 1;
+        inst[q] = i;
+        off[i + 1] += 1;
+    }
+    for (int i = 0; i < b->count; ++i) off[i + 1] += off[i];
+    b->lr_inst = (int*)dev_alloc(h, sizeof(int) * (size_t)nl);
+    b->lroff = (int*)dev_alloc(h, sizeof(int) * (size_t)(b->count + 1));
+    b->part_r = (double*)dev_alloc(h, sizeof(double) * (size_t)nl);
+    if (!b->lr_inst || !b->lroff || !b->part_r)
+        return fail(NUM_ERR_OOM, "device allocation failed");
+    e = cudaMemcpyAsync(b->lr_inst, inst.data(), sizeof(int) * (size_t)nl, cudaMemcpyHostToDevice,
+                        st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->lroff, off.data(), sizeof(int) * (size_t)(b->count + 1),
+                            cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->part_r, 0, sizeof(double) * (size_t)nl, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // the host vectors go out of scope
+    if (e != cudaSuccess) return cuda_fail(e, "copying the long-route tables");
     return NUM_OK;
 }
 
@@ -367,6 +410,7 @@ int num_batch_create(num_batch** out, int32_t count, const int64_t* stream_off,
                        st), "copy scales");
     BK(cudaMemsetAsync(b->hist, 0, sizeof(double) * 3 * (size_t)H * count, st), "memset");
     rc = batch_chunk_tables(b);
+    if (rc == NUM_OK) rc = batch_long_route_tables(b);
     if (rc != NUM_OK) {
         batch_destroy(b);
         return rc;

@@ -178,6 +178,10 @@ struct BatchView {
     T* carry;              // [nchunks] chunk sums
     int* arrive_c;         // [nchunks] chunks of a link done (at its first chunk)
     double* part_c;        // [2 nchunks] residual terms of a chunked link (at its first chunk)
+    // streams with more than kLongRoute links (v.long_routes, in stream order), one warp each
+    const int* lr_inst;    // [v.nlong] instance of each
+    const int* lroff;      // [count + 1] range of each instance in the list
+    double* part_r;        // [v.nlong] residual term of each
 };
 
 // Profiling event after a kernel: an external event node while the stream is being

@@ -22,8 +22,23 @@ def _mixed_batch():
             W.random_instance(1000, 500, 2, 6, seed=5),
             W.random_instance(3000, 200, 1, 6, seed=6, box=box),
             W.random_instance(5000, 5000, 1, 4, seed=7, frac_log=0.5, frac_alpha2=0.5),
+            _with_long_routes(W.random_instance(3000, 1000, 1, 6, seed=9), seed=9),
             W.random_instance(20000, 2000, 2, 8, seed=8, link_dist="zipf", frac_log=1.0,
                               c_scale=0.1, w_dist="lognormal", box=(0.0, 10.0))]
+
+
+def _with_long_routes(inst, seed):
+    """2% of the streams get routes of 33..300 links, which the stream kernels sum by
+    warps on both the single-instance and the batched path."""
+    rng = np.random.default_rng(seed + 100)
+    n, m = inst["n"], inst["m"]
+    lens = np.diff(inst["route_ptr"])
+    longs = rng.choice(n, size=n // 50, replace=False)
+    lens[longs] = rng.integers(33, 301, size=longs.size)
+    rp = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(lens, out=rp[1:])
+    rl = np.concatenate([rng.choice(m, size=int(k), replace=False) for k in lens])
+    return dict(inst, route_ptr=rp, route_links=rl.astype(np.int32))
 
 
 @pytest.fixture(scope="module")
@@ -84,7 +99,8 @@ def test_batch_instances_stop_independently(batch):
 def test_batch_equals_single_solves(batch):
     """Same rows, same arithmetic: bit-identical to solving each instance alone, including
     the Zipf instance, whose links above 256 streams are summed by whole warps in chunks
-    of 2,048 entries on both paths (8 lanes per shorter link, the default partition)."""
+    of 2,048 entries on both paths (8 lanes per shorter link, the default partition), and
+    the instance whose long routes are summed by warps on both paths."""
     from paper_2509_10722_b300 import capi
     assert np.bincount(batch[-1]["route_links"], minlength=batch[-1]["m"]).max() > 2 * 2048
     g = _run_batch(batch, 200, 0)
