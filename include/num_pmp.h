@@ -229,7 +229,8 @@ NUM_API int num_set_weights(num_problem* h, const double* w);
  * value this forward run takes): for the cotangent xbar (HOST double[n], caller order, or
  * NULL) plus, if objective = 1, the total utility J = sum_j U_j(x_j) (its gradient in x
  * and its direct dependence on w), writes dJ/dc to c_grad (HOST double[m]) and dJ/dw to
- * w_grad (HOST double[n], caller order), each may be NULL, and J to *objective_out (may be
+ * w_grad (HOST double[n], caller order), each may be NULL, and the total utility
+ * sum_j U_j(x_j) at the final rates (whatever `objective` is) to *objective_out (may be
  * NULL).  The derivative runs the adjoint of every step backwards: transposed gathers over
  * R and the Jacobians of the stream prox (zero at the box bounds) and of the slack prox.
  * It keeps the full iterate every checkpoint_every iterations (0: only at the start) and

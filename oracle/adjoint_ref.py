@@ -99,4 +99,8 @@ def gradients(inst, iters, decisions, xbar=None, objective=True, **kw):
         J = J + torch.where(is_log, w * torch.log(safe),
                             torch.where(is_a2, -w / safe, w * x)).sum()
     J.backward()
-    return c.grad.numpy().copy(), w.grad.numpy().copy(), float(J.detach())
+    # autograd leaves the gradient of an input unset when J does not depend on it (e.g. c
+    # after one iteration, before any capacity has entered x): that gradient is zero
+    gc = c.grad.numpy().copy() if c.grad is not None else np.zeros(c.shape)
+    gw = w.grad.numpy().copy() if w.grad is not None else np.zeros(w.shape)
+    return gc, gw, float(J.detach())
