@@ -104,7 +104,9 @@ typedef struct {
  *               order; 0: keep the caller's order
  *   profile     1: record a CUDA event on the handle's stream after every kernel of every
  *               iteration (inside the replayed graphs) and accumulate per-kernel device
- *               times, read with num_get_kernel_times; 0 (default): no events
+ *               times, read with num_get_kernel_times; 2: the same for the first
+ *               iteration of every replay of check_every iterations only (a sample that
+ *               costs 1 / check_every of the events); 0 (default): no events
  *   allocator   NULL (default): cudaMalloc / cudaFree */
 typedef struct {
     double rho0;
@@ -252,11 +254,12 @@ NUM_API int num_reset(num_problem* h);
  * gathered vector once).  out[0] = stream kernel, out[1] = link kernel (host doubles). */
 NUM_API int num_iteration_bytes(const num_problem* h, double* out);
 
-/* Per-kernel device time of the iterations run so far (profile = 1 only).  Kernel q of an
- * iteration (fused paths: 0 = stream kernel, 1 = link kernel; plain path: 0 SpMV-transpose,
- * 1 stream prox, 2 SpMV, 3 link update, 4-6 reductions, 7 finalize): ms[q] = total
- * milliseconds between the event before and the event after it, launches[q] = how many
- * of its launches did work (launches after the stop flag was set are not counted).
+/* Per-kernel device time of the profiled iterations run so far (profile = 1 or 2).
+ * Kernel q of an iteration (fused paths: 0 = stream kernel, 1 = link kernel; plain path:
+ * 0 SpMV-transpose, 1 stream prox, 2 SpMV, 3 link update, 4-6 reductions, 7 finalize):
+ * ms[q] = total milliseconds between the event before and the event after it,
+ * launches[q] = how many of its timed launches did work (launches after the stop flag
+ * was set are not counted).
  * Fills min(max_kernels, kernels per iteration) entries of the HOST arrays; *nkernels
  * receives the number of kernels per iteration. */
 NUM_API int num_get_kernel_times(const num_problem* h, double* ms, int64_t* launches,
@@ -379,7 +382,7 @@ NUM_API int num_batch_solve(num_batch* b, int64_t max_iters, double eps_abs,
  * info[count * NUM_INFO_LEN], one NUM_INFO_* record per instance (may be NULL). */
 NUM_API int num_batch_get(const num_batch* b, double* x, double* prices, double* info);
 
-/* As num_get_kernel_times, for the batch's two kernels (profile = 1). */
+/* As num_get_kernel_times, for the batch's two kernels (profile = 1 or 2). */
 NUM_API int num_batch_get_kernel_times(const num_batch* b, double* ms, int64_t* launches,
                                        int32_t max_kernels, int32_t* nkernels);
 

@@ -116,7 +116,8 @@ cudaError_t run_iterations(num_problem* h, int count) {
         if (e != cudaSuccess) return e;
     }
     for (int i = 0; i < count; ++i) {
-        cudaEvent_t* ev = prof ? h->evs.data() + 1 + (size_t)i * h->kpi : nullptr;
+        cudaEvent_t* ev =
+            prof && i < profiled_iterations(h) ? h->evs.data() + 1 + (size_t)i * h->kpi : nullptr;
         cudaError_t e;
         const bool rows = h->sched_kind == NUM_SCHEDULE_ROWS;
         if (h->prec == NUM_FUSED_FP32)
@@ -133,9 +134,11 @@ cudaError_t run_iterations(num_problem* h, int count) {
 }
 
 // After a batch of iterations completed (stream synchronized): add the per-kernel times of
-// the first `ran` iterations of the batch (the later ones exited at the stop flag).
+// the profiled ones among the first `ran` iterations of the batch (the later ones exited
+// at the stop flag).
 cudaError_t accumulate_kernel_times(num_problem* h, long long ran) {
-    for (long long i = 0; i < ran; ++i) {
+    const long long timed = std::min(ran, (long long)profiled_iterations(h));
+    for (long long i = 0; i < timed; ++i) {
         for (int q = 0; q < h->kpi; ++q) {
             const size_t cur = 1 + (size_t)i * h->kpi + q;
             float ms = 0.f;
@@ -191,7 +194,7 @@ int check_params(const num_params& p) {
     if (p.tile_items != 0 && !is_pow2_tile(p.tile_items))
         return fail(NUM_ERR_INVALID, "tile_items must be 0 or a power of two in [256, 8192]");
     if (p.history < 0) return fail(NUM_ERR_INVALID, "history must be >= 0");
-    if (p.profile != 0 && p.profile != 1) return fail(NUM_ERR_INVALID, "profile must be 0 or 1");
+    if (p.profile < 0 || p.profile > 2) return fail(NUM_ERR_INVALID, "profile must be 0, 1 or 2");
     if (p.schedule < 0 || p.schedule > NUM_SCHEDULE_TILES)
         return fail(NUM_ERR_INVALID, "unknown schedule");
     if (p.reorder != 0 && p.reorder != 1) return fail(NUM_ERR_INVALID, "reorder must be 0 or 1");
@@ -397,7 +400,7 @@ int create_impl(num_problem** out, int64_t n, int64_t m, const int64_t* route_pt
     CK(cudaHostAlloc((void**)&h->ctl_host, sizeof(Ctl), cudaHostAllocDefault), "cudaHostAlloc");
     h->kpi = plain ? pmp::kPlainKernelsPerIter : pmp::kFusedKernelsPerIter;
     if (prm.profile) {
-        h->evs.resize(1 + (size_t)prm.check_every * h->kpi, nullptr);
+        h->evs.resize(1 + (size_t)profiled_iterations(h) * h->kpi, nullptr);
         for (auto& ev : h->evs) CK(cudaEventCreate(&ev), "cudaEventCreate");
     }
     CK(order_after_legacy(h), "ordering after the default stream");

@@ -114,7 +114,7 @@ cudaError_t batch_run(num_batch* b, int count) {
         if (e != cudaSuccess) return e;
     }
     for (int i = 0; i < count; ++i) {
-        cudaEvent_t* ev = prof ? h->evs.data() + 1 + (size_t)i * 2 : nullptr;
+        cudaEvent_t* ev = prof && i < profiled_iterations(h) ? h->evs.data() + 1 + (size_t)i * 2 : nullptr;
         cudaError_t e = h->prec == NUM_FUSED_FP32
                             ? pmp::batch_iteration<float>(make_batch_view<float>(b), b->grid_s,
                                                           b->grid_l, h->stream, ev)
@@ -532,7 +532,8 @@ int num_batch_solve(num_batch* b, int64_t max_iters, double eps_abs, int64_t* it
                     most = std::max(most, b->ctls_host[i].k - k0[i]);
                 const long long ran = most - done_prev;
                 done_prev = most;
-                for (long long i = 0; i < ran; ++i)
+                const long long timed = std::min(ran, (long long)profiled_iterations(h));
+                for (long long i = 0; i < timed; ++i)
                     for (int q = 0; q < 2; ++q) {
                         float ms = 0.f;
                         e = cudaEventElapsedTime(&ms, h->evs[i * 2 + q], h->evs[i * 2 + q + 1]);

@@ -99,6 +99,11 @@ void dev_free(num_problem* h, void* p);
 void destroy_handle(num_problem* h);
 cudaError_t order_after_legacy(num_problem* h);  // order the handle's stream after the legacy one
 cudaError_t run_iterations(num_problem* h, int count);
+// Iterations of each replay of check_every iterations that carry kernel events: all of
+// them (profile = 1), the first (profile = 2) or none.
+inline int profiled_iterations(const num_problem* h) {
+    return h->prm.profile == 1 ? h->prm.check_every : (h->prm.profile == 2 ? 1 : 0);
+}
 cudaError_t zero_state(num_problem* h);
 // NUM_OK, or in a debug build NUM_ERR_STATE if a kernel recorded an out-of-range gather
 int check_debug_flag(num_problem* h);

@@ -287,6 +287,32 @@ def test_profile_times_and_launch_count(c1):
     assert list(runs) == [30] * 8 and np.all(ms > 0)
 
 
+@pytest.mark.parametrize("precision,nk", [(0, 2), (2, 8)])
+def test_sampled_profile(c1, precision, nk):
+    """profile = 2 times the kernels of the first iteration of every replay only (95
+    iterations in replays of 10: ten timed launches per kernel), and leaves the iterates
+    bit-identical to a run without events."""
+    from paper_2509_10722_b300 import capi
+    out = []
+    for prof in (2, 0):
+        with capi.Problem(c1, precision=precision, profile=prof, check_every=10) as p:
+            status, done = p.solve(95, 0.0)
+            if prof:
+                ms, runs = p.kernel_times()
+                assert list(runs) == [10] * nk and np.all(ms > 0)
+            out.append(p.get()[0])
+    assert done == 95 and np.array_equal(out[0], out[1])
+
+
+def test_sampled_profile_batch(c1):
+    from paper_2509_10722_b300 import capi
+    insts = [c1, W.random_instance(300, 40, 2, 8, seed=4)]
+    with capi.Batch(insts, precision=0, profile=2, check_every=10) as b:
+        b.solve(95, 0.0)
+        ms, runs = b.kernel_times()
+    assert list(runs) == [10, 10] and np.all(ms > 0)
+
+
 @pytest.mark.parametrize("precision,schedule,nk", [(0, 1, 2), (1, 2, 2), (2, 1, 8)])
 def test_profile_without_graphs(c1, precision, schedule, nk):
     """Per-kernel times with plain launches (use_graph = 0): the events are recorded on the
