@@ -374,22 +374,21 @@ __global__ void __launch_bounds__(kTh) k_link(View<T> v) {
     p.inv_rho = (T)(1.0 / ctl->rho);
     double d0 = 0.0, d1 = 0.0;
     seg_tiles<T, ITEMS>(p, smem, max_rows_link(kTh * ITEMS), d0, d1);
-    double* red = (double*)smem;
-    const double r2 = block_sum(d0, red);
-    const double s2 = block_sum(d1, red);
+    double* red = (double*)smem;  // the tile staging area, far larger than 3 * kTh / 32 doubles
+    double rs[2] = {d0, d1};
+    block_sum_n<2>(rs, red);
     __shared__ int last;
     if (threadIdx.x == 0) {
-        v.part_l[2 * blockIdx.x] = r2;
-        v.part_l[2 * blockIdx.x + 1] = s2;
+        v.part_l[2 * blockIdx.x] = rs[0];
+        v.part_l[2 * blockIdx.x + 1] = rs[1];
         __threadfence();
         last = atomicAdd(&ctl->ticket, 1u) == gridDim.x - 1;
     }
     __syncthreads();
     if (last) {  // every block's partials are visible: finish the iteration
         __threadfence();
-        const double R2 = block_sum_global(v.part_l, gridDim.x, 2, red);
-        const double S2l = block_sum_global(v.part_l + 1, gridDim.x, 2, red);
-        const double S2s = block_sum_global(v.part_s, v.grid_s, 1, red);
+        double R2, S2l, S2s;
+        grid_residual_sums(v.part_l, gridDim.x, v.part_s, v.grid_s, red, R2, S2l, S2s);
         if (threadIdx.x == 0) {
             ctl->ticket = 0;
             finalize_iteration(ctl, R2, S2s + S2l, v.hist, v.sched);

@@ -41,6 +41,29 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
     return s;
 }
 
+// Sums of K values over the block at once, valid in thread 0: each value reduced exactly
+// as block_sum would (the same order, so the same bits), with two barriers in all instead
+// of two per value.  `red` holds at least K * blockDim.x / 32 doubles.
+template <int K>
+__device__ __forceinline__ void block_sum_n(double (&v)[K], double* red) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < K; ++k) v[k] = warp_sum(v[k]);
+    __syncthreads();
+    if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) red[k * nw + warp] = v[k];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        double s = 0.0;
+        if (threadIdx.x == 0)
+            for (int i = 0; i < nw; ++i) s += red[k * nw + i];
+        v[k] = s;
+    }
+}
+
 // Sum over the block of a[0..count) of a global array (strided per thread, then a block
 // reduction), bypassing L1 so values written by other blocks of the same launch are seen.
 __device__ __forceinline__ double block_sum_global(const double* a, int count, int stride,
@@ -48,6 +71,29 @@ __device__ __forceinline__ double block_sum_global(const double* a, int count, i
     double s = 0.0;
     for (int i = threadIdx.x; i < count; i += blockDim.x) s += __ldcg(a + (size_t)i * stride);
     return block_sum(s, red);
+}
+
+// The grid's residual sums at the end of an iteration, in one pass: the link blocks'
+// (r2, s2) pairs part_l[2 * grid_l] and the stream blocks' s2 part_s[grid_s].  Each sum
+// takes the same per-thread order as block_sum_global, so the same bits.  Results valid
+// in thread 0; `red` holds at least 3 * blockDim.x / 32 doubles.
+__device__ __forceinline__ void grid_residual_sums(const double* part_l, int grid_l,
+                                                   const double* part_s, int grid_s,
+                                                   double* red, double& r2, double& s2l,
+                                                   double& s2s) {
+    double v[3] = {0.0, 0.0, 0.0};
+    const int count = grid_l > grid_s ? grid_l : grid_s;
+    for (int i = threadIdx.x; i < count; i += blockDim.x) {
+        if (i < grid_l) {
+            v[0] += __ldcg(part_l + 2 * (size_t)i);
+            v[1] += __ldcg(part_l + 2 * (size_t)i + 1);
+        }
+        if (i < grid_s) v[2] += __ldcg(part_s + i);
+    }
+    block_sum_n<3>(v, red);
+    r2 = v[0];
+    s2l = v[1];
+    s2s = v[2];
 }
 
 // ---- the end-of-iteration step -----------------------------------------------------------------

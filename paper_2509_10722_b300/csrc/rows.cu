@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(kTh) k_stream_rows(View<T> v) {
 
 template <typename T>
 __global__ void __launch_bounds__(kTh) k_link_rows(View<T> v) {
-    __shared__ double red[kWarps];
+    __shared__ double red[3 * kWarps];
     __shared__ int last;
     Ctl* ctl = v.ctl;
     if (ctl->stop) return;
@@ -130,20 +130,19 @@ __global__ void __launch_bounds__(kTh) k_link_rows(View<T> v) {
             }
         }
     }
-    const double R2 = block_sum(r2.value(), red);
-    const double S2 = block_sum(s2.value(), red);
+    double rs[2] = {r2.value(), s2.value()};
+    block_sum_n<2>(rs, red);
     if (threadIdx.x == 0) {
-        v.part_l[2 * blockIdx.x] = R2;
-        v.part_l[2 * blockIdx.x + 1] = S2;
+        v.part_l[2 * blockIdx.x] = rs[0];
+        v.part_l[2 * blockIdx.x + 1] = rs[1];
         __threadfence();
         last = atomicAdd(&ctl->ticket, 1u) == gridDim.x - 1;
     }
     __syncthreads();
     if (last) {
         __threadfence();
-        const double a = block_sum_global(v.part_l, gridDim.x, 2, red);
-        const double b = block_sum_global(v.part_l + 1, gridDim.x, 2, red);
-        const double c = block_sum_global(v.part_s, v.grid_s, 1, red);
+        double a, b, c;
+        grid_residual_sums(v.part_l, gridDim.x, v.part_s, v.grid_s, red, a, b, c);
         if (threadIdx.x == 0) {
             ctl->ticket = 0;
             finalize_iteration(ctl, a, c + b, v.hist, v.sched);
