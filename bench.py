@@ -17,6 +17,7 @@ from __future__ import annotations
 
 import argparse
 import csv
+import ctypes
 import hashlib
 import io
 import json
@@ -279,7 +280,6 @@ class Solver:
         self.eps, self.max_iters = eps, max_iters
         self.stream = stream
         self.alloc = capi.torch_allocator()
-        import ctypes
         self.params = capi.num_default_params(precision=precision, profile=2, tile_items=tile,
                                               schedule=schedule,
                                               allocator=ctypes.pointer(self.alloc))
@@ -453,7 +453,8 @@ def run_ours(args, dist):
     peak, peak_note = measured_peaks()
     kernel_key = ["k_stream_rows", "k_link_rows"][dom] if args.schedule == "rows" else \
         ["k_stream", "k_link"][dom]
-    trec = traffic_record(f"{args.workload}:{kernel_key}")
+    # the committed capture is of the full-size workload only
+    trec = traffic_record(f"{args.workload}:{kernel_key}") if args.scale is None else None
     iter_bytes = float(sum(fp32.bytes))
     iter_ms = float(np.sum(per_launch_ms))
     roofline = {"bound": "hbm", "kernel": KERNEL_NAMES[0][dom], "achieved": achieved,
@@ -528,7 +529,10 @@ def run_ours(args, dist):
 
     if not args.no_e2e:
         host = pinned_copy(inst, torch)
-        e2e_params = capi.num_default_params(precision=0, schedule=sched)
+        # device memory from PyTorch's caching allocator, as in the device-resident leg
+        e2e_alloc = capi.torch_allocator()
+        e2e_params = capi.num_default_params(precision=0, schedule=sched,
+                                             allocator=ctypes.pointer(e2e_alloc))
         # results land in pinned host memory (a device-to-host copy at full speed)
         xh = torch.empty(n, dtype=torch.float64, pin_memory=True).numpy()
         ph = torch.empty(m, dtype=torch.float64, pin_memory=True).numpy()
@@ -549,8 +553,8 @@ def run_ours(args, dist):
                        "h2d_bytes_per_step": W.instance_bytes(inst),
                        "d2h_bytes_per_step": 8 * (n + m) + 8 * 8,
                        "time_to_tol_s": t_e2e / args.steps,
-                       "path": "num_create (pinned host arrays) + num_solve + num_get (pinned host) + "
-                               "num_destroy, wall clock"}
+                       "path": "num_create (pinned host arrays, PyTorch caching allocator) + "
+                               "num_solve + num_get (pinned host) + num_destroy, wall clock"}
 
     if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args, inst)
@@ -568,8 +572,6 @@ def run_batched(args):
     The batch runs with the partition chosen by num_batch_autotune (headline: that partition
     set with num_batch_set_schedule, as a caller that tuned once would), and is also timed
     with the tuning inside the step and with the default partition."""
-    import ctypes
-
     import torch
     from paper_2509_10722_b300 import capi
     insts = W.batched_instances(256, seed=0, congested=args.congested)
