@@ -301,7 +301,7 @@ class Solver:
             ev[1].record(self.stream)
             status, iters = c.num_solve(h, self.max_iters, self.eps)
             ev[2].record(self.stream)
-            info = c.num_get_device(h, self.x, self.p)
+            info = c.num_get_device(h, self.x, self.p, self.n, self.m)
             ev[3].record(self.stream)
             ev[3].synchronize()
             self.phase_ms += [ev[q].elapsed_time(ev[q + 1]) for q in range(3)]

@@ -254,11 +254,14 @@ def num_get(h, n, m, x=True, prices=True, out_x=None, out_prices=None):
     return xa, pa, {k: float(info[i]) for k, i in INFO.items()}
 
 
-def num_get_device(h, x=None, prices=None):
-    """Write x / prices into float64 CUDA tensors (either may be None); returns info dict."""
+def num_get_device(h, x=None, prices=None, n=None, m=None):
+    """Write x / prices into float64 CUDA tensors (either may be None); returns info dict.
+    The library writes n values to x and m to prices: pass n and m to have the tensor
+    sizes checked (a smaller tensor would be overrun)."""
     info = np.zeros(NUM_INFO_LEN)
-    xp = None if x is None else _dptr(x, "float64", x.numel(), "x")
-    pp = None if prices is None else _dptr(prices, "float64", prices.numel(), "prices")
+    xp = None if x is None else _dptr(x, "float64", x.numel() if n is None else int(n), "x")
+    pp = None if prices is None else _dptr(prices, "float64",
+                                           prices.numel() if m is None else int(m), "prices")
     _check(_lib.num_get_device(h, xp, pp, _hptr(info)))
     return {k: float(info[i]) for k, i in INFO.items()}
 
@@ -295,7 +298,8 @@ def num_set_weights(h, n, w):
 
 def num_adjoint(h, n, m, iters, checkpoint_every=50, xbar=None, objective=True):
     """Gradients of `iters` unrolled iterations from the zero state: returns
-    (dJ/dc [m], dJ/dw [n], J) for J = xbar . x (+ sum_j U_j(x_j) if objective)."""
+    (dJ/dc [m], dJ/dw [n], U) for J = xbar . x (+ sum_j U_j(x_j) if objective), with U the
+    total utility sum_j U_j(x_j) at the final rates."""
     cg = np.empty(int(m))
     wg = np.empty(int(n))
     xb = None if xbar is None else _host(xbar, np.float64, int(n), "xbar")
@@ -531,6 +535,10 @@ class Problem:
 
     def get(self, x=True, prices=True):
         return num_get(self.h, self.n, self.m, x, prices)
+
+    def get_device(self, x=None, prices=None):
+        """x / prices into float64 CUDA tensors of n / m values; returns the info dict."""
+        return num_get_device(self.h, x, prices, self.n, self.m)
 
     def history(self, max_rows=None):
         return num_get_history(self.h, self.params.history if max_rows is None else max_rows)

@@ -69,3 +69,19 @@ def test_bad_solve_arguments():
         with pytest.raises(capi.NumError):
             p.set_rho_schedule([0, 2, 0])
         assert p.solve(0, 0.0) == (1, 0)
+
+
+def test_get_device_checks_tensor_sizes():
+    """A device output smaller than the handle's n (or m) is refused on the host, before
+    the library could write past its end."""
+    import torch
+    from paper_2509_10722_b300 import capi
+    with capi.Problem(_base()) as p:
+        p.solve(5, 0.0)
+        with pytest.raises(ValueError):
+            p.get_device(x=torch.empty(p.n - 1, dtype=torch.float64, device="cuda"))
+        with pytest.raises(ValueError):
+            p.get_device(prices=torch.empty(p.m + 1, dtype=torch.float64, device="cuda"))
+        x = torch.empty(p.n, dtype=torch.float64, device="cuda")
+        info = p.get_device(x=x)
+        assert np.allclose(x.cpu().numpy(), p.get()[0]) and info["iters"] == 5

@@ -25,7 +25,7 @@ def test_noalloc_objective_matches_num_get(n, m, a2):
     with capi.Problem(inst, precision=capi.NUM_FUSED_FP64) as p:
         p.solve(300, 0.0)
         x = torch.empty(n, dtype=torch.float64, device="cuda")
-        info = capi.num_get_device(p.h, x, None)
+        info = capi.num_get_device(p.h, x, None, n=p.n)
     ut = torch.as_tensor(inst["utype"]).cuda()
     w = torch.as_tensor(inst["w"]).cuda()
     out = torch.full((2,), float("nan"), dtype=torch.float64, device="cuda")
