@@ -354,7 +354,8 @@ def num_objective_noalloc(n, x, utype, w, objective, stream=None):
     _check(_lib.num_objective_noalloc(n, _dptr(x, "float64", n, "x"),
                                       _dptr(utype, "uint8", n, "utype"),
                                       _dptr(w, "float64", n, "w"),
-                                      _dptr(objective, "float64", objective.numel(), "objective"),
+                                      _dptr(objective, "float64", max(objective.numel(), 1),
+                                            "objective"),
                                       ctypes.c_void_p(stream) if stream else None))
 
 
