@@ -381,11 +381,30 @@ int create_impl(num_problem** out, int64_t n, int64_t m, const int64_t* route_pt
 
     // ---- from here on: CUDA work ----
     cudaError_t e;
+    // Host inputs are copied on a second stream, `cs`: the routes first, then the other
+    // arrays, which arrive while the routes are validated and the operator is built.  Any
+    // early return waits for those copies before the memory they target is released.
+    cudaStream_t cs = nullptr;
+    cudaEvent_t ev_start = nullptr, ev_routes = nullptr, ev_values = nullptr;
+    auto end_copies = [&]() {
+        if (cs) {
+            cudaStreamSynchronize(cs);
+            cudaStreamDestroy(cs);
+        }
+        for (cudaEvent_t ev : {ev_start, ev_routes, ev_values})
+            if (ev) cudaEventDestroy(ev);
+        cs = nullptr;
+        ev_start = ev_routes = ev_values = nullptr;
+    };
+    auto drop = [&]() {
+        end_copies();
+        destroy_handle(h);
+    };
 #define CK(call, what)                          \
     do {                                        \
         e = (call);                             \
         if (e != cudaSuccess) {                 \
-            destroy_handle(h);                  \
+            drop();                             \
             return cuda_fail(e, what);          \
         }                                       \
     } while (0)
@@ -406,13 +425,21 @@ int create_impl(num_problem** out, int64_t n, int64_t m, const int64_t* route_pt
     CK(order_after_legacy(h), "ordering after the default stream");
     cudaStream_t st = h->stream;
     if (!on_device) {
-        CK(cudaMemcpyAsync(d_rp, route_ptr, 8 * (N + 1), cudaMemcpyHostToDevice, st), "copy route_ptr");
-        CK(cudaMemcpyAsync(d_rl, route_links, 4 * NNZ, cudaMemcpyHostToDevice, st), "copy route_links");
-        CK(cudaMemcpyAsync(d_c, c, 8 * M, cudaMemcpyHostToDevice, st), "copy c");
-        CK(cudaMemcpyAsync(d_w, w, 8 * N, cudaMemcpyHostToDevice, st), "copy w");
-        if (lo) CK(cudaMemcpyAsync(d_lo, lo, 8 * N, cudaMemcpyHostToDevice, st), "copy lo");
-        CK(cudaMemcpyAsync(d_hi, hi, 8 * N, cudaMemcpyHostToDevice, st), "copy hi");
-        CK(cudaMemcpyAsync(d_ut, utype, N, cudaMemcpyHostToDevice, st), "copy utype");
+        CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking), "cudaStreamCreate");
+        for (cudaEvent_t* ev : {&ev_start, &ev_routes, &ev_values})
+            CK(cudaEventCreateWithFlags(ev, cudaEventDisableTiming), "cudaEventCreate");
+        CK(cudaEventRecord(ev_start, st), "cudaEventRecord");
+        CK(cudaStreamWaitEvent(cs, ev_start, 0), "cudaStreamWaitEvent");
+        CK(cudaMemcpyAsync(d_rp, route_ptr, 8 * (N + 1), cudaMemcpyHostToDevice, cs), "copy route_ptr");
+        CK(cudaMemcpyAsync(d_rl, route_links, 4 * NNZ, cudaMemcpyHostToDevice, cs), "copy route_links");
+        CK(cudaEventRecord(ev_routes, cs), "cudaEventRecord");
+        CK(cudaMemcpyAsync(d_c, c, 8 * M, cudaMemcpyHostToDevice, cs), "copy c");
+        CK(cudaMemcpyAsync(d_w, w, 8 * N, cudaMemcpyHostToDevice, cs), "copy w");
+        if (lo) CK(cudaMemcpyAsync(d_lo, lo, 8 * N, cudaMemcpyHostToDevice, cs), "copy lo");
+        CK(cudaMemcpyAsync(d_hi, hi, 8 * N, cudaMemcpyHostToDevice, cs), "copy hi");
+        CK(cudaMemcpyAsync(d_ut, utype, N, cudaMemcpyHostToDevice, cs), "copy utype");
+        CK(cudaEventRecord(ev_values, cs), "cudaEventRecord");
+        CK(cudaStreamWaitEvent(st, ev_routes, 0), "cudaStreamWaitEvent");
         route_ptr = d_rp;
         route_links = d_rl;
         c = d_c;
@@ -421,10 +448,10 @@ int create_impl(num_problem** out, int64_t n, int64_t m, const int64_t* route_pt
         hi = d_hi;
         utype = d_ut;
     }
+    // the routes first: the ordering and the operator build index with them
     CK(cudaMemsetAsync(d_err, 0, sizeof(int) * 2, st), "memset");
-    CK(pmp::validate_inputs((int)n, (int)m, route_ptr, route_links, c, utype, w, lo, hi, d_err,
-                            d_box, st),
-       "validating the inputs");
+    CK(pmp::validate_routes((int)n, (int)m, (long long)nnz, route_ptr, route_links, d_err, st),
+       "validating the routes");
     if (batch) {
         CK(cudaMemcpyAsync(d_soff, batch->stream_off, 8 * ((size_t)batch->count + 1),
                            cudaMemcpyHostToDevice, st), "copy offsets");
@@ -433,10 +460,8 @@ int create_impl(num_problem** out, int64_t n, int64_t m, const int64_t* route_pt
     }
     int err_bits = 0, flags[2] = {0, 0};
     unsigned long long box[4];
-    CK(cudaMemcpyAsync(flags, d_err, sizeof(flags), cudaMemcpyDeviceToHost, st), "read flags");
-    CK(cudaMemcpyAsync(box, d_box, sizeof(box), cudaMemcpyDeviceToHost, st), "read box");
+    CK(cudaMemcpyAsync(&err_bits, d_err, sizeof(int), cudaMemcpyDeviceToHost, st), "read flags");
     CK(cudaStreamSynchronize(st), "validation");
-    err_bits = flags[0];
     if (!err_bits && batch) {
         CK(pmp::check_blocks(batch->count, d_soff, d_loff, n, route_ptr, route_links, d_err, st),
            "checking the instance blocks");
@@ -444,7 +469,7 @@ int create_impl(num_problem** out, int64_t n, int64_t m, const int64_t* route_pt
         CK(cudaStreamSynchronize(st), "validation");
     }
     if (err_bits) {
-        destroy_handle(h);
+        drop();
         return fail(NUM_ERR_INVALID, describe_bits(err_bits));
     }
     if (reorder) {
@@ -459,8 +484,19 @@ int create_impl(num_problem** out, int64_t n, int64_t m, const int64_t* route_pt
     CK(cudaMemcpyAsync(&err_bits, d_err, sizeof(int), cudaMemcpyDeviceToHost, st), "read flags");
     CK(cudaStreamSynchronize(st), "operator build");
     if (err_bits) {
-        destroy_handle(h);
+        drop();
         return fail(NUM_ERR_INVALID, describe_bits(err_bits));
+    }
+    // then the values, once their copies are in
+    if (cs) CK(cudaStreamWaitEvent(st, ev_values, 0), "cudaStreamWaitEvent");
+    CK(pmp::validate_values((int)n, (int)m, c, utype, w, lo, hi, d_err, d_box, st),
+       "validating the values");
+    CK(cudaMemcpyAsync(flags, d_err, sizeof(flags), cudaMemcpyDeviceToHost, st), "read flags");
+    CK(cudaMemcpyAsync(box, d_box, sizeof(box), cudaMemcpyDeviceToHost, st), "read box");
+    CK(cudaStreamSynchronize(st), "validation");
+    if (flags[0]) {
+        drop();
+        return fail(NUM_ERR_INVALID, describe_bits(flags[0]));
     }
     const double lmin = pmp::ordered_key_to_double(box[0]), lmax = pmp::ordered_key_to_double(box[1]);
     const double hmin = pmp::ordered_key_to_double(box[2]), hmax = pmp::ordered_key_to_double(box[3]);
@@ -468,7 +504,7 @@ int create_impl(num_problem** out, int64_t n, int64_t m, const int64_t* route_pt
     if (flags[1]) {  // some stream has U = -w / x: keep the types on the device
         h->ut = (uint8_t*)dev_alloc(h, N);
         if (!h->ut) {
-            destroy_handle(h);
+            drop();
             return fail(NUM_ERR_OOM, "device allocation failed");
         }
     }
@@ -502,7 +538,7 @@ int create_impl(num_problem** out, int64_t n, int64_t m, const int64_t* route_pt
         h->arrive_l = (int*)dev_alloc(h, sizeof(int) * nc);
         h->narrive_l = (int)nc;
         if (!h->chunks || !h->carry_l || !h->arrive_l) {
-            destroy_handle(h);
+            drop();
             return fail(NUM_ERR_OOM, "device allocation failed");
         }
         if (h->nchunks > 0)
@@ -511,7 +547,7 @@ int create_impl(num_problem** out, int64_t n, int64_t m, const int64_t* route_pt
            "counting long routes");
         h->long_routes = (int*)dev_alloc(h, sizeof(int) * (size_t)(h->nlong > 0 ? h->nlong : 1));
         if (!h->long_routes) {
-            destroy_handle(h);
+            drop();
             return fail(NUM_ERR_OOM, "device allocation failed");
         }
         if (h->nlong > 0)
@@ -522,6 +558,7 @@ int create_impl(num_problem** out, int64_t n, int64_t m, const int64_t* route_pt
     }
     CK(zero_state(h), "zeroing the state");
     CK(cudaStreamSynchronize(st), "setup");
+    end_copies();
     // release the transient buffers
     for (void* q : {(void*)d_rp, (void*)d_rl, (void*)d_c, (void*)d_w, (void*)d_lo, (void*)d_hi,
                     (void*)d_ut, (void*)d_err, (void*)d_box, (void*)s.keys_a, (void*)s.vals_a,

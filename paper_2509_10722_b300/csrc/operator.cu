@@ -30,16 +30,23 @@ __device__ __forceinline__ unsigned long long ordered_key(double v) {
     return (b & 0x8000000000000000ull) ? ~b : (b | 0x8000000000000000ull);
 }
 
-__global__ void k_validate_streams(int n, const int64_t* __restrict__ route_ptr,
-                                   const uint8_t* __restrict__ utype,
+// Every route nonempty, the pointers increasing from 0.
+__global__ void k_validate_routes(int n, const int64_t* __restrict__ route_ptr, int* err) {
+    int bits = 0;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+        const int64_t p0 = route_ptr[j], p1 = route_ptr[j + 1];
+        if (p1 <= p0 || (j == 0 && p0 != 0)) bits |= VB_ROUTE;
+    }
+    if (bits) atomicOr(err, bits);
+}
+
+__global__ void k_validate_streams(int n, const uint8_t* __restrict__ utype,
                                    const double* __restrict__ w, const double* __restrict__ lo,
                                    const double* __restrict__ hi, int* err,
                                    unsigned long long* box) {
     int bits = 0, alpha2 = 0;
     unsigned long long lo_min = ~0ull, lo_max = 0ull, hi_min = ~0ull, hi_max = 0ull;
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
-        const int64_t p0 = route_ptr[j], p1 = route_ptr[j + 1];
-        if (p1 <= p0 || (j == 0 && p0 != 0)) bits |= VB_ROUTE;
         const double wj = w[j];
         if (!(wj > 0.0) || !isfinite(wj)) bits |= VB_WEIGHT;
         const uint8_t t = utype[j];
@@ -91,15 +98,20 @@ __global__ void k_validate_streams(int n, const int64_t* __restrict__ route_ptr,
     }
 }
 
-__global__ void k_validate_links(int m, long long nnz, const int* __restrict__ route_links,
-                                 const double* __restrict__ c, int* err) {
+__global__ void k_validate_link_ids(int m, long long nnz, const int* __restrict__ route_links,
+                                    int* err) {
     int bits = 0;
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nnz; e += stride) {
         const int l = route_links[e];
         if (l < 0 || l >= m) bits |= VB_LINK_ID;
     }
-    for (long long l = blockIdx.x * (long long)blockDim.x + threadIdx.x; l < m; l += stride) {
+    if (bits) atomicOr(err, bits);
+}
+
+__global__ void k_validate_capacities(int m, const double* __restrict__ c, int* err) {
+    int bits = 0;
+    for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < m; l += gridDim.x * blockDim.x) {
         const double cl = c[l];
         if (!(cl > 0.0) || !isfinite(cl)) bits |= VB_CAPACITY;
     }
@@ -512,23 +524,25 @@ double ordered_key_to_double(unsigned long long k) {
     return d;
 }
 
-cudaError_t validate_inputs(int n, int m, const int64_t* route_ptr, const int* route_links,
-                            const double* c, const uint8_t* utype, const double* w,
-                            const double* lo, const double* hi, int* err_bits,
+cudaError_t validate_routes(int n, int m, long long nnz, const int64_t* route_ptr,
+                            const int* route_links, int* err_bits, cudaStream_t st) {
+    k_validate_routes<<<blocks_for(n, kThreads, 4096), kThreads, 0, st>>>(n, route_ptr, err_bits);
+    note_launches(1);
+    k_validate_link_ids<<<blocks_for(nnz, kThreads, 8192), kThreads, 0, st>>>(m, nnz, route_links,
+                                                                              err_bits);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t validate_values(int n, int m, const double* c, const uint8_t* utype,
+                            const double* w, const double* lo, const double* hi, int* err_bits,
                             unsigned long long* box_minmax, cudaStream_t st) {
     k_init_box<<<1, 1, 0, st>>>(box_minmax);
     note_launches(1);
     k_validate_streams<<<blocks_for(n, kThreads, 4096), kThreads, 0, st>>>(
-        n, route_ptr, utype, w, lo, hi, err_bits, box_minmax);
+        n, utype, w, lo, hi, err_bits, box_minmax);
     note_launches(1);
-    int64_t nnz_host = 0;
-    cudaError_t e = cudaMemcpyAsync(&nnz_host, route_ptr + n, sizeof(int64_t),
-                                    cudaMemcpyDeviceToHost, st);
-    if (e != cudaSuccess) return e;
-    e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) return e;
-    k_validate_links<<<blocks_for(nnz_host > m ? nnz_host : m, kThreads, 8192), kThreads, 0, st>>>(
-        m, (long long)nnz_host, route_links, c, err_bits);
+    k_validate_capacities<<<blocks_for(m, kThreads, 4096), kThreads, 0, st>>>(m, c, err_bits);
     note_launches(1);
     return cudaGetLastError();
 }

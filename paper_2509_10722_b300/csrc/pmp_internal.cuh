@@ -289,12 +289,17 @@ struct Scratch {  // transient buffers of the operator build, caller-allocated
 size_t radix_hist_len(int nnz);
 size_t scan_tmp_len(size_t len);
 
-// Validate the inputs; *err_bits (device int) accumulates ValidationBits; box_minmax
+// Validate the inputs in two parts, so that the routes can be checked and the operator
+// built while the other arrays are still being copied: the routes (route_ptr increasing
+// from 0, link ids in [0, m); nnz = route_ptr[n], read on the host), then the values
+// (weights, types, boxes, capacities).  *err_bits (device int) accumulates
+// ValidationBits, err_bits[1] is set when some stream has U = -w / x, and box_minmax
 // (device unsigned long long[4]) receives order-preserving keys of min lo, max lo, min hi,
 // max hi.
-cudaError_t validate_inputs(int n, int m, const int64_t* route_ptr, const int* route_links,
-                            const double* c, const uint8_t* utype, const double* w,
-                            const double* lo, const double* hi, int* err_bits,
+cudaError_t validate_routes(int n, int m, long long nnz, const int64_t* route_ptr,
+                            const int* route_links, int* err_bits, cudaStream_t st);
+cudaError_t validate_values(int n, int m, const double* c, const uint8_t* utype,
+                            const double* w, const double* lo, const double* hi, int* err_bits,
                             unsigned long long* box_minmax, cudaStream_t st);
 // Order the streams by the first link of their route (stable): perm[j] = caller's index of
 // the stream placed at position j; route_ptr_new / route_links_new receive the routes in
