@@ -591,6 +591,7 @@ def run_batched(args):
             if keep is not None:
                 keep["x"] = [x.copy() for x in xs]
                 keep["obj"] = np.array([inf["objective"] for inf in infos])
+                keep["iters"] = it.copy()
         return int(it.sum()), st, ms, runs, tune
 
     def seq_leg(precision):
@@ -621,10 +622,15 @@ def run_batched(args):
     t_a, (it_a, st_a, kms_a, kruns_a, tune) = timed_leg(lambda: batch_leg("autotune"), args.steps)
     chosen, trials = tune
     t_d, (it_d, st_d, kms_d, kruns_d, _) = timed_leg(lambda: batch_leg("default"), args.steps)
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    launches0 = capi.num_kernel_launches()
     t_f, (it_f, st_f, kms_f, kruns_f, _) = timed_leg(lambda: batch_leg("pinned", chosen), args.steps)
+    launches = (capi.num_kernel_launches() - launches0) // max(args.steps, 1)
+    clocks = sampler.stop()
     # precision: the same batch in FP64 (default partition, untimed) against the FP32 run
     r32, r64 = {}, {}
-    batch_leg("pinned", chosen, 0, r32)
+    batch_leg("pinned", chosen, 0, r32)  # also gives the per-instance iteration counts
     batch_leg("default", None, 1, r64)
     obj_rel = np.abs(r32["obj"] - r64["obj"]) / np.maximum(np.abs(r64["obj"]), 1e-300)
     x_rel = [float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
@@ -636,8 +642,47 @@ def run_batched(args):
         t_s, it_s = timed_leg(lambda: seq_leg(0), 1)
         t_p, it_p = timed_leg(lambda: seq_leg(2), 1)
     n_tot = int(sum(t["n"] for t in insts))
+    m_tot = int(sum(t["m"] for t in insts))
     nnz_tot = int(sum(int(t["route_ptr"][-1]) for t in insts))
     st1, st2 = trials[:5], trials[5:]
+    # Both kernels against their ceilings.  The sampled launches spread over the whole run,
+    # tail included, where few instances still run; so the work of an average launch is
+    # each instance's work weighted by its iterations, over the launches of the run.
+    pk = [float(kms_f[q] / max(kruns_f[q], 1)) for q in range(2)]
+    its = np.asarray(r32["iters"], dtype=np.float64)
+    launches_run = float(its.max())
+    ns = np.array([t["n"] for t in insts], dtype=np.float64)
+    ms_ = np.array([t["m"] for t in insts], dtype=np.float64)
+    nnzs = np.array([int(t["route_ptr"][-1]) for t in insts], dtype=np.float64)
+    reads = float((its * nnzs).sum() / launches_run)
+    rate = {4: capi.num_measure_gather_rate(nnz_tot, n_tot, 4, 5),
+            8: capi.num_measure_gather_rate(nnz_tot, m_tot, 8, 5)}
+    gk = {}
+    for q, vb in enumerate((8, 4)):
+        gk[["stream", "link"][q]] = {"reads_per_launch": reads,
+                                     "achieved_g_per_s": reads / (pk[q] / 1e3) / 1e9,
+                                     "ceiling_g_per_s": rate[vb] / 1e9,
+                                     "frac": reads / rate[vb] * 1e3 / pk[q]}
+    gather = {"bound": "random L2 reads (one 32-byte sector each)", "unit": "G reads/s",
+              "kernels": gk, "note": "reads per launch = sum over instances of iterations x "
+                                     "nnz, over the launches of the run"}
+    # algorithmic bytes of the batch kernels: the single-instance formulas (FP32, uniform
+    # box [0, 20]: no per-stream box arrays), weighted the same way
+    b_stream = float((its * (4.0 * (ns + 1) + 4.0 * nnzs + 20.0 * ns + 8.0 * ms_)).sum()
+                     / launches_run)
+    b_link = float((its * (4.0 * (ms_ + 1) + 4.0 * nnzs + 4.0 * ns + 44.0 * ms_)).sum()
+                   / launches_run)
+    peak, peak_note = measured_peaks()
+    dom = int(np.argmax(pk))
+    bytes_dom = [b_stream, b_link][dom]
+    roofline = {"bound": "hbm", "kernel": ["stream", "link"][dom],
+                "achieved": bytes_dom / (pk[dom] / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
+                "frac": bytes_dom / (pk[dom] / 1e3) / 1e9 / peak, "peak_note": peak_note,
+                "traffic": None, "algorithmic_bytes_per_launch": bytes_dom,
+                "launch_ms": pk[dom],
+                "launch_timing": "CUDA events around the kernels of the first iteration of "
+                                 "every replay of 50 iterations (profile = 2), over the timed "
+                                 "batch solves"}
     line = {"metric": "batched PMP: 256 instances to eps_abs 1e-4, aggregate iterations/s",
             "value": it_f / (t_f / 1e3), "unit": "iterations/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_f,
@@ -671,7 +716,9 @@ def run_batched(args):
                                            "eps_abs 1e-4"},
             "kernels_ms_per_launch": {"autotuned": kern(kms_a, kruns_a),
                                       "default_partition": kern(kms_d, kruns_d),
-                                      "pinned": kern(kms_f, kruns_f)}}
+                                      "pinned": kern(kms_f, kruns_f)},
+            "roofline": roofline, "gather_roofline": gather, "gpu_launches": int(launches),
+            "clocks": clocks}
     print(json.dumps(line), flush=True)
 
 
