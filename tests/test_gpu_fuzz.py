@@ -12,6 +12,8 @@ iteration count.
   iteration) or in FP32 on the oracle's decisions.
 - Adjoints: dJ/dc and dJ/dw of an FP64 or plain run with a random checkpoint interval,
   for the total utility or a random cotangent on x, against the CPU reference gradient.
+- Warm starts: new capacities (some links kept, the others scaled by U[0.2, 1.5]) set
+  after k1 iterations, then k2 more, against the oracle switching at the same iteration.
 
 FP64 results must match to 1e-9 and FP32 to 1e-4 in relative norm.  Prices are marginal
 utilities, of the order of w / x, and an uncongested link's price tends to zero through
@@ -197,3 +199,45 @@ def test_random_adjoints_match_reference(case):
     assert price_err(gc, rc, inst) <= 1e-9, price_err(gc, rc, inst)
     floor = 1e-3 * np.sqrt(rw.size)
     assert np.linalg.norm(gw - rw) / max(np.linalg.norm(rw), floor) <= 1e-9
+
+
+# ---- warm starts after a capacity change --------------------------------------------------
+
+@st.composite
+def switch_cases(draw):
+    inst = draw(instances(max_n=1500, max_m=300))
+    params = solver_params(draw)
+    k1 = draw(st.integers(0, 150))
+    k2 = draw(st.integers(1, 150))
+    path = draw(st.sampled_from(["fp64_rows", "plain", "fp32_rows"]))
+    seed = draw(st.integers(0, 2**31 - 1))
+    rng = np.random.default_rng(seed)
+    c = np.asarray(inst["c"], dtype=np.float64)
+    keep = rng.random(c.size) < draw(st.sampled_from([0.0, 0.5, 0.9]))
+    c_new = np.where(keep, c, c * rng.uniform(0.2, 1.5, c.size))
+    return inst, params, k1, k2, path, c_new
+
+
+@settings(max_examples=50, **FUZZ)
+@given(switch_cases())
+def test_random_capacity_switches_match_oracle(case):
+    """num_set_capacity after k1 iterations, then k2 more, against the oracle whose
+    capacities switch at iteration k1 (the warm start of Sec. V-D)."""
+    from paper_2509_10722_b300 import capi
+    inst, params, k1, k2, path, c_new = case
+    if k1 == 0:  # a switch before the first iteration is a cold start on the new network
+        ref = oracle_run(dict(inst, c=c_new), k2, **params)
+    else:
+        ref = oracle_run(inst, k1 + k2, c_switch=c_new, switch_iter=k1, **params)
+    precision = {"fp64_rows": 1, "plain": 2, "fp32_rows": 0}[path]
+    with capi.Problem(inst, precision=precision, history=k1 + k2, **gpu_params(params)) as p:
+        if precision == 0:
+            p.set_rho_schedule(ref["decisions"])
+        p.solve(k1, 0.0)
+        p.set_capacity(c_new)
+        p.solve(k2, 0.0)
+        x, lam, _ = p.get()
+    tol = 1e-4 if precision == 0 else 1e-9
+    assert rel(x, ref["x"]) <= tol, (path, rel(x, ref["x"]))
+    err = price_err(lam, ref["lam"], inst)
+    assert err <= tol, (path, err)
