@@ -180,6 +180,24 @@ def parse_clocks(text):
             "reasons": sorted(reasons), "samples": len(sm)}
 
 
+class Measured:
+    """SM clocks sampled and library kernels counted over a region of a scenario run."""
+
+    def __init__(self, torch, capi):
+        self.sampler = ClockSampler(torch.cuda.current_device())
+        self.capi = capi
+        self.clocks, self.launches = None, 0
+
+    def start(self):
+        self.sampler.start()
+        self.l0 = self.capi.num_kernel_launches()
+        return self
+
+    def stop(self):
+        self.launches = int(self.capi.num_kernel_launches() - self.l0)
+        self.clocks = self.sampler.stop()
+
+
 # ---- helpers --------------------------------------------------------------------------------------
 
 def measured_peaks():
@@ -733,6 +751,7 @@ def run_congestion(args):
     stream = torch.cuda.Stream()
     sp = stream.cuda_stream
     out = {}
+    meas = Measured(torch, capi).start()
     for name, inst in (("uncongested", base), ("congested", cong)):
         deg = np.bincount(inst["route_links"], minlength=inst["m"])
         with capi.Problem(inst, stream=sp, precision=0) as p:
@@ -749,6 +768,7 @@ def run_congestion(args):
                      "ms_per_iteration": e0.elapsed_time(e1) / max(int(it), 1),
                      "nnz": int(inst["route_ptr"][-1]), "max_link_degree": int(deg.max()),
                      "objective": info["objective"]}
+    meas.stop()
     u, c = out["uncongested"], out["congested"]
     line = {"metric": "iterations to eps_abs 1e-4 with and without congestion (Sec. V-C)",
             "value": c["iterations"] - u["iterations"], "unit": "extra iterations",
@@ -758,7 +778,7 @@ def run_congestion(args):
                                    "0.1% of links each on 10% of the streams",
                        "eps_abs": args.eps, "scale": args.scale},
             "paper": "about 1,000 iterations uncongested, a few hundred more congested",
-            **out}
+            **out, "gpu_launches": meas.launches, "clocks": meas.clocks}
     print(json.dumps(line), flush=True)
 
 
@@ -783,6 +803,7 @@ def run_warmstart(args):
         return e0.elapsed_time(e1), it, status
 
     out = {}
+    meas = Measured(torch, capi).start()
     with capi.Problem(inst, stream=sp, precision=0) as p:
         t0, it0, _ = timed_solve(p)
         base_state = p.get_state()
@@ -803,6 +824,7 @@ def run_warmstart(args):
         tc, ic, sc = timed_solve(q)
         q.set_state(warm)
         tw, iw, sw = timed_solve(q)
+    meas.stop()
     out["fail_prune"] = {"links_failed": int(failed.sum()), "streams_left": pr["n"],
                          "links_left": pr["m"], "warm_ms": tw, "warm_iters": iw, "cold_ms": tc,
                          "cold_iters": ic, "speedup_time": tc / tw,
@@ -813,7 +835,7 @@ def run_warmstart(args):
             "config": {"workload": f"{args.workload}: {WORKLOAD_TEXT[args.workload]}",
                        "scale": args.scale, "base_solve_ms": t0, "base_iters": it0},
             "paper": {"degrade": "about 5x", "fail_prune": "about 10x (pruned vs full cold)"},
-            **out}
+            **out, "gpu_launches": meas.launches, "clocks": meas.clocks}
     print(json.dumps(line), flush=True)
 
 
@@ -830,6 +852,7 @@ def run_adjoint(args):
     iters, kc = 500, 50
     out = {}
     grads = {}
+    meas = Measured(torch, capi).start()
     for name, prec in (("fp32", 0), ("fp64", 1)):
         with capi.Problem(inst, stream=sp, precision=prec) as p:
             p.adjoint(iters, kc)  # warm-up
@@ -857,6 +880,7 @@ def run_adjoint(args):
                      "one_segment_ratio": t_one / t_fwd,
                      "one_segment_equal": bool(np.array_equal(cg, cg1) and
                                                np.array_equal(wg, wg1))}
+    meas.stop()
     rel = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))
     line = {"metric": "adjoint of 500 unrolled PMP iterations (dJ/dc, dJ/dw), c5",
             "value": out["fp32"]["adjoint_ms"], "unit": "ms", "higher_is_better": False,
@@ -866,7 +890,8 @@ def run_adjoint(args):
                        "checkpoint_every": kc, "scale": args.scale},
             **out,
             "fp32_vs_fp64": {"dc_rel": rel(grads["fp32"][0], grads["fp64"][0]),
-                             "dw_rel": rel(grads["fp32"][1], grads["fp64"][1])}}
+                             "dw_rel": rel(grads["fp32"][1], grads["fp64"][1])},
+            "gpu_launches": meas.launches, "clocks": meas.clocks}
     print(json.dumps(line), flush=True)
 
 
