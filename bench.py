@@ -211,7 +211,7 @@ def measured_peaks():
 ROW_SOURCES = ("rows.cu", "pmp_rows.cuh", "pmp_device.cuh", "pmp_internal.cuh")
 TRAFFIC_CMD = ("ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum --clock-control none "
                "--print-units base -k regex:\"k_(stream|link)_rows\" -s 200 -c 2 --csv "
-               "--log-file gpurun_out/traffic.csv python bench.py --steps 1 --warmup 0 "
+               "--log-file traffic.csv python bench.py --steps 1 --warmup 0 "
                "--no-fp64 --no-e2e --no-cpu-baseline")
 
 
