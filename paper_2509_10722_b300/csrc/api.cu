@@ -242,9 +242,13 @@ int create_impl(num_problem** out, int64_t n, int64_t m, const int64_t* route_pt
 
     int64_t p0 = 0, nnz = 0;
     if (on_device) {
-        cudaError_t e = cudaMemcpy(&p0, route_ptr, sizeof(int64_t), cudaMemcpyDeviceToHost);
+        // on the caller's stream, so that work it queued there (which may be what fills
+        // route_ptr) comes first; NULL is the legacy default stream
+        cudaStream_t us = (cudaStream_t)cuda_stream;
+        cudaError_t e = cudaMemcpyAsync(&p0, route_ptr, sizeof(int64_t), cudaMemcpyDeviceToHost, us);
         if (e == cudaSuccess)
-            e = cudaMemcpy(&nnz, route_ptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost);
+            e = cudaMemcpyAsync(&nnz, route_ptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost, us);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(us);
         if (e != cudaSuccess) return cuda_fail(e, "reading route_ptr");
     } else {
         p0 = route_ptr[0];
