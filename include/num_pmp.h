@@ -154,7 +154,10 @@ NUM_API int num_create(num_problem** out, int64_t n, int64_t m, const int64_t* r
                const double* w, const double* lo, const double* hi, const num_params* p,
                void* cuda_stream);
 
-/* As num_create, with every array argument a DEVICE pointer (same layout, same rules). */
+/* As num_create, with every array argument a DEVICE pointer (same layout, same rules).
+ * The arrays are read in the order of cuda_stream: work the caller queued on that stream
+ * before the call (for example, what fills the arrays) completes first.  The arrays of
+ * num_create are host memory and are read when the call is made. */
 NUM_API int num_create_device(num_problem** out, int64_t n, int64_t m, const int64_t* route_ptr,
                       const int32_t* route_links, const double* c, const uint8_t* utype,
                       const double* w, const double* lo, const double* hi,
