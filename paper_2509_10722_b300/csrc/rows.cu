@@ -91,16 +91,31 @@ __global__ void __launch_bounds__(kTh) k_link_rows(View<T> v) {
     const int* __restrict__ col_idx = v.col_idx;
     const T* __restrict__ x = v.x;
     Acc<T> r2, s2;
-    // links of up to kLongRow streams: one group each
+    // links of up to kLongRow streams: one group each; the bounds of the group's next link
+    // are loaded before the current link is summed, so they are at hand when it is done
     constexpr int kGroups = kTh / kGroup;
-    for (int l = blockIdx.x * kGroups + (int)(threadIdx.x / kGroup); l < m;
-         l += gridDim.x * kGroups) {
-        const int p0 = __ldg(row_ptr + l), p1 = __ldg(row_ptr + l + 1);
-        if (p1 - p0 > kLongRow) continue;  // done by its chunks
-        LinkState<T> st;
-        if (leader) st = load_link(v, l);
-        const T s = group_gather_sum<kGroup>(g, col_idx, x, p0, p1, v.n, v.dbg);
-        if (leader) link_epilogue(v, l, st, s, p1 - p0, alpha, rho, inv_rho, r2, s2);
+    int l = blockIdx.x * kGroups + (int)(threadIdx.x / kGroup);
+    int p0 = 0, p1 = 0;
+    if (l < m) {
+        p0 = __ldg(row_ptr + l);
+        p1 = __ldg(row_ptr + l + 1);
+    }
+    while (l < m) {
+        const int ln = l + gridDim.x * kGroups;
+        int q0 = 0, q1 = 0;
+        if (ln < m) {
+            q0 = __ldg(row_ptr + ln);
+            q1 = __ldg(row_ptr + ln + 1);
+        }
+        if (p1 - p0 <= kLongRow) {  // longer links are done by their chunks
+            LinkState<T> st;
+            if (leader) st = load_link(v, l);
+            const T s = group_gather_sum<kGroup>(g, col_idx, x, p0, p1, v.n, v.dbg);
+            if (leader) link_epilogue(v, l, st, s, p1 - p0, alpha, rho, inv_rho, r2, s2);
+        }
+        l = ln;
+        p0 = q0;
+        p1 = q1;
     }
     // chunks of the longer links: one warp each (four gathers in flight per lane), so that
     // a chunk is a short chain of round trips and the chunks balance across warps
