@@ -103,6 +103,7 @@ struct View {
     double* part_s;             // per-block residual partials of the stream kernel [grid_s]
     double* part_l;             // ... of the link kernel [2 * grid_l]
     int grid_s, grid_l;
+    int link_pairs;             // row link kernel: pairs of gathers in flight per lane (1, 2)
     const int4* chunks;         // row kernels: (link, first entry, end entry, first chunk)
     int nchunks;
     const int* perm;            // caller's index of the stream at each position (or NULL)
@@ -239,7 +240,11 @@ template <typename T>
 cudaError_t set_weights(const View<T>& v, const double* w, cudaStream_t st);
 
 // ---- row kernels (rows.cu) ------------------------------------------------------------------
-cudaError_t rows_grids(int precision, int n, int m, int nchunks, int* grid_s, int* grid_l);
+// Grids of the two row kernels, and the link kernel's pairs of gathers in flight per lane:
+// 2 when each group has few links to sum (a short chain of dependent loads per group is
+// then the limit), else 1; the sums are the same either way.
+cudaError_t rows_grids(int precision, int n, int m, int nchunks, int* grid_s, int* grid_l,
+                       int* link_pairs);
 template <typename T>
 cudaError_t rows_iteration(const View<T>& v, cudaStream_t st, cudaEvent_t* evs);
 // Chunk table of the links with more than kLongRow streams: counts[m+1] and offs[m+1] are

@@ -136,19 +136,27 @@ __device__ __forceinline__ void link_epilogue(const View<T>& v, int l, const Lin
 }
 
 // Sum of x over entries [e0, e1) of the link-major index array, by one group of G lanes,
-// in a fixed order (lane-strided, two loads in flight per lane, then a shuffle tree).
-template <int G, typename T, class Group>
+// in a fixed order: lane k adds the pairs (e, e + G) for e = e0 + k, e0 + k + 2G, ..., each
+// pair summed first, then the shuffle tree.  kPairs pairs of gathers are in flight per
+// lane; the additions keep the same order whatever kPairs is, so the result is too.
+template <int G, int kPairs = 1, typename T, class Group>
 __device__ __forceinline__ T group_gather_sum(const Group& g, const int* __restrict__ col_idx,
                                               const T* __restrict__ x, int e0, int e1, int n,
                                               unsigned int* dbg) {
     const int sl = g.thread_rank();
     T s = T(0);
-    for (int e = e0 + sl; e < e1; e += 2 * G) {
-        const int i0 = checked_index(__ldg(col_idx + e), n, dbg);
-        const int i1 = e + G < e1 ? checked_index(__ldg(col_idx + e + G), n, dbg) : -1;
-        const T a = __ldg(x + i0);
-        const T b = i1 >= 0 ? __ldg(x + i1) : T(0);
-        s += a + b;
+    for (int e = e0 + sl; e < e1; e += 2 * kPairs * G) {
+        int ix[2 * kPairs];
+#pragma unroll
+        for (int k = 0; k < 2 * kPairs; ++k)
+            ix[k] = (k == 0 || e + k * G < e1) ? checked_index(__ldg(col_idx + e + k * G), n, dbg)
+                                               : -1;
+        T v[2 * kPairs];
+#pragma unroll
+        for (int k = 0; k < 2 * kPairs; ++k) v[k] = ix[k] >= 0 ? __ldg(x + ix[k]) : T(0);
+#pragma unroll
+        for (int q = 0; q < kPairs; ++q)
+            if (q == 0 || e + 2 * q * G < e1) s += v[2 * q] + v[2 * q + 1];
     }
 #pragma unroll
     for (int o = G / 2; o > 0; o >>= 1) s += g.shfl_down(s, o);

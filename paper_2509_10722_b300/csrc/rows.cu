@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(kTh) k_stream_rows(View<T> v) {
 }
 // ---- link kernel ---------------------------------------------------------------------------------
 
-template <typename T>
+template <typename T, int kPairs>
 __global__ void __launch_bounds__(kTh) k_link_rows(View<T> v) {
     __shared__ double red[3 * kWarps];
     __shared__ int last;
@@ -110,7 +110,7 @@ __global__ void __launch_bounds__(kTh) k_link_rows(View<T> v) {
         if (p1 - p0 <= kLongRow) {  // longer links are done by their chunks
             LinkState<T> st;
             if (leader) st = load_link(v, l);
-            const T s = group_gather_sum<kGroup>(g, col_idx, x, p0, p1, v.n, v.dbg);
+            const T s = group_gather_sum<kGroup, kPairs>(g, col_idx, x, p0, p1, v.n, v.dbg);
             if (leader) link_epilogue(v, l, st, s, p1 - p0, alpha, rho, inv_rho, r2, s2);
         }
         l = ln;
@@ -166,32 +166,44 @@ __global__ void __launch_bounds__(kTh) k_link_rows(View<T> v) {
 }
 
 template <typename T>
-cudaError_t rows_occupancy(int* occ_s, int* occ_l) {
+cudaError_t rows_occupancy(int* occ_s, int* occ_l1, int* occ_l2) {
     // the variant with the warp phase uses at least as many registers
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ_s, k_stream_rows<T, true>,
                                                                   kTh, 0);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ_l, k_link_rows<T>, kTh, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ_l1, k_link_rows<T, 1>, kTh, 0);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ_l2, k_link_rows<T, 2>, kTh, 0);
 }
+
+// Two pairs in flight paid when each group slot of a resident grid had about 4 links to
+// sum (c5: 1e5 links) and cost when it had about 42 (c2: 1e6 links); the switch sits
+// between the two.
+constexpr int kFewLinksPerGroup = 16;
 
 }  // namespace
 
-cudaError_t rows_grids(int precision, int n, int m, int nchunks, int* grid_s, int* grid_l) {
-    int dev = 0, sms = 0, occ_s = 0, occ_l = 0;
+cudaError_t rows_grids(int precision, int n, int m, int nchunks, int* grid_s, int* grid_l,
+                       int* link_pairs) {
+    int dev = 0, sms = 0, occ_s = 0, occ_l1 = 0, occ_l2 = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
-    e = precision == 0 ? rows_occupancy<float>(&occ_s, &occ_l) : rows_occupancy<double>(&occ_s, &occ_l);
+    e = precision == 0 ? rows_occupancy<float>(&occ_s, &occ_l1, &occ_l2)
+                       : rows_occupancy<double>(&occ_s, &occ_l1, &occ_l2);
     if (e != cudaSuccess) return e;
-    if (occ_s < 1 || occ_l < 1) return cudaErrorInvalidConfiguration;
+    if (occ_s < 1 || occ_l1 < 1 || occ_l2 < 1) return cudaErrorInvalidConfiguration;
     const long long need_s = ((long long)n + kTh - 1) / kTh;
     const long long need_l = ((long long)m + nchunks + (kTh / kGroup) - 1) / (kTh / kGroup);
-    long long gs = (long long)occ_s * sms, gl = (long long)occ_l * sms;
+    const long long full_l1 = (long long)occ_l1 * sms;
+    const int pairs = (long long)m <= (long long)kFewLinksPerGroup * full_l1 * (kTh / kGroup) ? 2 : 1;
+    long long gs = (long long)occ_s * sms, gl = (long long)(pairs == 2 ? occ_l2 : occ_l1) * sms;
     gs = gs < need_s ? gs : need_s;
     gl = gl < need_l ? gl : need_l;
     *grid_s = (int)(gs < kMaxRowsGrid ? gs : kMaxRowsGrid);
     *grid_l = (int)(gl < kMaxRowsGrid ? gl : kMaxRowsGrid);
+    *link_pairs = pairs;
     return cudaSuccess;
 }
 
@@ -202,7 +214,10 @@ cudaError_t rows_iteration(const View<T>& v, cudaStream_t st, cudaEvent_t* evs) 
     else
         k_stream_rows<T, false><<<v.grid_s, kTh, 0, st>>>(v);
     if (evs) record_kernel_event(evs[0], st);
-    k_link_rows<T><<<v.grid_l, kTh, 0, st>>>(v);
+    if (v.link_pairs == 2)
+        k_link_rows<T, 2><<<v.grid_l, kTh, 0, st>>>(v);
+    else
+        k_link_rows<T, 1><<<v.grid_l, kTh, 0, st>>>(v);
     if (evs) record_kernel_event(evs[1], st);
     return cudaGetLastError();
 }
