@@ -70,11 +70,25 @@ __global__ void __launch_bounds__(kTh) k_adj_link(AdjView<T> a, const T* __restr
          l += gridDim.x * kGroups) {
         const int p0 = __ldg(v.row_ptr + l), p1 = __ldg(v.row_ptr + l + 1);
         if (a.abc && p1 - p0 > kLongRow) continue;  // done by its chunks
-        T sa = T(0), sb = T(0);  // R Abar, R Bbar: fixed order over the link's streams
-        for (int e = p0 + g.thread_rank(); e < p1; e += kGroup) {
-            const T2 ab = a.ab[checked_index(__ldg(v.col_idx + e), v.n, v.dbg)];
-            sa += ab.x;
-            sb += ab.y;
+        // R Abar, R Bbar: lane k adds entries p0 + k, p0 + k + kGroup, ... in that order,
+        // four gathers in flight
+        T sa = T(0), sb = T(0);
+        for (int e = p0 + g.thread_rank(); e < p1; e += 4 * kGroup) {
+            int ix[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                ix[k] = (k == 0 || e + k * kGroup < p1)
+                            ? checked_index(__ldg(v.col_idx + e + k * kGroup), v.n, v.dbg)
+                            : -1;
+            T2 u[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) u[k] = ix[k] >= 0 ? __ldg(a.ab + ix[k]) : T2{T(0), T(0)};
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                if (ix[k] >= 0) {
+                    sa += u[k].x;
+                    sb += u[k].y;
+                }
         }
 #pragma unroll
         for (int o = kGroup / 2; o > 0; o >>= 1) {
@@ -179,8 +193,21 @@ __global__ void __launch_bounds__(kTh) k_adj_stream(AdjView<T> a, const T* __res
     for (int j = blockIdx.x * kTh + threadIdx.x; j < v.n; j += gridDim.x * kTh) {
         const int p = __ldg(v.col_ptr + j), pn = __ldg(v.col_ptr + j + 1);
         if (split && pn - p > kLongRoute) continue;  // summed by a warp below
-        T r = T(0);
-        for (int e = p; e < pn; ++e) r += a.Rxb[checked_index(__ldg(v.row_idx + e), v.m, v.dbg)];
+        T r = T(0);  // (R' Rx_bar)_j in route order, four gathers in flight
+        int e = p;
+        for (; e + 4 <= pn; e += 4) {
+            const int l0 = checked_index(__ldg(v.row_idx + e), v.m, v.dbg);
+            const int l1 = checked_index(__ldg(v.row_idx + e + 1), v.m, v.dbg);
+            const int l2 = checked_index(__ldg(v.row_idx + e + 2), v.m, v.dbg);
+            const int l3 = checked_index(__ldg(v.row_idx + e + 3), v.m, v.dbg);
+            const T g0 = __ldg(a.Rxb + l0), g1 = __ldg(a.Rxb + l1);
+            const T g2 = __ldg(a.Rxb + l2), g3 = __ldg(a.Rxb + l3);
+            r += g0;
+            r += g1;
+            r += g2;
+            r += g3;
+        }
+        for (; e < pn; ++e) r += __ldg(a.Rxb + checked_index(__ldg(v.row_idx + e), v.m, v.dbg));
         adj_stream_epilogue(a, j, r, pn - p, x_k, alpha, rho);
     }
     // streams with more than kLongRoute links: one warp each, as in the forward kernel
