@@ -128,17 +128,28 @@ def test_batch_rejects_cross_instance_routes():
 
 def test_c4_recipe_batch_converges():
     """The batched recipe (256 instances, n log-uniform in [1e3, 1e5], m = n / 10, routes of
-    2..8 links, degraded capacities): every instance reaches eps_abs = 1e-4, and sampled
-    instances match their FP64 oracle objective at the same tolerance to 1e-5."""
+    2..8 links, degraded capacities), FP32: every instance reaches eps_abs = 1e-4; every
+    instance's objective matches the FP64 batch stopped by the same test to 1e-5; and a
+    sample of instances (the four smallest and four drawn at random among those below
+    2e4 streams) matches the FP64 oracle objective at the same tolerance to 1e-5."""
     from oracle import kkt
     insts = W.batched_instances(256, seed=0)
     g = _run_batch(insts, 50_000, 0, eps=1e-4)
     assert np.all(g["status"] == 0)
-    order = np.argsort([t["n"] for t in insts])
-    for i in order[:4]:
+    g64 = _run_batch(insts, 50_000, 1, eps=1e-4)
+    assert np.all(g64["status"] == 0)
+    for i in range(len(insts)):
+        o32, o64 = g["info"][i]["objective"], g64["info"][i]["objective"]
+        assert abs(o32 - o64) <= 1e-5 * abs(o64), i
+    ns = np.array([t["n"] for t in insts])
+    order = np.argsort(ns)
+    pool = np.flatnonzero((ns < 20_000) & ~np.isin(np.arange(ns.size), order[:4]))
+    sample = list(order[:4]) + list(np.random.default_rng(4).choice(pool, 4, replace=False))
+    for i in sample:
         ref = oracle_run(insts[i], 100_000, eps=1e-4)
         u = kkt.utility(insts[i], ref["x"])
         assert abs(g["info"][i]["objective"] - u) <= 1e-5 * abs(u), i
+        assert int(g64["iters"][i]) == int(ref["iters"]), i  # FP64: the oracle's stop
 
 
 # ---- the work partition and its autotuner ---------------------------------------------------
