@@ -329,6 +329,29 @@ NUM_API int num_batch_create(num_batch** out, int32_t count, const int64_t* stre
                              const uint8_t* utype, const double* w, const double* lo,
                              const double* hi, const num_params* p, void* cuda_stream);
 
+/* One instance of a batch, as HOST arrays in the layout of num_create (its own link ids
+ * 0..m-1; lo may be NULL for lo = 0). */
+typedef struct {
+    int64_t n, m;
+    const int64_t* route_ptr; /* n + 1, route_ptr[0] = 0 */
+    const int32_t* route_links;
+    const double* c;
+    const uint8_t* utype;
+    const double* w;
+    const double* lo; /* or NULL */
+    const double* hi;
+} num_instance;
+
+/* Create a batch from `count` separate instances (HOST array insts[count]), as
+ * num_batch_create would from their block-diagonal stack, without the caller stacking
+ * them: the arrays of each instance are copied to their place in the stacked device arrays
+ * and the link ids and route offsets are shifted there, on the device.  Instance i then
+ * owns the streams and links that follow those of instances 0..i-1.  The same checks,
+ * parameters and results as num_batch_create; the caller keeps ownership of every array.
+ * Synchronizes the stream. */
+NUM_API int num_batch_create_instances(num_batch** out, int32_t count, const num_instance* insts,
+                                       const num_params* p, void* cuda_stream);
+
 /* Force the first len rho decisions of every instance: decisions[i * len + q] is the
  * decision of instance i at its q-th update point (-1, 0, +1; host array, copied). */
 NUM_API int num_batch_set_rho_schedules(num_batch* b, const int8_t* decisions, int64_t len);

@@ -59,6 +59,14 @@ class num_params(ctypes.Structure):
                 ("allocator", ctypes.POINTER(num_allocator))]
 
 
+class num_instance(ctypes.Structure):
+    """One instance of a batch (host arrays, its own link ids)."""
+    _fields_ = [("n", ctypes.c_int64), ("m", ctypes.c_int64),
+                ("route_ptr", ctypes.c_void_p), ("route_links", ctypes.c_void_p),
+                ("c", ctypes.c_void_p), ("utype", ctypes.c_void_p), ("w", ctypes.c_void_p),
+                ("lo", ctypes.c_void_p), ("hi", ctypes.c_void_p)]
+
+
 class BatchSchedule(ctypes.Structure):
     """num_batch_schedule: work partition of a batch's kernels."""
     _fields_ = [("stream_item", ctypes.c_int32), ("link_item", ctypes.c_int32),
@@ -105,6 +113,8 @@ def _load():
         "num_measure_gather_rate": (ctypes.c_int, [i64, i64, i32, i32, ctypes.POINTER(d)]),
         "num_batch_create": (ctypes.c_int, [ctypes.POINTER(P), i32, P, P, P, P, P, P, P, P, P,
                                             pp, P]),
+        "num_batch_create_instances": (ctypes.c_int, [ctypes.POINTER(P), i32,
+                                                      ctypes.POINTER(num_instance), pp, P]),
         "num_batch_set_rho_schedules": (ctypes.c_int, [P, P, i64]),
         "num_batch_solve": (ctypes.c_int, [P, i64, d, P, P]),
         "num_batch_get": (ctypes.c_int, [P, P, P, P]),
@@ -133,7 +143,8 @@ EXPORTED = ("num_default_params", "num_create", "num_create_device", "num_set_rh
             "num_iteration_bytes", "num_get_kernel_times", "num_kernel_launches",
             "num_objective_noalloc", "num_measure_gather_rate", "num_destroy", "num_strerror",
             "num_last_error",
-            "num_batch_create", "num_batch_set_rho_schedules", "num_batch_solve",
+            "num_batch_create", "num_batch_create_instances", "num_batch_set_rho_schedules",
+            "num_batch_solve",
             "num_batch_get", "num_batch_get_kernel_times", "num_batch_get_schedule",
             "num_batch_set_schedule", "num_batch_autotune", "num_batch_destroy")
 
@@ -404,19 +415,44 @@ class Batch:
     """Owner of a num_batch over a list of instance dicts (see workloads.py)."""
 
     def __init__(self, insts, stream=None, **params):
+        """The instances are passed one by one (num_batch_create_instances): the library
+        stacks them on the device, so nothing is concatenated on the host."""
         self.count = len(insts)
-        self.so, self.lo, st = stack_instances(insts)
-        self.n, self.m = st["n"], st["m"]
+        self.so = np.zeros(self.count + 1, dtype=np.int64)
+        self.lo = np.zeros(self.count + 1, dtype=np.int64)
+        np.cumsum([int(t["n"]) for t in insts], out=self.so[1:])
+        np.cumsum([int(t["m"]) for t in insts], out=self.lo[1:])
+        self.n, self.m = int(self.so[-1]), int(self.lo[-1])
         self.params = num_default_params(**params)
+        keep = []  # the arrays must stay alive during the call
+
+        def arr(a, dtype, size, name):
+            a = np.ascontiguousarray(a, dtype=dtype)
+            if a.shape != (size,):
+                raise ValueError(f"{name} must have {size} elements, got {a.shape}")
+            keep.append(a)
+            return a.ctypes.data
+
+        table = (num_instance * self.count)()
+        for i, t in enumerate(insts):
+            n, m = int(t["n"]), int(t["m"])
+            rp = arr(t["route_ptr"], np.int64, n + 1, "route_ptr")
+            nnz = int(keep[-1][-1]) if keep[-1][0] == 0 else 0
+            rl = np.ascontiguousarray(t["route_links"], dtype=np.int32)
+            if rl.size < nnz:
+                raise ValueError("route_links shorter than route_ptr[n]")
+            keep.append(rl)
+            lo = t.get("lo")
+            table[i] = num_instance(n, m, rp, rl.ctypes.data, arr(t["c"], np.float64, m, "c"),
+                                    arr(t["utype"], np.uint8, n, "utype"),
+                                    arr(t["w"], np.float64, n, "w"),
+                                    None if lo is None else arr(lo, np.float64, n, "lo"),
+                                    arr(t["hi"], np.float64, n, "hi"))
         h = ctypes.c_void_p()
-        arrs = [np.ascontiguousarray(st["route_ptr"], np.int64),
-                np.ascontiguousarray(st["route_links"], np.int32),
-                np.ascontiguousarray(st["c"], np.float64), np.ascontiguousarray(st["utype"], np.uint8),
-                np.ascontiguousarray(st["w"], np.float64), np.ascontiguousarray(st["lo"], np.float64),
-                np.ascontiguousarray(st["hi"], np.float64)]
-        _check(_lib.num_batch_create(ctypes.byref(h), self.count, _hptr(self.so), _hptr(self.lo),
-                                     *[_hptr(a) for a in arrs], ctypes.byref(self.params),
-                                     ctypes.c_void_p(stream) if stream else None))
+        _check(_lib.num_batch_create_instances(ctypes.byref(h), self.count, table,
+                                               ctypes.byref(self.params),
+                                               ctypes.c_void_p(stream) if stream else None))
+        del keep
         self.h = h
 
     def set_rho_schedules(self, decisions):

@@ -275,6 +275,39 @@ __global__ void k_check_blocks(int count, const int64_t* __restrict__ stream_off
     if (bad) atomicOr(err, VB_BLOCKS);
 }
 
+// The largest i in [0, count) with off[i] <= pos (off increasing, off[0] <= pos).
+__device__ __forceinline__ int block_of(const int64_t* __restrict__ off, int count, long long pos) {
+    int lo = 0, hi = count - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= pos)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+// Shift the instances' own numbering to the stacked one, in place: route_ptr[p] of instance
+// i (p in (so[i], so[i+1]]) gains the entries of instances 0..i-1, eo[i]; its link ids gain
+// the links before it, lo[i].  A link id that leaves the int32 range becomes -1, which the
+// validation rejects.
+__global__ void k_stack_offsets(int count, const int64_t* __restrict__ so,
+                                const int64_t* __restrict__ lo, const int64_t* __restrict__ eo,
+                                int64_t* route_ptr, int* route_links, long long n, long long nnz) {
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n + nnz;
+         q += (long long)gridDim.x * blockDim.x) {
+        if (q < n) {
+            const long long p = q + 1;
+            route_ptr[p] += eo[block_of(so, count, p - 1)];
+        } else {
+            const long long e = q - n;
+            const long long l = (long long)route_links[e] + lo[block_of(eo, count, e)];
+            route_links[e] = (l >= 0 && l <= 2147483647LL) ? (int)l : -1;
+        }
+    }
+}
+
 __global__ void k_batch_arm(Ctl* ctls, BatchGlobal* glob, int count, long long max_iters,
                             double eps_abs, const double* eps_scale) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
@@ -362,6 +395,15 @@ cudaError_t check_blocks(int count, const int64_t* stream_off, const int64_t* li
                          cudaStream_t st) {
     k_check_blocks<<<blocks_for(n), kTh, 0, st>>>(count, stream_off, link_off, route_ptr,
                                                   route_links, err);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t stack_offsets(int count, const int64_t* so, const int64_t* lo, const int64_t* eo,
+                          int64_t* route_ptr, int* route_links, long long n, long long nnz,
+                          cudaStream_t st) {
+    k_stack_offsets<<<blocks_for(n + nnz), kTh, 0, st>>>(count, so, lo, eo, route_ptr,
+                                                        route_links, n, nnz);
     note_launches(1);
     return cudaGetLastError();
 }

@@ -315,21 +315,13 @@ int batch_time_schedule(num_batch* b, const num_batch_schedule& cfg, int iters, 
     return NUM_OK;
 }
 
-}  // namespace
-
-extern "C" {
-
-int num_batch_create(num_batch** out, int32_t count, const int64_t* stream_off,
-                     const int64_t* link_off, const int64_t* route_ptr,
-                     const int32_t* route_links, const double* c, const uint8_t* utype,
-                     const double* w, const double* lo, const double* hi, const num_params* p,
-                     void* cuda_stream) {
-    TraceRange trace("num_batch_create");
-    g_last_error.clear();
-    if (!out) return fail(NUM_ERR_INVALID, "out is NULL");
-    *out = nullptr;
-    if (count < 1 || !stream_off || !link_off || !route_ptr)
-        return fail(NUM_ERR_INVALID, "count must be >= 1 and the offsets non-NULL");
+// The batch over a stacked problem (host or device arrays, as create_impl takes them);
+// inst_nnz[count] (host) holds each instance's route entries.  The offsets are checked.
+int batch_create_impl(num_batch** out, int32_t count, const int64_t* stream_off,
+                      const int64_t* link_off, const int64_t* inst_nnz, const int64_t* route_ptr,
+                      const int32_t* route_links, const double* c, const uint8_t* utype,
+                      const double* w, const double* lo, const double* hi, const num_params* p,
+                      void* cuda_stream, bool on_device) {
     if (stream_off[0] != 0 || link_off[0] != 0)
         return fail(NUM_ERR_INVALID, "stream_off[0] and link_off[0] must be 0");
     for (int i = 0; i < count; ++i)
@@ -352,7 +344,7 @@ int num_batch_create(num_batch** out, int32_t count, const int64_t* stream_off,
     b->loff.assign(link_off, link_off + count + 1);
     BatchSpec spec{count, stream_off, link_off};
     int rc = create_impl(&b->p, n, m, route_ptr, route_links, c, utype, w, lo, hi, &prm,
-                         cuda_stream, false, &spec);
+                         cuda_stream, on_device, &spec);
     if (rc != NUM_OK) {
         delete b;
         return rc;
@@ -364,8 +356,7 @@ int num_batch_create(num_batch** out, int32_t count, const int64_t* stream_off,
     for (int i = 0; i < count; ++i) {
         cap_s += (stream_off[i + 1] - stream_off[i] + kStreamItemMin - 1) / kStreamItemMin;
         cap_l += (link_off[i + 1] - link_off[i] + kLinkItemMin - 1) / kLinkItemMin;
-        const int64_t nnz_i = route_ptr[stream_off[i + 1]] - route_ptr[stream_off[i]];
-        b->J.push_back((double)(nnz_i + link_off[i + 1] - link_off[i]));
+        b->J.push_back((double)(inst_nnz[i] + link_off[i + 1] - link_off[i]));
         scale[i] = std::sqrt(b->J.back());
     }
     if (cap_s > INT32_MAX / 4 || cap_l > INT32_MAX / 4) {
@@ -429,6 +420,135 @@ int num_batch_create(num_batch** out, int32_t count, const int64_t* stream_off,
 #undef BK
     *out = b;
     return NUM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int num_batch_create(num_batch** out, int32_t count, const int64_t* stream_off,
+                     const int64_t* link_off, const int64_t* route_ptr,
+                     const int32_t* route_links, const double* c, const uint8_t* utype,
+                     const double* w, const double* lo, const double* hi, const num_params* p,
+                     void* cuda_stream) {
+    TraceRange trace("num_batch_create");
+    g_last_error.clear();
+    if (!out) return fail(NUM_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    if (count < 1 || !stream_off || !link_off || !route_ptr)
+        return fail(NUM_ERR_INVALID, "count must be >= 1 and the offsets non-NULL");
+    const int64_t n = stream_off[count];
+    if (n < 1 || n > INT32_MAX - 1) return fail(NUM_ERR_INVALID, "total n must be in [1, 2^31 - 1)");
+    std::vector<int64_t> nnz(count);
+    for (int i = 0; i < count; ++i) {
+        if (stream_off[i + 1] <= stream_off[i] || stream_off[i + 1] > n)
+            return fail(NUM_ERR_INVALID, "every instance needs >= 1 stream");
+        nnz[i] = route_ptr[stream_off[i + 1]] - route_ptr[stream_off[i]];
+    }
+    return batch_create_impl(out, count, stream_off, link_off, nnz.data(), route_ptr,
+                             route_links, c, utype, w, lo, hi, p, cuda_stream, false);
+}
+
+int num_batch_create_instances(num_batch** out, int32_t count, const num_instance* insts,
+                               const num_params* p, void* cuda_stream) {
+    TraceRange trace("num_batch_create_instances");
+    g_last_error.clear();
+    if (!out) return fail(NUM_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    if (count < 1 || !insts) return fail(NUM_ERR_INVALID, "count must be >= 1 and insts non-NULL");
+    std::vector<int64_t> so(count + 1, 0), lo(count + 1, 0), eo(count + 1, 0), nnz(count);
+    bool any_lo = false;
+    for (int i = 0; i < count; ++i) {
+        const num_instance& t = insts[i];
+        if (t.n < 1 || t.m < 1) return fail(NUM_ERR_INVALID, "every instance needs n, m >= 1");
+        if (!t.route_ptr || !t.route_links || !t.c || !t.utype || !t.w || !t.hi)
+            return fail(NUM_ERR_INVALID, "an instance has a required array NULL");
+        if (t.route_ptr[0] != 0) return fail(NUM_ERR_INVALID, "an instance has route_ptr[0] != 0");
+        nnz[i] = t.route_ptr[t.n];
+        if (nnz[i] < t.n) return fail(NUM_ERR_INVALID, "an instance has an empty route");
+        so[i + 1] = so[i] + t.n;
+        lo[i + 1] = lo[i] + t.m;
+        eo[i + 1] = eo[i] + nnz[i];
+        if (so[i + 1] > INT32_MAX - 1 || lo[i + 1] > INT32_MAX - 1 || eo[i + 1] > INT32_MAX - 1)
+            return fail(NUM_ERR_INVALID, "the stacked problem exceeds 2^31 - 1 streams, links or entries");
+        any_lo = any_lo || t.lo != nullptr;
+    }
+    num_params prm;
+    if (p)
+        prm = *p;
+    else
+        num_default_params(&prm);
+    const size_t N = (size_t)so[count], M = (size_t)lo[count], NNZ = (size_t)eo[count];
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    // the stacked inputs live on the device only for the duration of this call
+    std::vector<std::pair<void*, size_t>> bufs;
+    auto alloc = [&](size_t bytes) -> void* {
+        void* q = nullptr;
+        if (prm.allocator) {
+            q = prm.allocator->alloc(prm.allocator->ctx, bytes, st);
+        } else if (cudaMalloc(&q, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            q = nullptr;
+        }
+        if (q) bufs.push_back({q, bytes});
+        return q;
+    };
+    auto release = [&]() {
+        cudaStreamSynchronize(st);
+        for (auto& q : bufs) {
+            if (prm.allocator)
+                prm.allocator->release(prm.allocator->ctx, q.first, q.second, st);
+            else
+                cudaFree(q.first);
+        }
+        bufs.clear();
+    };
+    int64_t* d_rp = (int64_t*)alloc(8 * (N + 1));
+    int32_t* d_rl = (int32_t*)alloc(4 * NNZ);
+    double* d_c = (double*)alloc(8 * M);
+    uint8_t* d_ut = (uint8_t*)alloc(N);
+    double* d_w = (double*)alloc(8 * N);
+    double* d_lo = any_lo ? (double*)alloc(8 * N) : nullptr;
+    double* d_hi = (double*)alloc(8 * N);
+    int64_t* d_off = (int64_t*)alloc(8 * 3 * ((size_t)count + 1));
+    if (!d_rp || !d_rl || !d_c || !d_ut || !d_w || (any_lo && !d_lo) || !d_hi || !d_off) {
+        release();
+        return fail(NUM_ERR_OOM, "device allocation failed");
+    }
+    cudaError_t e = cudaMemsetAsync(d_rp, 0, 8, st);
+    for (int i = 0; i < count && e == cudaSuccess; ++i) {
+        const num_instance& t = insts[i];
+        const size_t n = (size_t)t.n, m = (size_t)t.m;
+        e = cudaMemcpyAsync(d_rp + so[i] + 1, t.route_ptr + 1, 8 * n, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(d_rl + eo[i], t.route_links, 4 * (size_t)nnz[i],
+                                cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(d_c + lo[i], t.c, 8 * m, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(d_ut + so[i], t.utype, n, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(d_w + so[i], t.w, 8 * n, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(d_hi + so[i], t.hi, 8 * n, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess && d_lo)
+            e = t.lo ? cudaMemcpyAsync(d_lo + so[i], t.lo, 8 * n, cudaMemcpyHostToDevice, st)
+                     : cudaMemsetAsync(d_lo + so[i], 0, 8 * n, st);  // +0.0 is all zero bits
+    }
+    std::vector<int64_t> offs;
+    offs.insert(offs.end(), so.begin(), so.end());
+    offs.insert(offs.end(), lo.begin(), lo.end());
+    offs.insert(offs.end(), eo.begin(), eo.end());
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_off, offs.data(), 8 * offs.size(), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = pmp::stack_offsets(count, d_off, d_off + count + 1, d_off + 2 * (count + 1), d_rp,
+                               d_rl, (long long)N, (long long)NNZ, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // offs is a pageable host vector
+    if (e != cudaSuccess) {
+        release();
+        return cuda_fail(e, "stacking the instances");
+    }
+    const int rc = batch_create_impl(out, count, so.data(), lo.data(), nnz.data(), d_rp, d_rl,
+                                     d_c, d_ut, d_w, d_lo, d_hi, &prm, cuda_stream, true);
+    release();
+    return rc;
 }
 
 int num_batch_set_rho_schedules(num_batch* b, const int8_t* decisions, int64_t len) {

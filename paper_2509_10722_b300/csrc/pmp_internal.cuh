@@ -201,6 +201,12 @@ cudaError_t batch_grids(int precision, int lanes, int nsitems, int nlitems, int 
 cudaError_t check_blocks(int count, const int64_t* stream_off, const int64_t* link_off,
                          long long n, const int64_t* route_ptr, const int* route_links, int* err,
                          cudaStream_t st);
+// In place on the device: route_ptr[1..n] and route_links[0..nnz) of instances copied
+// one after the other, each in its own numbering, shifted to the stacked numbering (so,
+// lo, eo: device int64[count + 1] offsets of the streams, links and entries).
+cudaError_t stack_offsets(int count, const int64_t* so, const int64_t* lo, const int64_t* eo,
+                          int64_t* route_ptr, int* route_links, long long n, long long nnz,
+                          cudaStream_t st);
 template <typename T>
 cudaError_t batch_iteration(const BatchView<T>& b, int grid_s, int grid_l, cudaStream_t st,
                             cudaEvent_t* evs);

@@ -227,3 +227,67 @@ def test_bad_partitions_are_rejected(bad):
             b.set_schedule(*bad)
         assert e.value.code == capi.NUM_ERR_INVALID
         assert b.schedule() == (2048, 256, 8)
+
+
+# ---- creation from separate instances (num_batch_create_instances) -------------------------
+
+def _create_stacked(insts, precision):
+    """A batch through num_batch_create from arrays stacked on the host."""
+    import ctypes
+    from paper_2509_10722_b300 import capi
+    so, lo, st = capi.stack_instances(insts)
+    prm = capi.num_default_params(precision=precision, history=64)
+    arrs = [np.ascontiguousarray(st[k], dt) for k, dt in
+            (("route_ptr", np.int64), ("route_links", np.int32), ("c", np.float64),
+             ("utype", np.uint8), ("w", np.float64), ("lo", np.float64), ("hi", np.float64))]
+    h = ctypes.c_void_p()
+    rc = capi.library().num_batch_create(ctypes.byref(h), len(insts), capi._hptr(so),
+                                         capi._hptr(lo), *[capi._hptr(a) for a in arrs],
+                                         ctypes.byref(prm), None)
+    assert rc == 0, capi.num_last_error()
+    return h, int(so[-1]), int(lo[-1])
+
+
+def test_instances_equal_host_stacked(batch):
+    """Stacking on the device gives the same batch as stacking on the host: bit-identical
+    iterates after 150 iterations, FP32 and FP64.  Half the instances pass lo = None."""
+    from paper_2509_10722_b300 import capi
+    insts = [dict(t, lo=None) if i % 2 else t for i, t in enumerate(batch)]
+    insts_host = [dict(t, lo=np.zeros(t["n"])) if t["lo"] is None else t for t in insts]
+    for precision in (0, 1):
+        h, n, m = _create_stacked(insts_host, precision)
+        try:
+            capi.library().num_batch_solve(h, 150, 0.0, None, None)
+            x1, p1 = np.empty(n), np.empty(m)
+            assert capi.library().num_batch_get(h, capi._hptr(x1), capi._hptr(p1), None) == 0
+        finally:
+            capi.library().num_batch_destroy(h)
+        with capi.Batch(insts, precision=precision, history=64) as b:
+            b.solve(150, 0.0)
+            xs, ps, _ = b.get()
+        assert np.array_equal(np.concatenate(xs), x1) and np.array_equal(np.concatenate(ps), p1)
+
+
+@pytest.mark.parametrize("defect,msg", [("link_beyond_own", "another instance"),
+                                         ("negative_link", "outside"),
+                                         ("route_ptr_start", "route_ptr[0]")])
+def test_instances_rejects_bad_instances(batch, defect, msg):
+    from paper_2509_10722_b300 import capi
+    insts = [dict(t) for t in batch[:4]]
+    t = insts[1]
+    if defect == "link_beyond_own":
+        rl = np.array(t["route_links"]).copy()
+        rl[0] = t["m"]  # a link of the next instance once stacked
+        t["route_links"] = rl
+    elif defect == "negative_link":  # in the first instance, where it stays negative
+        t = insts[0]
+        rl = np.array(t["route_links"]).copy()
+        rl[-1] = -5
+        t["route_links"] = rl
+    else:
+        rp = np.array(t["route_ptr"]).copy()
+        rp[0] = 1
+        t["route_ptr"] = rp
+    with pytest.raises(capi.NumError) as ei:
+        capi.Batch(insts, precision=0)
+    assert ei.value.code == capi.NUM_ERR_INVALID and msg in str(ei.value)
