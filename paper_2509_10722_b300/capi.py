@@ -468,10 +468,15 @@ class Batch:
                                          _hptr(stt)))
         return rc, it, stt
 
-    def get(self):
-        """Per-instance lists of x and prices, and an info dict per instance."""
-        x = np.empty(self.n)
-        p = np.empty(self.m)
+    def get(self, out_x=None, out_prices=None):
+        """Per-instance lists of x and prices, and an info dict per instance.  out_x /
+        out_prices (contiguous float64 arrays of the total n / m, e.g. views of pinned
+        memory) receive the stacked results instead of new arrays; the lists are views."""
+        x = np.empty(self.n) if out_x is None else out_x
+        p = np.empty(self.m) if out_prices is None else out_prices
+        for a, k, name in ((x, self.n, "out_x"), (p, self.m, "out_prices")):
+            if a.dtype != np.float64 or a.size != k or not a.flags.c_contiguous:
+                raise ValueError(f"{name} must be a contiguous float64 array of {k} values")
         info = np.zeros((self.count, NUM_INFO_LEN))
         _check(_lib.num_batch_get(self.h, _hptr(x), _hptr(p), _hptr(info)))
         xs = [x[self.so[i]:self.so[i + 1]] for i in range(self.count)]
