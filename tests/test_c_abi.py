@@ -13,10 +13,12 @@ LIBDIR = os.path.join(ROOT, "paper_2509_10722_b300", "lib")
 
 
 @pytest.fixture(scope="module")
-def exe(tmp_path_factory):
+def exe():
     from paper_2509_10722_b300 import build
     build.build()
-    out = str(tmp_path_factory.mktemp("cabi") / "four_stream")
+    outdir = os.path.join(ROOT, "tests", "c", "build")  # git-ignored
+    os.makedirs(outdir, exist_ok=True)
+    out = os.path.join(outdir, "four_stream")
     subprocess.run(["gcc", "-std=c11", "-O2", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"),
                     SRC, "-o", out, "-L", LIBDIR, "-lnum_pmp", f"-Wl,-rpath,{LIBDIR}", "-lm"],
                    check=True)
