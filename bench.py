@@ -24,7 +24,7 @@ import json
 import os
 import subprocess
 import sys
-import tempfile
+import threading
 import time
 
 import numpy as np
@@ -129,21 +129,28 @@ CLOCK_QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.ac
 
 
 class ClockSampler:
+    """nvidia-smi sampling the clocks every 200 ms while it runs; its lines are read from
+    a pipe by a thread, so nothing is written to disk."""
+
     def __init__(self, gpu_index):
         self.idx = gpu_index
         self.proc = None
-        self.path = None
+        self.lines = []
+        self.reader = None
 
     def start(self):
-        fd, self.path = tempfile.mkstemp(suffix=".csv")
-        os.close(fd)
+        self.lines = []
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={CLOCK_QUERY}",
                  "--format=csv,noheader,nounits", "-lms", "200"],
-                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
+            return
+        self.reader = threading.Thread(target=lambda: self.lines.extend(self.proc.stdout),
+                                       daemon=True)
+        self.reader.start()
 
     def stop(self):
         if self.proc is None:
@@ -153,9 +160,8 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
-        text = open(self.path).read()
-        os.unlink(self.path)
-        return parse_clocks(text)
+        self.reader.join(timeout=5)
+        return parse_clocks("".join(self.lines))
 
 
 def parse_clocks(text):
