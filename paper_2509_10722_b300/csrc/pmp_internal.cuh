@@ -103,7 +103,9 @@ struct View {
     double* part_s;             // per-block residual partials of the stream kernel [grid_s]
     double* part_l;             // ... of the link kernel [2 * grid_l]
     int grid_s, grid_l;
-    int link_pairs;             // row link kernel: pairs of gathers in flight per lane (1, 2)
+    int link_pairs;             // row link kernel: 2 (few links per group: one group per link,
+                                // two pairs of gathers in flight) or 1 (many: epilogues spread
+                                // over the lanes, one pair in flight)
     const int4* chunks;         // row kernels: (link, first entry, end entry, first chunk)
     int nchunks;
     const int* perm;            // caller's index of the stream at each position (or NULL)
@@ -246,9 +248,10 @@ template <typename T>
 cudaError_t set_weights(const View<T>& v, const double* w, cudaStream_t st);
 
 // ---- row kernels (rows.cu) ------------------------------------------------------------------
-// Grids of the two row kernels, and the link kernel's pairs of gathers in flight per lane:
-// 2 when each group has few links to sum (a short chain of dependent loads per group is
-// then the limit), else 1; the sums are the same either way.
+// Grids of the two row kernels, and the link kernel's variant: link_pairs = 2 when each
+// group has few links to sum (a short chain of dependent loads per group is then the
+// limit: one group per link, two pairs of gathers in flight), else 1 (epilogues spread
+// over the group's lanes); the sums are the same either way.
 cudaError_t rows_grids(int precision, int n, int m, int nchunks, int* grid_s, int* grid_l,
                        int* link_pairs);
 template <typename T>

@@ -77,7 +77,9 @@ __global__ void __launch_bounds__(kTh) k_stream_rows(View<T> v) {
 }
 // ---- link kernel ---------------------------------------------------------------------------------
 
-template <typename T, int kPairs>
+// kPairs: pairs of gathers in flight per lane; kSpread: the epilogues of a group's links
+// run on all its lanes (many links per group) rather than on its leader (few).
+template <typename T, int kPairs, bool kSpread>
 __global__ void __launch_bounds__(kTh) k_link_rows(View<T> v) {
     __shared__ double red[3 * kWarps];
     __shared__ int last;
@@ -91,31 +93,63 @@ __global__ void __launch_bounds__(kTh) k_link_rows(View<T> v) {
     const int* __restrict__ col_idx = v.col_idx;
     const T* __restrict__ x = v.x;
     Acc<T> r2, s2;
-    // links of up to kLongRow streams: one group each; the bounds of the group's next link
-    // are loaded before the current link is summed, so they are at hand when it is done
     constexpr int kGroups = kTh / kGroup;
-    int l = blockIdx.x * kGroups + (int)(threadIdx.x / kGroup);
-    int p0 = 0, p1 = 0;
-    if (l < m) {
-        p0 = __ldg(row_ptr + l);
-        p1 = __ldg(row_ptr + l + 1);
-    }
-    while (l < m) {
-        const int ln = l + gridDim.x * kGroups;
-        int q0 = 0, q1 = 0;
-        if (ln < m) {
-            q0 = __ldg(row_ptr + ln);
-            q1 = __ldg(row_ptr + ln + 1);
+    if (kSpread) {
+        // links of up to kLongRow streams, many per group: a group takes kGroup consecutive
+        // links at a time and sums them one after the other with all its lanes; lane k then
+        // runs the epilogue of the k-th of them, so that the epilogues use every lane
+        const int sl = g.thread_rank();
+        const long long stride = (long long)gridDim.x * kGroups * kGroup;
+        for (long long base = ((long long)blockIdx.x * kGroups + threadIdx.x / kGroup) * kGroup;
+             base < m; base += stride) {
+            const long long lk = base + sl;  // this lane's link
+            int q0 = 0, q1 = 0;
+            if (lk < m) {
+                q0 = __ldg(row_ptr + lk);
+                q1 = __ldg(row_ptr + lk + 1);
+            }
+            T mine = T(0);
+#pragma unroll 1
+            for (int j = 0; j < kGroup; ++j) {
+                if (base + j >= m) break;  // the same for the whole group
+                const int p0 = g.shfl(q0, j), p1 = g.shfl(q1, j);
+                if (p1 - p0 > kLongRow) continue;  // done by its chunks
+                const T s = group_gather_sum<kGroup, kPairs>(g, col_idx, x, p0, p1, v.n, v.dbg);
+                const T sj = g.shfl(s, 0);
+                if (sl == j) mine = sj;
+            }
+            if (lk < m && q1 - q0 <= kLongRow) {
+                const LinkState<T> st = load_link(v, (int)lk);
+                link_epilogue(v, (int)lk, st, mine, q1 - q0, alpha, rho, inv_rho, r2, s2);
+            }
         }
-        if (p1 - p0 <= kLongRow) {  // longer links are done by their chunks
-            LinkState<T> st;
-            if (leader) st = load_link(v, l);
-            const T s = group_gather_sum<kGroup, kPairs>(g, col_idx, x, p0, p1, v.n, v.dbg);
-            if (leader) link_epilogue(v, l, st, s, p1 - p0, alpha, rho, inv_rho, r2, s2);
+    } else {
+        // links of up to kLongRow streams, few per group: one group per link, its leader
+        // runs the epilogue; the bounds of the group's next link are loaded before the
+        // current link is summed, so they are at hand when it is done
+        int l = blockIdx.x * kGroups + (int)(threadIdx.x / kGroup);
+        int p0 = 0, p1 = 0;
+        if (l < m) {
+            p0 = __ldg(row_ptr + l);
+            p1 = __ldg(row_ptr + l + 1);
         }
-        l = ln;
-        p0 = q0;
-        p1 = q1;
+        while (l < m) {
+            const int ln = l + gridDim.x * kGroups;
+            int q0 = 0, q1 = 0;
+            if (ln < m) {
+                q0 = __ldg(row_ptr + ln);
+                q1 = __ldg(row_ptr + ln + 1);
+            }
+            if (p1 - p0 <= kLongRow) {  // longer links are done by their chunks
+                LinkState<T> st;
+                if (leader) st = load_link(v, l);
+                const T s = group_gather_sum<kGroup, kPairs>(g, col_idx, x, p0, p1, v.n, v.dbg);
+                if (leader) link_epilogue(v, l, st, s, p1 - p0, alpha, rho, inv_rho, r2, s2);
+            }
+            l = ln;
+            p0 = q0;
+            p1 = q1;
+        }
     }
     // chunks of the longer links: one warp each (four gathers in flight per lane), so that
     // a chunk is a short chain of round trips and the chunks balance across warps
@@ -171,14 +205,15 @@ cudaError_t rows_occupancy(int* occ_s, int* occ_l1, int* occ_l2) {
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ_s, k_stream_rows<T, true>,
                                                                   kTh, 0);
     if (e != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ_l1, k_link_rows<T, 1>, kTh, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ_l1, k_link_rows<T, 1, true>, kTh, 0);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ_l2, k_link_rows<T, 2>, kTh, 0);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ_l2, k_link_rows<T, 2, false>, kTh, 0);
 }
 
-// Two pairs in flight paid when each group slot of a resident grid had about 4 links to
-// sum (c5: 1e5 links) and cost when it had about 42 (c2: 1e6 links); the switch sits
-// between the two.
+// With about 4 links to sum per group slot of a resident grid (c5: 1e5 links), one group
+// per link with two pairs of gathers in flight was fastest; with about 42 (c2: 1e6 links)
+// or more (4.2e2 for 1e7 links), spreading the epilogues over the lanes with one pair in
+// flight.  The switch sits between the two.
 constexpr int kFewLinksPerGroup = 16;
 
 }  // namespace
@@ -215,9 +250,9 @@ cudaError_t rows_iteration(const View<T>& v, cudaStream_t st, cudaEvent_t* evs) 
         k_stream_rows<T, false><<<v.grid_s, kTh, 0, st>>>(v);
     if (evs) record_kernel_event(evs[0], st);
     if (v.link_pairs == 2)
-        k_link_rows<T, 2><<<v.grid_l, kTh, 0, st>>>(v);
+        k_link_rows<T, 2, false><<<v.grid_l, kTh, 0, st>>>(v);
     else
-        k_link_rows<T, 1><<<v.grid_l, kTh, 0, st>>>(v);
+        k_link_rows<T, 1, true><<<v.grid_l, kTh, 0, st>>>(v);
     if (evs) record_kernel_event(evs[1], st);
     return cudaGetLastError();
 }
