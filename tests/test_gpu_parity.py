@@ -344,3 +344,29 @@ def test_badly_scaled_instances(decades):
     g64 = run_gpu(inst, 300, "fp64")
     assert rel(g32["x"], ref["x"]) <= 1e-4 and rel(g32["lam"], ref["lam"]) <= 1e-4
     assert rel(g64["x"], ref["x"]) <= 1e-9 and rel(g64["lam"], ref["lam"]) <= 1e-9
+
+
+@pytest.fixture(scope="module")
+def many_links():
+    """About a million links (not a multiple of 8) for 60,000 streams of 1..6 Zipf-chosen
+    links: each link group of a resident grid has many links to sum, so the link kernel
+    spreads the epilogues of 8 consecutive links over a group's lanes; most links carry no
+    stream, and the hottest carry thousands (summed in chunks by whole warps)."""
+    inst = W.random_instance(60_000, 1_000_003, 1, 6, seed=61, link_dist="zipf",
+                             frac_log=0.6, frac_alpha2=0.1, box=(0.0, 20.0))
+    deg = np.bincount(inst["route_links"], minlength=inst["m"])
+    assert deg.max() > 2048 and (deg == 0).mean() > 0.5
+    return inst
+
+
+@pytest.mark.parametrize("precision", ["fp64", "plain"])
+def test_many_links_fp64_match_oracle(many_links, precision):
+    ref = oracle_run(many_links, 150)
+    g = run_gpu(many_links, 150, precision)
+    assert rel(g["x"], ref["x"]) <= 1e-9 and rel(g["lam"], ref["lam"]) <= 1e-9
+
+
+def test_many_links_fp32_match_oracle(many_links):
+    ref = oracle_run(many_links, 150)
+    g = run_gpu(many_links, 150, "fp32", schedule_decisions=ref["decisions"])
+    assert rel(g["x"], ref["x"]) <= 1e-4 and rel(g["lam"], ref["lam"]) <= 1e-4
