@@ -558,7 +558,7 @@ int create_impl(num_problem** out, int64_t n, int64_t m, const int64_t* route_pt
             CK(pmp::fill_long_routes(h->col_ptr, (int)n, d_coff, h->long_routes, st),
                "long routes");
         CK(pmp::rows_grids(fp32 ? 0 : 1, (int)n, (int)m, h->nchunks, &h->grid_s, &h->grid_l,
-                           &h->link_pairs),
+                           &h->link_spread),
            "sizing the row-kernel grids");
     }
     CK(zero_state(h), "zeroing the state");

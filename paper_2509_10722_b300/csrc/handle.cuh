@@ -33,7 +33,7 @@ struct num_problem {
     int *col_ptr = nullptr, *row_idx = nullptr, *row_ptr = nullptr, *col_idx = nullptr;
     int2 *tiles_s = nullptr, *tiles_l = nullptr;
     int ntiles_s = 0, ntiles_l = 0, tile_s = 0, tile_l = 0, grid_s = 0, grid_l = 0;
-    int link_pairs = 1;
+    int link_spread = 0;
     int sched_kind = NUM_SCHEDULE_ROWS;  // fused paths: row kernels or merge-path tiles
     int* perm = nullptr;                 // caller's index of the stream at each position
     uint8_t* ut = nullptr;               // utility types, only if some stream has U = -w / x
@@ -149,7 +149,7 @@ View<T> make_view(const num_problem* h) {
     v.part_l = h->part_l;
     v.grid_s = h->grid_s;
     v.grid_l = h->grid_l;
-    v.link_pairs = h->link_pairs;
+    v.link_spread = h->link_spread;
     v.chunks = h->chunks;
     v.nchunks = h->nchunks;
     v.perm = h->perm;

@@ -103,9 +103,9 @@ struct View {
     double* part_s;             // per-block residual partials of the stream kernel [grid_s]
     double* part_l;             // ... of the link kernel [2 * grid_l]
     int grid_s, grid_l;
-    int link_pairs;             // row link kernel: 2 (few links per group: one group per link,
-                                // two pairs of gathers in flight) or 1 (many: epilogues spread
-                                // over the lanes, one pair in flight)
+    int link_spread;            // row link kernel: 1 (many links per group: the epilogues of a
+                                // group's links spread over its lanes) or 0 (few: one group
+                                // per link, its leader runs the epilogue)
     const int4* chunks;         // row kernels: (link, first entry, end entry, first chunk)
     int nchunks;
     const int* perm;            // caller's index of the stream at each position (or NULL)
@@ -248,12 +248,12 @@ template <typename T>
 cudaError_t set_weights(const View<T>& v, const double* w, cudaStream_t st);
 
 // ---- row kernels (rows.cu) ------------------------------------------------------------------
-// Grids of the two row kernels, and the link kernel's variant: link_pairs = 2 when each
-// group has few links to sum (a short chain of dependent loads per group is then the
-// limit: one group per link, two pairs of gathers in flight), else 1 (epilogues spread
-// over the group's lanes); the sums are the same either way.
+// Grids of the two row kernels, and the link kernel's variant: link_spread = 0 when each
+// group has few links to sum (one group per link, the leader runs the epilogue), else 1
+// (a group sums 8 consecutive links and each lane runs one epilogue); the sums are the
+// same either way.
 cudaError_t rows_grids(int precision, int n, int m, int nchunks, int* grid_s, int* grid_l,
-                       int* link_pairs);
+                       int* link_spread);
 template <typename T>
 cudaError_t rows_iteration(const View<T>& v, cudaStream_t st, cudaEvent_t* evs);
 // Chunk table of the links with more than kLongRow streams: counts[m+1] and offs[m+1] are

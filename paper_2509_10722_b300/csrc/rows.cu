@@ -77,9 +77,9 @@ __global__ void __launch_bounds__(kTh) k_stream_rows(View<T> v) {
 }
 // ---- link kernel ---------------------------------------------------------------------------------
 
-// kPairs: pairs of gathers in flight per lane; kSpread: the epilogues of a group's links
-// run on all its lanes (many links per group) rather than on its leader (few).
-template <typename T, int kPairs, bool kSpread>
+// kSpread: the epilogues of a group's links run on all its lanes (many links per group)
+// rather than on its leader (few).  Two pairs of gathers are in flight per lane.
+template <typename T, bool kSpread>
 __global__ void __launch_bounds__(kTh) k_link_rows(View<T> v) {
     __shared__ double red[3 * kWarps];
     __shared__ int last;
@@ -114,7 +114,7 @@ __global__ void __launch_bounds__(kTh) k_link_rows(View<T> v) {
                 if (base + j >= m) break;  // the same for the whole group
                 const int p0 = g.shfl(q0, j), p1 = g.shfl(q1, j);
                 if (p1 - p0 > kLongRow) continue;  // done by its chunks
-                const T s = group_gather_sum<kGroup, kPairs>(g, col_idx, x, p0, p1, v.n, v.dbg);
+                const T s = group_gather_sum<kGroup, 2>(g, col_idx, x, p0, p1, v.n, v.dbg);
                 const T sj = g.shfl(s, 0);
                 if (sl == j) mine = sj;
             }
@@ -143,7 +143,7 @@ __global__ void __launch_bounds__(kTh) k_link_rows(View<T> v) {
             if (p1 - p0 <= kLongRow) {  // longer links are done by their chunks
                 LinkState<T> st;
                 if (leader) st = load_link(v, l);
-                const T s = group_gather_sum<kGroup, kPairs>(g, col_idx, x, p0, p1, v.n, v.dbg);
+                const T s = group_gather_sum<kGroup, 2>(g, col_idx, x, p0, p1, v.n, v.dbg);
                 if (leader) link_epilogue(v, l, st, s, p1 - p0, alpha, rho, inv_rho, r2, s2);
             }
             l = ln;
@@ -200,45 +200,44 @@ __global__ void __launch_bounds__(kTh) k_link_rows(View<T> v) {
 }
 
 template <typename T>
-cudaError_t rows_occupancy(int* occ_s, int* occ_l1, int* occ_l2) {
+cudaError_t rows_occupancy(int* occ_s, int* occ_spread, int* occ_leader) {
     // the variant with the warp phase uses at least as many registers
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ_s, k_stream_rows<T, true>,
                                                                   kTh, 0);
     if (e != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ_l1, k_link_rows<T, 1, true>, kTh, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ_spread, k_link_rows<T, true>, kTh, 0);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ_l2, k_link_rows<T, 2, false>, kTh, 0);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ_leader, k_link_rows<T, false>, kTh, 0);
 }
 
 // With about 4 links to sum per group slot of a resident grid (c5: 1e5 links), one group
-// per link with two pairs of gathers in flight was fastest; with about 42 (c2: 1e6 links)
-// or more (4.2e2 for 1e7 links), spreading the epilogues over the lanes with one pair in
-// flight.  The switch sits between the two.
+// per link was fastest; with about 42 (c2: 1e6 links) or more (4.2e2 for 1e7 links),
+// spreading the epilogues over the lanes.  The switch sits between the two.
 constexpr int kFewLinksPerGroup = 16;
 
 }  // namespace
 
 cudaError_t rows_grids(int precision, int n, int m, int nchunks, int* grid_s, int* grid_l,
-                       int* link_pairs) {
-    int dev = 0, sms = 0, occ_s = 0, occ_l1 = 0, occ_l2 = 0;
+                       int* link_spread) {
+    int dev = 0, sms = 0, occ_s = 0, occ_spread = 0, occ_leader = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
-    e = precision == 0 ? rows_occupancy<float>(&occ_s, &occ_l1, &occ_l2)
-                       : rows_occupancy<double>(&occ_s, &occ_l1, &occ_l2);
+    e = precision == 0 ? rows_occupancy<float>(&occ_s, &occ_spread, &occ_leader)
+                       : rows_occupancy<double>(&occ_s, &occ_spread, &occ_leader);
     if (e != cudaSuccess) return e;
-    if (occ_s < 1 || occ_l1 < 1 || occ_l2 < 1) return cudaErrorInvalidConfiguration;
+    if (occ_s < 1 || occ_spread < 1 || occ_leader < 1) return cudaErrorInvalidConfiguration;
     const long long need_s = ((long long)n + kTh - 1) / kTh;
     const long long need_l = ((long long)m + nchunks + (kTh / kGroup) - 1) / (kTh / kGroup);
-    const long long full_l1 = (long long)occ_l1 * sms;
-    const int pairs = (long long)m <= (long long)kFewLinksPerGroup * full_l1 * (kTh / kGroup) ? 2 : 1;
-    long long gs = (long long)occ_s * sms, gl = (long long)(pairs == 2 ? occ_l2 : occ_l1) * sms;
+    const long long full_spread = (long long)occ_spread * sms;
+    const int spread = (long long)m > (long long)kFewLinksPerGroup * full_spread * (kTh / kGroup);
+    long long gs = (long long)occ_s * sms, gl = (long long)(spread ? occ_spread : occ_leader) * sms;
     gs = gs < need_s ? gs : need_s;
     gl = gl < need_l ? gl : need_l;
     *grid_s = (int)(gs < kMaxRowsGrid ? gs : kMaxRowsGrid);
     *grid_l = (int)(gl < kMaxRowsGrid ? gl : kMaxRowsGrid);
-    *link_pairs = pairs;
+    *link_spread = spread;
     return cudaSuccess;
 }
 
@@ -249,10 +248,10 @@ cudaError_t rows_iteration(const View<T>& v, cudaStream_t st, cudaEvent_t* evs) 
     else
         k_stream_rows<T, false><<<v.grid_s, kTh, 0, st>>>(v);
     if (evs) record_kernel_event(evs[0], st);
-    if (v.link_pairs == 2)
-        k_link_rows<T, 2, false><<<v.grid_l, kTh, 0, st>>>(v);
+    if (v.link_spread)
+        k_link_rows<T, true><<<v.grid_l, kTh, 0, st>>>(v);
     else
-        k_link_rows<T, 1, true><<<v.grid_l, kTh, 0, st>>>(v);
+        k_link_rows<T, false><<<v.grid_l, kTh, 0, st>>>(v);
     if (evs) record_kernel_event(evs[1], st);
     return cudaGetLastError();
 }
