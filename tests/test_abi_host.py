@@ -163,3 +163,48 @@ def test_batch_host_rejections(capi, so, lo, msg):
                                          ptr(rl), ptr(one), ptr(ut), ptr(one), None, ptr(one),
                                          None, None)
     assert rc == capi.NUM_ERR_INVALID and not h.value
+
+
+def _instance(capi, keep, n=2, m=1, rp0=0, links=None):
+    rp = np.array([rp0] + list(range(1, n + 1)), np.int64)
+    rl = np.zeros(n, np.int32) if links is None else np.array(links, np.int32)
+    arrs = [rp, rl, np.ones(m), np.zeros(n, np.uint8), np.ones(n), np.ones(n)]
+    keep.extend(arrs)
+    p = [ctypes.c_void_p(a.ctypes.data) for a in arrs]
+    return capi.num_instance(n, m, p[0], p[1], p[2], p[3], p[4], None, p[5])
+
+
+@pytest.mark.parametrize("case,msg", [("count", "count"), ("empty_n", "n, m >= 1"),
+                                      ("null", "NULL"), ("rp0", "route_ptr[0]"),
+                                      ("empty_route", "empty route")])
+def test_batch_instances_host_rejections(capi, case, msg):
+    """num_batch_create_instances checks sizes, pointers and route offsets of every
+    instance on the host, before any CUDA call."""
+    keep = []
+    insts = (capi.num_instance * 2)(_instance(capi, keep), _instance(capi, keep))
+    count = 2
+    if case == "count":
+        count = 0
+    elif case == "empty_n":
+        insts[1].n = 0
+    elif case == "null":
+        insts[0].w = None
+    elif case == "rp0":
+        insts[1] = _instance(capi, keep, rp0=1)
+    else:
+        rp = np.array([0, 1, 1], np.int64)  # route_ptr[n] = 1 < n = 2
+        keep.append(rp)
+        insts[1].route_ptr = ctypes.c_void_p(rp.ctypes.data)
+    h = ctypes.c_void_p()
+    rc = capi.library().num_batch_create_instances(ctypes.byref(h), count, insts, None, None)
+    assert rc == capi.NUM_ERR_INVALID and msg in capi.num_last_error() and not h.value
+
+
+def test_batch_binding_checks_array_sizes(capi):
+    """The binding refuses an instance whose arrays do not match its n and m before it
+    calls the library."""
+    from paper_2509_10722_b300 import workloads as W
+    t = W.random_instance(20, 5, 1, 3, seed=1)
+    bad = dict(t, c=np.ones(4))
+    with pytest.raises(ValueError):
+        capi.Batch([t, bad])
