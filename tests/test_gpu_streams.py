@@ -59,3 +59,33 @@ def test_get_device_is_ordered_on_the_handles_stream():
         s.synchronize()
         x_host = p.get()[0]
     assert np.array_equal(out.cpu().numpy(), x_host)
+
+
+def test_separate_handles_from_two_threads():
+    """Two handles driven from two host threads at once (the binding releases the
+    interpreter lock during library calls): each result matches the oracle."""
+    import threading
+    from paper_2509_10722_b300 import capi
+    insts = [W.random_instance(4000, 600, 1, 8, seed=71 + i, frac_log=0.6, box=(0.0, 20.0))
+             for i in range(2)]
+    out = [None, None]
+    errors = []
+
+    def work(i):
+        try:
+            with capi.Problem(insts[i], precision=capi.NUM_FUSED_FP64) as p:
+                for _ in range(4):
+                    p.solve(50, 0.0)
+                out[i] = p.get()[:2]
+        except Exception as exc:  # reported below, on the main thread
+            errors.append(exc)
+
+    threads = [threading.Thread(target=work, args=(i,)) for i in range(2)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    assert not errors, errors
+    for i in range(2):
+        ref = oracle_run(insts[i], 200)
+        assert rel(out[i][0], ref["x"]) <= 1e-10 and rel(out[i][1], ref["lam"]) <= 1e-10
