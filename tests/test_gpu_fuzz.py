@@ -14,6 +14,8 @@ iteration count.
   for the total utility or a random cotangent on x, against the CPU reference gradient.
 - Warm starts: new capacities (some links kept, the others scaled by U[0.2, 1.5]) set
   after k1 iterations, then k2 more, against the oracle switching at the same iteration.
+- Many links: 5e5 to 1.2e6 links for 1e3 to 3e4 streams, where the link kernel spreads
+  the epilogues of a group's links over its lanes.
 
 FP64 results must match to 1e-9 and FP32 to 1e-4 in relative norm.  Prices are marginal
 utilities, of the order of w / x, and an uncongested link's price tends to zero through
@@ -240,4 +242,38 @@ def test_random_capacity_switches_match_oracle(case):
     tol = 1e-4 if precision == 0 else 1e-9
     assert rel(x, ref["x"]) <= tol, (path, rel(x, ref["x"]))
     err = price_err(lam, ref["lam"], inst)
+    assert err <= tol, (path, err)
+
+
+# ---- many links: the link kernel's spread variant ------------------------------------------
+
+@st.composite
+def many_link_cases(draw):
+    """Half a million links or more, where each link group of a resident grid has many
+    links to sum and the link kernel runs the epilogues of 8 consecutive links on a
+    group's lanes; few streams, so most links carry none."""
+    n = draw(st.integers(1_000, 30_000))
+    m = draw(st.integers(500_000, 1_200_000))
+    zipf = draw(st.booleans())
+    inst = W.random_instance(n, m, 1, draw(st.integers(1, 8)), seed=draw(st.integers(0, 2**31 - 1)),
+                             link_dist="zipf" if zipf else "uniform", frac_log=0.7,
+                             frac_alpha2=draw(st.sampled_from([0.0, 0.2])), box=(0.0, 20.0))
+    iters = draw(st.integers(1, 80))
+    path = draw(st.sampled_from(["fp64_rows", "fp32_rows"]))
+    return inst, iters, path
+
+
+@settings(max_examples=10, **FUZZ)
+@given(many_link_cases())
+def test_random_many_link_instances_match_oracle(case):
+    inst, iters, path = case
+    ref = oracle_run(inst, iters)
+    if path == "fp64_rows":
+        g = run_gpu(inst, iters, "fp64", schedule=1)
+        tol = 1e-9
+    else:
+        g = run_gpu(inst, iters, "fp32", schedule=1, schedule_decisions=ref["decisions"])
+        tol = 1e-4
+    assert rel(g["x"], ref["x"]) <= tol, (path, rel(g["x"], ref["x"]))
+    err = price_err(g["lam"], ref["lam"], inst)
     assert err <= tol, (path, err)
