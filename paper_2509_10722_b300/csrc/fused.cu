@@ -107,7 +107,7 @@ struct StreamPolicy {
     __device__ int* arrive() const { return v.arrive_s; }
     __device__ V gather(int l) const { return __ldg(v.pby + checked_index(l, v.m, v.dbg)); }
     // stream j: sum = (A_j, B_j), L = |j|
-    __device__ void epilogue(int j, V sum, int L, T& acc0, T&) const {
+    __device__ void epilogue(int j, V sum, int L, double& acc0, double&) const {
         const T Lf = (T)L;
         const T xo = v.x[j], Zo = v.Z[j], wt = __ldg(v.wt + j);
         const T Zn = alpha * Lf * xo + (T(1) - alpha) * Zo - alpha * sum.x;
@@ -118,7 +118,7 @@ struct StreamPolicy {
         v.Z[j] = Zn;
         v.x[j] = xn;
         const T dx = xn - xo;
-        acc0 += Lf * dx * dx;
+        acc0 += (double)(Lf * dx * dx);
     }
 };
 
@@ -137,7 +137,7 @@ struct LinkPolicy {
     __device__ int* arrive() const { return v.arrive_l; }
     __device__ V gather(int j) const { return __ldg(v.x + checked_index(j, v.n, v.dbg)); }
     // link l: sum = (R x)_l, deg = number of streams on l
-    __device__ void epilogue(int l, V Rxn, int deg, T& acc0, T& acc1) const {
+    __device__ void epilogue(int l, V Rxn, int deg, double& acc0, double& acc1) const {
         const T2 py = v.pby[l];
         const T pbo = py.x, y = py.y;
         const T Rxo = v.Rx[l], pso = v.ps[l], zso = v.zs[l], cl = __ldg(v.c + l);
@@ -154,16 +154,17 @@ struct LinkPolicy {
         v.zs[l] = zsn;
         v.Rx[l] = Rxn;
         v.ps[l] = psn;
-        acc0 += (degf + T(1)) * pbn * pbn;
-        const T dpb = pbn - pbo, dRx = Rxn - Rxo, dd = (psn - pbn) - (pso - pbo);
-        acc1 += degf * dpb * dpb - T(2) * dpb * dRx + dd * dd;
+        const double pbn_d = (double)pbn, pbo_d = (double)pbo, degd = (double)deg;
+        acc0 += (degd + 1.0) * pbn_d * pbn_d;
+        const double dpb = pbn_d - pbo_d, dRx = (double)Rxn - (double)Rxo;
+        const double dd = ((double)psn - pbn_d) - ((double)pso - pbo_d);
+        acc1 += degd * dpb * dpb - 2.0 * dpb * dRx + dd * dd;
     }
 };
 
 // ---- the tile engine -------------------------------------------------------------------------------
 // Processes tiles blockIdx.x, blockIdx.x + gridDim.x, ... and adds the epilogues' residual
-// partials of this thread to dacc0 / dacc1 (FP64; per tile the thread sums its own few
-// terms in T first).
+// partials of this thread to dacc0 / dacc1 (FP64).
 template <typename T, int ITEMS, class P>
 __device__ __forceinline__ void seg_tiles(const P& p, unsigned char* smem, int maxrows,
                                           double& dacc0, double& dacc1) {
@@ -280,7 +281,7 @@ __device__ __forceinline__ void seg_tiles(const P& p, unsigned char* smem, int m
 
         // 4. rows cut by tile boundaries: deposit this tile's part, count arrivals; the last
         //    tile to arrive sums the parts in tile order and runs the epilogue
-        T a0 = T(0), a1 = T(0);
+        double a0 = 0.0, a1 = 0.0;
         if (tid == 0) {
             V* carry = p.carry();
             int* arrive = p.arrive();
@@ -340,8 +341,8 @@ __device__ __forceinline__ void seg_tiles(const P& p, unsigned char* smem, int m
         const int ie = last_ends ? nr : nr - 1;
         for (int i = ib + tid; i < ie; i += kTh)
             p.epilogue(r0 + i, rsum[i], sptr[i + 1] - sptr[i] - 1, a0, a1);
-        dacc0 += (double)a0;
-        dacc1 += (double)a1;
+        dacc0 += a0;
+        dacc1 += a1;
         __syncthreads();
     }
 }

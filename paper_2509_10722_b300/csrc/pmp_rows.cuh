@@ -9,19 +9,10 @@
 
 namespace pmp {
 
-// Per-thread residual partial sum: compensated (Neumaier) in FP32, plain in FP64.
+// Per-thread residual partial sum, in FP64 for both precisions: the FP32 path forms the
+// residual terms of its FP32 iterates in FP64 (see the epilogues) and adds them in FP64.
 template <typename T>
 struct Acc {
-    T s = T(0), c = T(0);
-    __device__ __forceinline__ void add(T v) {
-        const T t = s + v;
-        c += (fabs(s) >= fabs(v)) ? ((s - t) + v) : ((v - t) + s);
-        s = t;
-    }
-    __device__ __forceinline__ double value() const { return (double)s + (double)c; }
-};
-template <>
-struct Acc<double> {
     double s = 0.0;
     __device__ __forceinline__ void add(double v) { s += v; }
     __device__ __forceinline__ double value() const { return s; }
@@ -91,8 +82,9 @@ __device__ __forceinline__ void stream_epilogue(const View<T>& v, int j, typenam
     const T xn = stream_prox<T>(S, L, wt, inv_rho, lo, hi, v.ut && v.ut[j] == 2);
     v.Z[j] = Zn;
     v.x[j] = xn;
+    // |sigma| (x - x_prev)^2, a sum of squares (no cancellation): formed in T, added in FP64
     const T dx = xn - xo;
-    acc.add(L * dx * dx);
+    acc.add((double)(L * dx * dx));
 }
 
 template <typename T>
@@ -130,9 +122,14 @@ __device__ __forceinline__ void link_epilogue(const View<T>& v, int l, const Lin
     v.zs[l] = alpha * (psn - pbn) + (T(1) - alpha) * st.zso;
     v.Rx[l] = Rxn;
     v.ps[l] = psn;
-    const T dpb = pbn - pbo, dRx = Rxn - st.Rxo, dd = (psn - pbn) - (st.pso - pbo);
-    r2.add((degf + T(1)) * pbn * pbn);
-    s2.add(degf * dpb * dpb - T(2) * dpb * dRx + dd * dd);
+    // residual terms in FP64 from the iterates (the same operations as in T when T is
+    // double): the three terms of the dual residual cancel as the iterates settle, so in
+    // the FP32 path they are not rounded to FP32 before they are added
+    const double pbn_d = (double)pbn, pbo_d = (double)pbo, degd = (double)deg;
+    const double dpb = pbn_d - pbo_d, dRx = (double)Rxn - (double)st.Rxo;
+    const double dd = ((double)psn - pbn_d) - ((double)st.pso - pbo_d);
+    r2.add((degd + 1.0) * pbn_d * pbn_d);
+    s2.add(degd * dpb * dpb - 2.0 * dpb * dRx + dd * dd);
 }
 
 // Sum of x over entries [e0, e1) of the link-major index array, by one group of G lanes,
