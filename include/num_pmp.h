@@ -282,10 +282,16 @@ NUM_API int64_t num_kernel_launches(void);
  * until the process exits), so n is limited to 33,554,432; larger n is rejected with
  * NUM_ERR_INVALID and a message.  The first call on each device looks up that array's
  * device address (cudaGetSymbolAddress) with the device current; make that first call
- * before any stream capture.  Work is enqueued on cuda_stream (NULL = the legacy default
- * stream) without synchronizing.  All calls share the array: calls that overlap on the GPU
- * (other streams or host threads) race and give wrong sums; calls ordered on one stream
- * are safe.  Inputs are not validated on the device. */
+ * before any stream capture.  The address is kept for the life of the process: it assumes
+ * one CUDA context per device throughout (after cudaDeviceReset and a new context, this
+ * entry point would launch into the old context's address).  Work is enqueued on
+ * cuda_stream (NULL = the legacy default stream) without synchronizing.  All calls share
+ * the array: calls that overlap on the GPU (other streams or host threads) race and give
+ * wrong sums; calls ordered on one stream are safe.  Inputs are not validated on the
+ * device: a utype other than NUM_LOG (0) or NUM_ALPHA2 (2) counts as NUM_LINEAR here
+ * (num_create rejects such values).  A non-sticky CUDA error left on this host thread by
+ * an earlier runtime call is cleared on entry, so an error reported by this call is its
+ * own. */
 NUM_API int num_objective_noalloc(int64_t n, const double* x, const uint8_t* utype,
                                   const double* w, double* objective, void* cuda_stream);
 

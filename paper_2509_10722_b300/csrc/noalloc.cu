@@ -36,6 +36,7 @@ static __device__ __align__(256) double g_noalloc_partials[kNoAllocMaxBlocks];
 
 // Device address of g_noalloc_partials per device, looked up once (host code may not use
 // the symbol's name as an address: on the host it only stands for the device variable).
+// Kept for the life of the process: one CUDA context per device is assumed throughout.
 std::mutex g_mu;
 void* g_addr[kMaxDevices] = {};
 
@@ -79,6 +80,9 @@ extern "C" int num_objective_noalloc(int64_t n, const double* x, const uint8_t* 
                                  "n exceeds the no-allocation maximum of " +
                                      std::to_string(kNoAllocMaxN) +
                                      " streams (use num_get on a handle instead)");
+    // a non-sticky error left on this thread by an earlier runtime call would otherwise be
+    // reported below as this call's launch failure
+    (void)cudaGetLastError();
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return pmp::report_cuda_error(e, "cudaGetDevice");

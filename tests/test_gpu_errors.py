@@ -13,8 +13,6 @@ def _base():
 
 
 def _mutations():
-    def dup(i):
-        i["route_links"][1] = i["route_links"][0]  # route 0 has >= 2 links? force it below
     yield "duplicate", "twice", lambda i: i["route_links"].__setitem__(
         slice(int(i["route_ptr"][_long(i)]) + 1, int(i["route_ptr"][_long(i)]) + 2),
         i["route_links"][int(i["route_ptr"][_long(i)])])

@@ -3,7 +3,8 @@ memory (allocation locked by a host framework, real-time loops that may not sync
 through cudaMalloc, fixed memory budgets).  It keeps its partial sums in a static device
 array of the library instead of allocating, so this test checks, through the C ABI, that
 two calls in a row give the same number as the objective num_get reports for the same
-rates, and that sizes beyond the array's limit are refused.
+rates and as an FP64 host sum of the utilities, and that sizes beyond the array's limit
+are refused.
 
 This file is collected last on purpose."""
 import numpy as np
@@ -36,6 +37,10 @@ def test_noalloc_objective_matches_num_get(n, m, a2):
     ref = info["objective"]
     assert np.all(np.abs(got - ref) <= 1e-12 * abs(ref)), (got, ref)
     assert got[0] == got[1]
+    # and the FP64 host sum of the same rates, written from Sec. II's definition
+    from oracle import kkt
+    host = kkt.utility(inst, x.cpu().numpy())
+    assert np.all(np.abs(got - host) <= 1e-12 * abs(host)), (got, host)
 
 
 def test_noalloc_rejects_sizes_beyond_its_array():
