@@ -616,8 +616,10 @@ def run_batched(args):
         with capi.Batch(insts, stream=sp, precision=precision, profile=2) as b:
             if mode == "autotune":
                 tune = b.autotune(trial_iters=args.tune_iters)
-            elif mode == "pinned":
+            elif mode in ("pinned", "persistent"):
                 b.set_schedule(*part)
+            if mode == "persistent":
+                b.set_persistent(True)
             rc, it, st = b.solve(args.max_iters, args.eps)
             xs, ps, infos = b.get(out_x=xh, out_prices=ph)
             ms, runs = b.kernel_times()
@@ -661,6 +663,9 @@ def run_batched(args):
     t_f, (it_f, st_f, kms_f, kruns_f, _) = timed_leg(lambda: batch_leg("pinned", chosen), args.steps)
     launches = (capi.num_kernel_launches() - launches0) // max(args.steps, 1)
     clocks = sampler.stop()
+    # the persistent form (one cooperative launch per 50 iterations, a team of blocks per
+    # instance) on the same partition
+    t_q, (it_q, st_q, _, _, _) = timed_leg(lambda: batch_leg("persistent", chosen), args.steps)
     # precision: the same batch in FP64 (default partition, untimed) against the FP32 run
     r32, r64 = {}, {}
     batch_leg("pinned", chosen, 0, r32)  # also gives the per-instance iteration counts
@@ -739,9 +744,11 @@ def run_batched(args):
                          "link_kernel_ms_best": float(st2[:, 3].min()),
                          "link_kernel_ms_worst": float(st2[:, 3].max())},
             "default_partition_ms": t_d, "pinned_tuned_partition_ms": t_f,
+            "persistent_ms": t_q, "persistent_converged": int(np.sum(st_q == 0)),
             "sequential_fp32_ms": t_s, "sequential_plain_fp64_ms": t_p,
             "speedup_vs_sequential_fp32": t_s / t_f, "speedup_vs_sequential_plain_fp64": t_p / t_f,
             "iterations": {"batch": it_f, "batch_default_partition": it_d,
+                           "batch_persistent": it_q,
                            "batch_with_autotune": it_a, "sequential_fp32": int(it_s),
                            "sequential_plain_fp64": int(it_p)},
             "fp32_vs_fp64_batch": {"objective_rel_max": float(obj_rel.max()),

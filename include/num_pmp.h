@@ -51,6 +51,7 @@ extern "C" {
 #define NUM_ERR_CUDA (-3)    /* a CUDA runtime call failed; num_last_error() names it */
 #define NUM_ERR_NUMERIC (-4) /* a residual became non-finite; iteration stopped */
 #define NUM_ERR_STATE (-5)   /* call not valid for this handle's state */
+#define NUM_ERR_TIMEOUT (-6) /* persistent batch: a bounded wait between blocks ran out */
 
 /* ---- utility types (Sec. III-B) ------------------------------------------------------------ */
 #define NUM_LOG 0    /* U(x) = w log x, the log-utility stream */
@@ -417,6 +418,29 @@ NUM_API int num_batch_get(const num_batch* b, double* x, double* prices, double*
 /* As num_get_kernel_times, for the batch's two kernels (profile = 1 or 2). */
 NUM_API int num_batch_get_kernel_times(const num_batch* b, double* ms, int64_t* launches,
                                        int32_t max_kernels, int32_t* nkernels);
+
+/* Persistent form of num_batch_solve (enable = 1; 0 returns to the default form of two
+ * launches per iteration replayed from a CUDA graph).  Each num_batch_solve then runs the
+ * instances with cooperative launches of one persistent kernel, check_every iterations per
+ * launch.  Before each launch the instances still running are planned onto the GPU's
+ * resident blocks: with the smallest load bound per block that fits, an instance of more
+ * work owns a team of blocks and smaller ones are packed several to a block (run in turn).
+ * A team steps through its instance's iterations on its own, its blocks meeting at two
+ * barriers per iteration (after the stream pass, and at the end of the iteration, where
+ * the team's first block runs the stopping test and rho rule of Sec. III-F / III-G).  The iterates equal those of the
+ * default form for the same rho decisions (the arithmetic of a stream or a link is the
+ * same); the FP64 residual sums are grouped differently.  Every wait is bounded: a block
+ * gives up after wait_polls polls of its barrier (wait_polls = 0: about 2^22 polls, roughly
+ * a second), records it, and returns, as do in turn the other blocks of its team;
+ * num_batch_solve then returns NUM_ERR_TIMEOUT, the iterates are undefined, and every
+ * further solve returns NUM_ERR_STATE until num_batch_reset.  Per-kernel times (profile)
+ * are not recorded in this form.  The
+ * paper solves one instance at a time; batches are a service of this library. */
+NUM_API int num_batch_set_persistent(num_batch* b, int32_t enable, int64_t wait_polls);
+
+/* Every instance back to the zero state of creation (rho0, no iterations, empty residual
+ * history); clears the broken state left by a NUM_ERR_TIMEOUT.  Synchronizes the stream. */
+NUM_API int num_batch_reset(num_batch* b);
 
 /* Free every resource of the batch.  NULL is ignored. */
 NUM_API void num_batch_destroy(num_batch* b);

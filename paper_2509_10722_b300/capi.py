@@ -24,6 +24,7 @@ NUM_ERR_OOM = -2
 NUM_ERR_CUDA = -3
 NUM_ERR_NUMERIC = -4
 NUM_ERR_STATE = -5
+NUM_ERR_TIMEOUT = -6
 
 NUM_LOG = 0
 NUM_LINEAR = 1
@@ -123,6 +124,8 @@ def _load():
         "num_batch_set_schedule": (ctypes.c_int, [P, ctypes.POINTER(BatchSchedule)]),
         "num_batch_autotune": (ctypes.c_int, [P, i32, ctypes.POINTER(BatchSchedule), P, i32,
                                               ctypes.POINTER(i32)]),
+        "num_batch_set_persistent": (ctypes.c_int, [P, i32, i64]),
+        "num_batch_reset": (ctypes.c_int, [P]),
         "num_batch_destroy": (None, [P]),
         "num_destroy": (None, [P]),
         "num_strerror": (ctypes.c_char_p, [ctypes.c_int]),
@@ -146,7 +149,8 @@ EXPORTED = ("num_default_params", "num_create", "num_create_device", "num_set_rh
             "num_batch_create", "num_batch_create_instances", "num_batch_set_rho_schedules",
             "num_batch_solve",
             "num_batch_get", "num_batch_get_kernel_times", "num_batch_get_schedule",
-            "num_batch_set_schedule", "num_batch_autotune", "num_batch_destroy")
+            "num_batch_set_schedule", "num_batch_autotune", "num_batch_set_persistent",
+            "num_batch_reset", "num_batch_destroy")
 
 
 def library():
@@ -510,6 +514,14 @@ class Batch:
         _check(_lib.num_batch_autotune(self.h, int(trial_iters), ctypes.byref(out), _hptr(trials),
                                        64, ctypes.byref(nt)))
         return out.as_tuple(), trials[:min(nt.value, 64)]
+
+    def set_persistent(self, enable=True, wait_polls=0):
+        """Persistent form of solve (one cooperative launch per check_every iterations,
+        a team of blocks per instance); wait_polls bounds each wait between blocks."""
+        _check(_lib.num_batch_set_persistent(self.h, int(bool(enable)), int(wait_polls)))
+
+    def reset(self):
+        _check(_lib.num_batch_reset(self.h))
 
     def close(self):
         if getattr(self, "h", None) is not None:

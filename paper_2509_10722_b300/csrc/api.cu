@@ -986,6 +986,7 @@ const char* num_strerror(int code) {
         case NUM_ERR_CUDA: return "CUDA runtime error";
         case NUM_ERR_NUMERIC: return "non-finite residual";
         case NUM_ERR_STATE: return "call not valid in this state";
+        case NUM_ERR_TIMEOUT: return "a bounded wait between blocks ran out";
         default: return "unknown status code";
     }
 }

@@ -50,6 +50,18 @@ struct num_batch {
     int* lr_inst = nullptr;            // [nlong] instance of each long-route stream
     int* lroff = nullptr;              // [count + 1] long-route range of each instance
     double* part_r = nullptr;          // [nlong] residual terms of long-route streams
+    // persistent form (num_batch_set_persistent)
+    bool persistent = false;
+    long long wait_polls = 0;          // polls of a team wait before it gives up
+    bool broken = false;               // a wait ran out: the iterates are undefined until reset
+    int* soff_d = nullptr;             // [count + 1] stream / link ranges of the instances
+    int* loff_d = nullptr;
+    unsigned int* bar = nullptr;       // [2 count] team barriers
+    int4* teams = nullptr;             // [cap_teams + count] tasks (instance, rank, size, first)
+    int2* btasks = nullptr;            // [cap_teams] each block's range of tasks
+    double* part_t = nullptr;          // [3 cap_teams] per-block residual partials
+    int cap_teams = 0;
+    int grid_p = 0;                    // blocks of the current team plan
 };
 
 namespace {
@@ -103,6 +115,14 @@ pmp::BatchView<T> make_batch_view(const num_batch* b) {
     v.lr_inst = b->lr_inst;
     v.lroff = b->lroff;
     v.part_r = b->part_r;
+    v.soff = b->soff_d;
+    v.loff = b->loff_d;
+    v.teams = b->teams;
+    v.btasks = b->btasks;
+    v.part_t = b->part_t;
+    v.bar = b->bar;
+    v.wait_polls = b->wait_polls;
+    v.iters = h->prm.check_every;
     return v;
 }
 
@@ -315,6 +335,166 @@ int batch_time_schedule(num_batch* b, const num_batch_schedule& cfg, int iters, 
     return NUM_OK;
 }
 
+// Persistent form: the plan of one launch.  Each running instance's work per iteration is
+// estimated as two gathers per route entry plus its streams and links.  With a load bound
+// B per block, an instance of more work than B gets a team of ceil(w / B) blocks (at most
+// one per 256 streams or per 256 lanes of links: more would have nothing to do), and the
+// others are packed several to a block, first-fit by decreasing work, each run in turn by
+// its block.  B is the smallest bound (bisection) whose plan fits in `cap` resident
+// blocks.  Fills tasks (instance, rank, team size, first block) and the per-block task
+// ranges; returns the number of blocks (0: nothing runs).
+constexpr int kPersistTh = 256;            // threads per block of the persistent kernel
+constexpr long long kDefaultWaitPolls = 1LL << 22;  // about a second of polling per wait
+
+int plan_teams(const num_batch* b, const std::vector<char>& live, int cap,
+               std::vector<int4>& tasks, std::vector<int2>& btasks) {
+    std::vector<int> ids;
+    std::vector<double> w(b->count, 0.0);
+    std::vector<int64_t> useful(b->count, 1);
+    double W = 0.0;
+    for (int i = 0; i < b->count; ++i) {
+        if (!live[i]) continue;
+        const int64_t n_i = b->soff[i + 1] - b->soff[i], m_i = b->loff[i + 1] - b->loff[i];
+        const double nnz_i = b->J[i] - (double)m_i;
+        w[i] = 2.0 * nnz_i + (double)n_i + (double)m_i;
+        useful[i] = std::max<int64_t>(
+            1, std::max<int64_t>((n_i + kPersistTh - 1) / kPersistTh,
+                                 (m_i * b->cfg.link_lanes + kPersistTh - 1) / kPersistTh));
+        W += w[i];
+        ids.push_back(i);
+    }
+    tasks.clear();
+    btasks.clear();
+    if (ids.empty()) return 0;
+    std::sort(ids.begin(), ids.end(), [&](int a, int c) { return w[a] > w[c] || (w[a] == w[c] && a < c); });
+    // blocks of the plan under bound B; with `build`, the plan itself
+    auto plan = [&](double B, bool build) -> long long {
+        long long blocks = 0;
+        std::vector<double> load;        // packed blocks: work so far
+        std::vector<std::vector<int>> members;
+        for (int i : ids) {
+            if (w[i] > B) {
+                const int64_t g = std::min<int64_t>((int64_t)std::ceil(w[i] / B), useful[i]);
+                if (build) {
+                    const int first = (int)btasks.size();
+                    for (int64_t r = 0; r < g; ++r) {
+                        btasks.push_back(make_int2((int)tasks.size(), 1));
+                        tasks.push_back(make_int4(i, (int)r, (int)g, first));
+                    }
+                }
+                blocks += g;
+            } else {
+                size_t k = 0;
+                while (k < load.size() && load[k] + w[i] > B) ++k;  // first fit
+                if (k == load.size()) {
+                    load.push_back(0.0);
+                    members.emplace_back();
+                }
+                load[k] += w[i];
+                members[k].push_back(i);
+            }
+        }
+        blocks += (long long)load.size();
+        if (build)
+            for (auto& mem : members) {
+                const int blk = (int)btasks.size();
+                btasks.push_back(make_int2((int)tasks.size(), (int)mem.size()));
+                for (int i : mem) tasks.push_back(make_int4(i, 0, 1, blk));
+            }
+        return blocks;
+    };
+    // at B = W everything fits in one block; at B = W / cap no plan uses fewer blocks
+    double lo = std::max(W / cap, 1.0), hi = std::max(W, lo);
+    if (plan(lo, false) > cap) {
+        for (int it = 0; it < 60 && hi > lo * (1.0 + 1e-3); ++it) {
+            const double mid = 0.5 * (lo + hi);
+            if (plan(mid, false) <= cap)
+                hi = mid;
+            else
+                lo = mid;
+        }
+    } else {
+        hi = lo;
+    }
+    plan(hi, true);
+    return (int)btasks.size();
+}
+
+// Runs the armed instances of the batch with cooperative launches of the persistent
+// kernel, check_every iterations per launch, re-planning the teams over the instances
+// still running before each launch, until none runs.  NUM_ERR_TIMEOUT if a team wait ran
+// out (the batch is then marked broken).
+int batch_solve_persistent(num_batch* b, int64_t max_iters) {
+    num_problem* h = b->p;
+    cudaStream_t st = h->stream;
+    int cap = 0;
+    cudaError_t e = pmp::batch_persistent_capacity(h->prec == NUM_FUSED_FP32 ? 0 : 1,
+                                                   b->cfg.link_lanes, h->nlong > 0, &cap);
+    if (e != cudaSuccess) return cuda_fail(e, "occupancy of the persistent kernel");
+    if (cap < 1) return fail(NUM_ERR_STATE, "the persistent kernel cannot be resident");
+    // tasks: at most one per block of a team, or one per instance
+    const int ntask_cap = cap + b->count;
+    if (cap > b->cap_teams) {
+        if (b->teams) dev_free(h, b->teams);
+        if (b->btasks) dev_free(h, b->btasks);
+        if (b->part_t) dev_free(h, b->part_t);
+        b->teams = (int4*)dev_alloc(h, sizeof(int4) * (size_t)ntask_cap);
+        b->btasks = (int2*)dev_alloc(h, sizeof(int2) * (size_t)cap);
+        b->part_t = (double*)dev_alloc(h, sizeof(double) * 3 * (size_t)cap);
+        b->cap_teams = b->teams && b->btasks && b->part_t ? cap : 0;
+        if (!b->cap_teams) return fail(NUM_ERR_OOM, "device allocation failed");
+    }
+    const int K = h->prm.check_every;
+    const long long max_launches = (max_iters + K - 1) / K + 1;
+    std::vector<char> live(b->count), planned;
+    std::vector<int4> teams;
+    std::vector<int2> btasks;
+    for (long long it = 0;; ++it) {
+        if (it >= max_launches) return fail(NUM_ERR_STATE, "the iteration limit was not honoured");
+        e = cudaMemcpyAsync(b->ctls_host, b->ctls, sizeof(pmp::Ctl) * b->count,
+                            cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_fail(e, "reading the control blocks");
+        for (int i = 0; i < b->count; ++i) live[i] = b->ctls_host[i].stop == pmp::RUNNING;
+        if (live != planned) {  // instances stopped since the last plan (or none yet)
+            b->grid_p = plan_teams(b, live, cap, teams, btasks);
+            if (b->grid_p == 0) break;
+            if (b->grid_p > cap || (int)teams.size() > ntask_cap)
+                return fail(NUM_ERR_STATE, "the team plan does not fit");
+            e = cudaMemcpyAsync(b->teams, teams.data(), sizeof(int4) * teams.size(),
+                                cudaMemcpyHostToDevice, st);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(b->btasks, btasks.data(), sizeof(int2) * btasks.size(),
+                                    cudaMemcpyHostToDevice, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // the vectors are reused
+            if (e != cudaSuccess) return cuda_fail(e, "copying the team plan");
+            planned = live;
+        }
+        e = cudaMemsetAsync(b->bar, 0, sizeof(unsigned int) * 2 * (size_t)b->count, st);
+        if (e == cudaSuccess)
+            e = cudaMemsetAsync(&b->glob->timeout, 0, 2 * sizeof(int), st);
+        if (e != cudaSuccess) return cuda_fail(e, "arming the team barriers");
+        TraceRange launch("num_batch_solve: persistent launch of check_every iterations");
+        e = h->prec == NUM_FUSED_FP32
+                ? pmp::batch_persistent_launch<float>(make_batch_view<float>(b), b->grid_p, st)
+                : pmp::batch_persistent_launch<double>(make_batch_view<double>(b), b->grid_p, st);
+        if (e != cudaSuccess) return cuda_fail(e, "cooperative launch of the persistent kernel");
+        e = cudaMemcpyAsync(b->glob_host, b->glob, sizeof(pmp::BatchGlobal),
+                            cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_fail(e, "persistent iterations");
+        if (b->glob_host->timeout) {
+            b->broken = true;
+            return fail(NUM_ERR_TIMEOUT,
+                        "a wait between the blocks of an instance's team ran out (block " +
+                            std::to_string(b->glob_host->timeout_block) +
+                            "); the iterates are undefined until num_batch_reset");
+        }
+        if (b->glob_host->running == 0) break;
+    }
+    return NUM_OK;
+}
+
 // The batch over a stacked problem (host or device arrays, as create_impl takes them);
 // inst_nnz[count] (host) holds each instance's route entries.  The offsets are checked.
 int batch_create_impl(num_batch** out, int32_t count, const int64_t* stream_off,
@@ -378,8 +558,12 @@ int batch_create_impl(num_batch** out, int32_t count, const int64_t* stream_off,
     b->arrive = (unsigned int*)dev_alloc(h, sizeof(unsigned int) * (size_t)count);
     b->hist = (double*)dev_alloc(h, sizeof(double) * 3 * (size_t)H * count);
     b->eps_scale = (double*)dev_alloc(h, sizeof(double) * count);
+    b->soff_d = (int*)dev_alloc(h, sizeof(int) * (count + 1));
+    b->loff_d = (int*)dev_alloc(h, sizeof(int) * (count + 1));
+    b->bar = (unsigned int*)dev_alloc(h, sizeof(unsigned int) * 2 * (size_t)count);
     if (!b->ctls || !b->glob || !b->sitems || !b->litems || !b->sitem_off || !b->litem_off ||
-        !b->part_s || !b->part_l || !b->part_e || !b->hist || !b->eps_scale || !b->arrive) {
+        !b->part_s || !b->part_l || !b->part_e || !b->hist || !b->eps_scale || !b->arrive ||
+        !b->soff_d || !b->loff_d || !b->bar) {
         batch_destroy(b);
         return fail(NUM_ERR_OOM, "device allocation failed");
     }
@@ -400,6 +584,19 @@ int batch_create_impl(num_batch** out, int32_t count, const int64_t* stream_off,
     BK(cudaMemcpyAsync(b->eps_scale, scale.data(), sizeof(double) * count, cudaMemcpyHostToDevice,
                        st), "copy scales");
     BK(cudaMemsetAsync(b->hist, 0, sizeof(double) * 3 * (size_t)H * count, st), "memset");
+    {
+        std::vector<int> so32(count + 1), lo32(count + 1);
+        for (int i = 0; i <= count; ++i) {
+            so32[i] = (int)stream_off[i];
+            lo32[i] = (int)link_off[i];
+        }
+        BK(cudaMemcpyAsync(b->soff_d, so32.data(), sizeof(int) * (count + 1),
+                           cudaMemcpyHostToDevice, st), "copy ranges");
+        BK(cudaMemcpyAsync(b->loff_d, lo32.data(), sizeof(int) * (count + 1),
+                           cudaMemcpyHostToDevice, st), "copy ranges");
+        BK(cudaMemsetAsync(b->bar, 0, sizeof(unsigned int) * 2 * (size_t)count, st), "memset");
+        BK(cudaStreamSynchronize(st), "copy ranges");  // the host vectors go out of scope
+    }
     rc = batch_chunk_tables(b);
     if (rc == NUM_OK) rc = batch_long_route_tables(b);
     if (rc != NUM_OK) {
@@ -603,6 +800,8 @@ int num_batch_solve(num_batch* b, int64_t max_iters, double eps_abs, int64_t* it
     if (!b) return fail(NUM_ERR_INVALID, "batch is NULL");
     if (max_iters < 0) return fail(NUM_ERR_INVALID, "max_iters must be >= 0");
     if (std::isnan(eps_abs)) return fail(NUM_ERR_INVALID, "eps_abs is NaN");
+    if (b->broken)
+        return fail(NUM_ERR_STATE, "a persistent solve timed out: call num_batch_reset first");
     num_problem* h = b->p;
     cudaStream_t st = h->stream;
     cudaError_t e = order_after_legacy(h);
@@ -617,7 +816,10 @@ int num_batch_solve(num_batch* b, int64_t max_iters, double eps_abs, int64_t* it
     e = pmp::batch_arm(b->ctls, b->glob, b->count, max_iters, eps, b->eps_scale, st);
     if (e != cudaSuccess) return cuda_fail(e, "arming the instances");
     const int K = h->prm.check_every;
-    if (max_iters > 0) {
+    if (max_iters > 0 && b->persistent) {
+        const int prc = batch_solve_persistent(b, max_iters);
+        if (prc != NUM_OK) return prc;
+    } else if (max_iters > 0) {
         if (h->prm.use_graph && !b->graph_exec) {
             e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
             if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
@@ -829,6 +1031,48 @@ int num_batch_autotune(num_batch* b, int32_t trial_iters, num_batch_schedule* ch
     b->kernel_runs[0] = b->kernel_runs[1] = 0;
     if (chosen) *chosen = best;
     if (ntrials) *ntrials = t;
+    return NUM_OK;
+}
+
+int num_batch_set_persistent(num_batch* b, int32_t enable, int64_t wait_polls) {
+    g_last_error.clear();
+    if (!b) return fail(NUM_ERR_INVALID, "batch is NULL");
+    if (enable != 0 && enable != 1) return fail(NUM_ERR_INVALID, "enable must be 0 or 1");
+    if (wait_polls < 0) return fail(NUM_ERR_INVALID, "wait_polls must be >= 0");
+    num_problem* h = b->p;
+    if (enable) {
+        int cap = 0;
+        cudaError_t e = pmp::batch_persistent_capacity(h->prec == NUM_FUSED_FP32 ? 0 : 1,
+                                                       b->cfg.link_lanes, h->nlong > 0, &cap);
+        if (e != cudaSuccess) return cuda_fail(e, "occupancy of the persistent kernel");
+        if (cap < 1) return fail(NUM_ERR_STATE, "the persistent kernel cannot be resident");
+    }
+    b->persistent = enable != 0;
+    b->wait_polls = wait_polls > 0 ? wait_polls : kDefaultWaitPolls;
+    return NUM_OK;
+}
+
+int num_batch_reset(num_batch* b) {
+    TraceRange trace("num_batch_reset");
+    g_last_error.clear();
+    if (!b) return fail(NUM_ERR_INVALID, "batch is NULL");
+    num_problem* h = b->p;
+    cudaError_t e = order_after_legacy(h);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e == cudaSuccess) e = zero_state(h);
+    if (e != cudaSuccess) return cuda_fail(e, "zeroing the state");
+    int rc = batch_reset_all(b);
+    if (rc != NUM_OK) return rc;
+    e = cudaMemsetAsync(b->hist, 0,
+                        sizeof(double) * 3 * (size_t)(h->prm.history > 0 ? h->prm.history : 1) *
+                            b->count, h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(b->bar, 0, sizeof(unsigned int) * 2 * (size_t)b->count, h->stream);
+    if (e == cudaSuccess && h->nchunks > 0)
+        e = cudaMemsetAsync(h->arrive_l, 0, sizeof(int) * (size_t)h->nchunks, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "resetting the batch");
+    b->broken = false;
     return NUM_OK;
 }
 

@@ -154,11 +154,9 @@ struct LinkPolicy {
         v.zs[l] = zsn;
         v.Rx[l] = Rxn;
         v.ps[l] = psn;
-        const double pbn_d = (double)pbn, pbo_d = (double)pbo, degd = (double)deg;
-        acc0 += (degd + 1.0) * pbn_d * pbn_d;
-        const double dpb = pbn_d - pbo_d, dRx = (double)Rxn - (double)Rxo;
-        const double dd = ((double)psn - pbn_d) - ((double)pso - pbo_d);
-        acc1 += degd * dpb * dpb - 2.0 * dpb * dRx + dd * dd;
+        acc0 += (double)((degf + T(1)) * pbn * pbn);
+        const T dpb = pbn - pbo, dRx = Rxn - Rxo, dd = (psn - pbn) - (pso - pbo);
+        acc1 += (double)(degf * dpb * dpb - T(2) * dpb * dRx + dd * dd);
     }
 };
 

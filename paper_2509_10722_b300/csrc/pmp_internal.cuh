@@ -149,6 +149,8 @@ constexpr int kFusedKernelsPerIter = 2;
 struct BatchGlobal {
     unsigned int ticket;  // last-block-done counter of the export kernel
     int running;          // number of instances still running
+    int timeout;          // persistent kernel: 1 once a bounded wait of some block ran out
+    int timeout_block;    // the block whose wait ran out first
 };
 
 // Work items are (instance, first row, end row, 0); item ranges of instance i are
@@ -185,6 +187,15 @@ struct BatchView {
     const int* lr_inst;    // [v.nlong] instance of each
     const int* lroff;      // [count + 1] range of each instance in the list
     double* part_r;        // [v.nlong] residual term of each
+    // persistent form (batch_persistent.cu): each instance has a team of blocks
+    const int* soff;       // [count + 1] stream range of each instance
+    const int* loff;       // [count + 1] link range of each instance
+    const int4* teams;     // [tasks] (instance, rank in its team, team size, team's first block)
+    const int2* btasks;    // [grid] each block's range of tasks (first, count)
+    double* part_t;        // [3 grid] per-block residual partials: s2 of streams, r2, s2 of links
+    unsigned int* bar;     // [2 count] per-instance team barrier: arrivals, generation
+    long long wait_polls;  // polls of a barrier wait before it gives up
+    int iters;             // iterations per launch
 };
 
 // Profiling event after a kernel: an external event node while the stream is being
@@ -200,6 +211,11 @@ inline cudaError_t record_kernel_event(cudaEvent_t ev, cudaStream_t st) {
 
 cudaError_t batch_grids(int precision, int lanes, int nsitems, int nlitems, int nchunks,
                         int* grid_s, int* grid_l, int* grid_e);
+// Persistent form: the most blocks of the persistent kernel that can be resident at once
+// (the bound of a cooperative launch), and one cooperative launch of it.
+cudaError_t batch_persistent_capacity(int precision, int lanes, bool split, int* blocks);
+template <typename T>
+cudaError_t batch_persistent_launch(const BatchView<T>& b, int grid, cudaStream_t st);
 cudaError_t check_blocks(int count, const int64_t* stream_off, const int64_t* link_off,
                          long long n, const int64_t* route_ptr, const int* route_links, int* err,
                          cudaStream_t st);

@@ -15,8 +15,8 @@
 //     runs the epilogue (no waiting, deterministic);
 //   the last block of the link kernel finishes the iteration (FP64 residual sums, stopping
 //   test, rho), as in the tile engine.
-// Residual terms are formed and summed in FP64 (per thread, per block, over the grid) in
-// both precisions.
+// Residual terms are summed in FP64 (per thread, per block, over the grid) in both
+// precisions.
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 

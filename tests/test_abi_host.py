@@ -24,7 +24,7 @@ def _declared():
 
 def test_every_declared_symbol_is_exported(capi):
     names = _declared()
-    assert len(names) == 33
+    assert len(names) == 35
     lib = ctypes.CDLL(capi.library_path())
     for name in names:
         assert hasattr(lib, name), name
@@ -146,6 +146,10 @@ def test_null_handle_calls(capi):
     with pytest.raises(capi.NumError):
         capi.num_reset(None)
     capi.num_destroy(None)
+    lib = capi.library()
+    assert lib.num_batch_set_persistent(None, 1, 0) == capi.NUM_ERR_INVALID
+    assert lib.num_batch_reset(None) == capi.NUM_ERR_INVALID
+    assert "wait between blocks" in capi.num_strerror(capi.NUM_ERR_TIMEOUT)
 
 
 @pytest.mark.parametrize("so,lo,msg", [([0], [0], "count"), ([1, 2], [0, 1], "must be 0"),
