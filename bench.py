@@ -953,12 +953,68 @@ def run_adjoint(args):
             e1.record(stream)
             e1.synchronize()
             t_fwd = e0.elapsed_time(e1)
+            # the split entries (what the torch Function calls): the forward that keeps its
+            # checkpoints, then the backward sweep from them (device arrays)
+            cgd = torch.empty(p.m, dtype=torch.float64, device="cuda")
+            wgd = torch.empty(p.n, dtype=torch.float64, device="cuda")
+            e0.record(stream)
+            p.adjoint_forward(iters, kc)
+            e1.record(stream)
+            e1.synchronize()
+            t_kf = e0.elapsed_time(e1)
+            e0.record(stream)
+            p.adjoint_backward(ubar=1.0, c_grad=cgd, w_grad=wgd)
+            e1.record(stream)
+            e1.synchronize()
+            t_kb = e0.elapsed_time(e1)
+            split_equal = bool(np.array_equal(cgd.cpu().numpy(), cg) and
+                               np.array_equal(wgd.cpu().numpy(), wg))
+            # the sweep alone: one kept segment (checkpoint_every = 0), so the backward
+            # recomputes nothing; against the random-read ceiling of its two gather passes
+            # ((Abar, Bbar) pairs from the n-vector, Rx_bar from the m-vector)
+            p.adjoint_forward(iters, 0)
+            e0.record(stream)
+            p.adjoint_backward(ubar=1.0, c_grad=cgd, w_grad=wgd)
+            e1.record(stream)
+            e1.synchronize()
+            t_sweep = e0.elapsed_time(e1)
+            nnz = int(inst["route_ptr"][-1])
+            # one 32-byte sector per read whatever the element size; the probe reads 4 or
+            # 8 bytes (an FP64 pair is 16: measured as 8-byte reads of the same vector)
+            r_pair = capi.num_measure_gather_rate(nnz, p.n, 8, 3)
+            r_one = capi.num_measure_gather_rate(nnz, p.m, 4 if prec == 0 else 8, 3)
+            sweep_bound_ms = iters * (nnz / r_pair + nnz / r_one) * 1e3
+            # the torch path: total_utility forward and backward (after one untimed call:
+            # the first autograd call of a process sets up torch's engine)
+            from paper_2509_10722_b300 import autograd
+            ct = torch.tensor(inst["c"], device="cuda", requires_grad=True)
+            wt = torch.tensor(inst["w"], device="cuda", requires_grad=True)
+            with torch.cuda.stream(stream):
+                autograd.total_utility(p, ct, wt, iters, kc).backward()
+                ct.grad = None
+                wt.grad = None
+            with torch.cuda.stream(stream):
+                e0.record(stream)
+                Jt = autograd.total_utility(p, ct, wt, iters, kc)
+                Jt.backward()
+                e1.record(stream)
+            e1.synchronize()
+            t_torch = e0.elapsed_time(e1)
+            torch_equal = bool(np.array_equal(ct.grad.cpu().numpy(), cg) and
+                               np.array_equal(wt.grad.cpu().numpy(), wg))
+            p.adjoint_release()
         grads[name] = (cg, wg)
         out[name] = {"adjoint_ms": t_adj, "forward_ms": t_fwd, "ratio": t_adj / t_fwd,
                      "objective": J, "one_segment_ms": t_one,
                      "one_segment_ratio": t_one / t_fwd,
                      "one_segment_equal": bool(np.array_equal(cg, cg1) and
-                                               np.array_equal(wg, wg1))}
+                                               np.array_equal(wg, wg1)),
+                     "kept_forward_ms": t_kf, "backward_ms": t_kb,
+                     "backward_ratio": t_kb / t_fwd, "split_equal": split_equal,
+                     "sweep_ms": t_sweep, "sweep_bound_ms": sweep_bound_ms,
+                     "sweep_frac_of_gather_ceiling": sweep_bound_ms / t_sweep,
+                     "torch_forward_backward_ms": t_torch,
+                     "torch_ratio": t_torch / t_fwd, "torch_equal": torch_equal}
     meas.stop()
     rel = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))
     line = {"metric": "adjoint of 500 unrolled PMP iterations (dJ/dc, dJ/dw), c5",

@@ -230,6 +230,13 @@ NUM_API int num_set_state(num_problem* h, const double* x, const double* Z, cons
  * types and the iterate are kept. */
 NUM_API int num_set_weights(num_problem* h, const double* w);
 
+/* num_set_capacity and num_set_weights with DEVICE arrays (double[m], double[n] in the
+ * caller's order), read on the handle's stream after the caller's prior work on the legacy
+ * default stream; the values are checked on the device (NUM_ERR_INVALID, nothing changed,
+ * if one is not finite and > 0).  Synchronizes the handle's stream. */
+NUM_API int num_set_capacity_device(num_problem* h, const double* c);
+NUM_API int num_set_weights_device(num_problem* h, const double* w);
+
 /* Reverse-mode derivative of `iters` PMP iterations run from the zero state (the map from
  * (c, w) to the rates x after exactly `iters` iterations, each iteration's rho fixed at the
  * value this forward run takes): for the cotangent xbar (HOST double[n], caller order, or
@@ -249,6 +256,32 @@ NUM_API int num_set_weights(num_problem* h, const double* w);
 NUM_API int num_adjoint(num_problem* h, int64_t iters, int32_t checkpoint_every,
                         const double* xbar, int32_t objective, double* c_grad, double* w_grad,
                         double* objective_out);
+
+/* The two halves of num_adjoint, for callers that run the forward map once and
+ * differentiate it later (an autograd framework's forward and backward).
+ * num_adjoint_forward runs `iters` iterations from the zero state exactly as num_adjoint
+ * does (checkpoints every checkpoint_every iterations, the last segment recorded on the
+ * way) and keeps what the derivative needs in device memory owned by the handle, until
+ * num_adjoint_release, the next num_adjoint_forward or num_adjoint, or num_destroy.  The
+ * handle is left at the result of the run (num_get / num_get_device read x and the total
+ * utility).  Synchronizes the handle's stream. */
+NUM_API int num_adjoint_forward(num_problem* h, int64_t iters, int32_t checkpoint_every);
+
+/* dJ/dc and dJ/dw of the kept forward run for J = <xbar, x> + ubar * sum_j U_j(x_j):
+ * xbar (DEVICE double[n], caller order, or NULL) and ubar (a finite scalar, 0 for no
+ * utility term; not both absent) are the cotangents of the final rates and of the total
+ * utility; c_grad (DEVICE double[m]) and w_grad (DEVICE double[n], caller order) receive
+ * the gradients (each may be NULL).  Runs on the handle's stream after the caller's prior
+ * work on the legacy default stream and synchronizes it.  Each segment but the one held
+ * in memory is recomputed from its checkpoint; the call may be repeated (each repeat
+ * recomputes every segment but the first).  NUM_ERR_STATE if no forward is kept or if the
+ * capacities or weights changed since it ran.  The handle is left at the forward
+ * result. */
+NUM_API int num_adjoint_backward(num_problem* h, const double* xbar, double ubar,
+                                 double* c_grad, double* w_grad);
+
+/* Free the device memory kept by num_adjoint_forward (nothing kept: no effect). */
+NUM_API int num_adjoint_release(num_problem* h);
 
 /* Zero the iteration state and history (x = z = u = 0, rho = rho0, iteration 0). */
 NUM_API int num_reset(num_problem* h);

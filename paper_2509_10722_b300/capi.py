@@ -105,6 +105,11 @@ def _load():
         "num_set_capacity": (ctypes.c_int, [P, P]),
         "num_set_weights": (ctypes.c_int, [P, P]),
         "num_adjoint": (ctypes.c_int, [P, i64, i32, P, i32, P, P, ctypes.POINTER(d)]),
+        "num_adjoint_forward": (ctypes.c_int, [P, i64, i32]),
+        "num_adjoint_backward": (ctypes.c_int, [P, P, d, P, P]),
+        "num_adjoint_release": (ctypes.c_int, [P]),
+        "num_set_capacity_device": (ctypes.c_int, [P, P]),
+        "num_set_weights_device": (ctypes.c_int, [P, P]),
         "num_get_state": (ctypes.c_int, [P, P, P, P, P, P, P, P, ctypes.POINTER(d)]),
         "num_set_state": (ctypes.c_int, [P, P, P, P, P, P, P, P, d]),
         "num_iteration_bytes": (ctypes.c_int, [P, P]),
@@ -142,6 +147,8 @@ _lib = _load()
 EXPORTED = ("num_default_params", "num_create", "num_create_device", "num_set_rho_schedule",
             "num_solve", "num_get", "num_get_device", "num_get_history", "num_get_operator",
             "num_reset", "num_set_capacity", "num_set_weights", "num_adjoint",
+            "num_adjoint_forward", "num_adjoint_backward", "num_adjoint_release",
+            "num_set_capacity_device", "num_set_weights_device",
             "num_get_state", "num_set_state",
             "num_iteration_bytes", "num_get_kernel_times", "num_kernel_launches",
             "num_objective_noalloc", "num_measure_gather_rate", "num_destroy", "num_strerror",
@@ -322,6 +329,31 @@ def num_adjoint(h, n, m, iters, checkpoint_every=50, xbar=None, objective=True):
     _check(_lib.num_adjoint(h, int(iters), int(checkpoint_every), _hptr(xb),
                             1 if objective else 0, _hptr(cg), _hptr(wg), ctypes.byref(obj)))
     return cg, wg, obj.value
+
+
+def num_set_capacity_device(h, m, c):
+    """c: contiguous float64 CUDA tensor of m values."""
+    _check(_lib.num_set_capacity_device(h, _dptr(c, "float64", int(m), "c")))
+
+
+def num_set_weights_device(h, n, w):
+    """w: contiguous float64 CUDA tensor of n values (caller order)."""
+    _check(_lib.num_set_weights_device(h, _dptr(w, "float64", int(n), "w")))
+
+
+def num_adjoint_forward(h, iters, checkpoint_every=50):
+    _check(_lib.num_adjoint_forward(h, int(iters), int(checkpoint_every)))
+
+
+def num_adjoint_backward(h, n, m, xbar=None, ubar=0.0, c_grad=None, w_grad=None):
+    """Device tensors: xbar [n] (or None), c_grad [m], w_grad [n] (float64, CUDA)."""
+    _check(_lib.num_adjoint_backward(h, _dptr(xbar, "float64", int(n), "xbar"), float(ubar),
+                                     _dptr(c_grad, "float64", int(m), "c_grad"),
+                                     _dptr(w_grad, "float64", int(n), "w_grad")))
+
+
+def num_adjoint_release(h):
+    _check(_lib.num_adjoint_release(h))
 
 
 def num_get_state(h, n, m):
@@ -614,6 +646,21 @@ class Problem:
 
     def adjoint(self, iters, checkpoint_every=50, xbar=None, objective=True):
         return num_adjoint(self.h, self.n, self.m, iters, checkpoint_every, xbar, objective)
+
+    def set_capacity_device(self, c):
+        num_set_capacity_device(self.h, self.m, c)
+
+    def set_weights_device(self, w):
+        num_set_weights_device(self.h, self.n, w)
+
+    def adjoint_forward(self, iters, checkpoint_every=50):
+        num_adjoint_forward(self.h, iters, checkpoint_every)
+
+    def adjoint_backward(self, xbar=None, ubar=0.0, c_grad=None, w_grad=None):
+        num_adjoint_backward(self.h, self.n, self.m, xbar, ubar, c_grad, w_grad)
+
+    def adjoint_release(self):
+        num_adjoint_release(self.h)
 
     def get_state(self):
         return num_get_state(self.h, self.n, self.m)

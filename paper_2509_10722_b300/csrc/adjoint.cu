@@ -225,27 +225,28 @@ __global__ void __launch_bounds__(kTh) k_adj_stream(AdjView<T> a, const T* __res
     }
 }
 
-// Initial cotangents for the final rates: x_bar = xbar_in (caller order) plus, for the
-// total utility, U'(x) (w / x or w); the direct dU/dw (log x or x) starts w_bar.
+// Initial cotangents for the final rates: x_bar = xbar_in (caller order) plus, for a
+// cotangent ubar of the total utility, ubar U'(x) (U' = w / x, w / x^2 or w); the direct
+// ubar dU/dw (log x, -1 / x or x) starts w_bar.
 template <typename T>
-__global__ void k_adj_init(AdjView<T> a, const double* __restrict__ xbar_in, int objective) {
+__global__ void k_adj_init(AdjView<T> a, const double* __restrict__ xbar_in, double ubar) {
     using T2 = typename Pair<T>::type;
     const View<T>& v = a.v;
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < v.n; j += gridDim.x * blockDim.x) {
         const int o = v.perm ? v.perm[j] : j;
         T xb = xbar_in ? (T)xbar_in[o] : T(0);
         T wb = T(0);
-        if (objective) {
-            const T x = v.x[j], wt = v.wt[j];
+        if (ubar != 0.0) {
+            const T x = v.x[j], wt = v.wt[j], u = (T)ubar;
             if (v.ut && v.ut[j] == 2) {
-                xb += wt / (x * x);  // U = -w / x
-                wb = -T(1) / x;
+                xb += u * (wt / (x * x));  // U = -w / x
+                wb = u * (-T(1) / x);
             } else if (wt > T(0)) {
-                xb += wt / x;
-                wb = log(x);
+                xb += u * (wt / x);
+                wb = u * log(x);
             } else {
-                xb += -wt;
-                wb = x;
+                xb += u * (-wt);
+                wb = u * x;
             }
         }
         a.xb[j] = xb;
@@ -292,8 +293,8 @@ int grid_for(long long count) {
 }  // namespace
 
 template <typename T>
-cudaError_t adjoint_init(const AdjView<T>& a, const double* xbar, int objective, cudaStream_t st) {
-    k_adj_init<T><<<grid_for(a.v.n > a.v.m ? a.v.n : a.v.m), kTh, 0, st>>>(a, xbar, objective);
+cudaError_t adjoint_init(const AdjView<T>& a, const double* xbar, double ubar, cudaStream_t st) {
+    k_adj_init<T><<<grid_for(a.v.n > a.v.m ? a.v.n : a.v.m), kTh, 0, st>>>(a, xbar, ubar);
     note_launches(1);
     return cudaGetLastError();
 }
@@ -328,7 +329,7 @@ cudaError_t set_weights(const View<T>& v, const double* w, cudaStream_t st) {
 }
 
 #define PMP_ADJ_INST(T)                                                                        \
-    template cudaError_t adjoint_init<T>(const AdjView<T>&, const double*, int, cudaStream_t); \
+    template cudaError_t adjoint_init<T>(const AdjView<T>&, const double*, double, cudaStream_t); \
     template cudaError_t adjoint_step<T>(const AdjView<T>&, const T*, const T*, const double*,  \
                                          cudaStream_t);                                        \
     template cudaError_t adjoint_export<T>(const AdjView<T>&, double*, double*, cudaStream_t);  \

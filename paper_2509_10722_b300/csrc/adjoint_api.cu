@@ -1,6 +1,17 @@
-// C ABI of the PMP solver: num_adjoint, the reverse-mode derivative of unrolled
-// iterations (forward with checkpoints, per-segment recompute to a tape, backward sweep;
-// the kernels are in adjoint.cu).
+// C ABI of the PMP solver: the reverse-mode derivative of unrolled iterations (kernels in
+// adjoint.cu).
+//
+//   num_adjoint_forward   K iterations from the zero state, keeping the iterate every Kc
+//                         iterations (checkpoints) and the last segment's tape (x, the
+//                         slack flows and the rho of each iteration) in the handle;
+//   num_adjoint_backward  the backward sweep from what the forward kept: per segment, last
+//                         first, the segment's tape (recomputed from its checkpoint unless
+//                         it is the one in the tape already), then the transposed
+//                         iterations; cotangents and gradients are caller DEVICE arrays;
+//   num_adjoint           both, with HOST arrays (the tape is released at the end);
+//   num_adjoint_release   frees what the forward kept.
+// Under the row kernels the tape is written by the forward kernels themselves; otherwise
+// (tile schedule, plain FP64 path) one iteration at a time is copied out.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -18,6 +29,36 @@
 using namespace pmp::host;
 using pmp::Ctl;
 using pmp::View;
+
+// What num_adjoint_forward keeps (device memory through the handle's allocator).
+struct AdjTape {
+    int64_t K = 0, Kc = 0, nseg = 0;
+    size_t sb = 0;              // bytes of one checkpoint
+    char* ckpt = nullptr;       // nseg + 1 checkpoints (segment starts, then the final state)
+    void* tape_x = nullptr;     // Kc x n iterates of one segment
+    void* tape_ps = nullptr;    // Kc x m slack flows
+    double* tape_rho = nullptr; // Kc rho values
+    int64_t tape_seg = -1;      // the segment whose iterations are in the tape
+    long long gen = 0;          // the handle's param_gen at the forward
+    int prec = 0;
+    void *xb = nullptr, *Zb = nullptr, *ab = nullptr, *wb = nullptr, *yb = nullptr,
+         *zsb = nullptr, *Rxb = nullptr, *cb = nullptr, *abc = nullptr;
+    std::vector<void*> owned;
+};
+
+namespace pmp {
+namespace host {
+
+void adjoint_tape_free(num_problem* h) {
+    if (!h || !h->adj) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    for (void* q : h->adj->owned) dev_free(h, q);
+    delete h->adj;
+    h->adj = nullptr;
+}
+
+}  // namespace host
+}  // namespace pmp
 
 namespace {
 
@@ -60,136 +101,199 @@ cudaError_t copy_state(num_problem* h, char* slot, bool save) {
     return cudaSuccess;
 }
 
-template <typename T>
-int adjoint_impl(num_problem* h, int64_t K, int64_t Kc, const double* xbar, int objective,
-                 double* c_grad, double* w_grad, double* objective_out) {
-    using T2 = typename pmp::Pair<T>::type;
-    cudaStream_t st = h->stream;
+// A new tape for K iterations with checkpoints every Kc (the old one is freed).
+int tape_alloc(num_problem* h, int64_t K, int64_t Kc) {
+    adjoint_tape_free(h);
+    AdjTape* t = new (std::nothrow) AdjTape();
+    if (!t) return fail(NUM_ERR_OOM, "host allocation failed");
+    h->adj = t;
+    const size_t ts = h->prec == NUM_FUSED_FP32 ? 4 : 8;
     const size_t N = (size_t)h->n, M = (size_t)h->m;
-    const int64_t nseg = (K + Kc - 1) / Kc;
-    const size_t sb = state_bytes(h);
-    std::vector<void*> owned;
+    t->K = K;
+    t->Kc = Kc;
+    t->nseg = (K + Kc - 1) / Kc;
+    t->sb = state_bytes(h);
+    t->prec = h->prec;
     bool ok = true;
     auto A = [&](size_t bytes) -> void* {
         void* q = ok ? dev_alloc(h, bytes) : nullptr;
-        if (!q) ok = false;
-        else owned.push_back(q);
+        if (!q)
+            ok = false;
+        else
+            t->owned.push_back(q);
         return q;
     };
+    t->ckpt = (char*)A(t->sb * (size_t)(t->nseg + 1));
+    t->tape_x = A(ts * N * (size_t)Kc);
+    t->tape_ps = A(ts * M * (size_t)Kc);
+    t->tape_rho = (double*)A(sizeof(double) * (size_t)Kc);
+    t->xb = A(ts * N);
+    t->Zb = A(ts * N);
+    t->ab = A(2 * ts * N);
+    t->wb = A(ts * N);
+    t->yb = A(ts * M);
+    t->zsb = A(ts * M);
+    t->Rxb = A(ts * M);
+    t->cb = A(ts * M);
+    if (h->chunks && h->nchunks > 0) t->abc = A(2 * ts * (size_t)h->nchunks);
+    if (!ok) {
+        adjoint_tape_free(h);
+        return fail(NUM_ERR_OOM, "device allocation failed (adjoint tape and checkpoints)");
+    }
+    return NUM_OK;
+}
+
+// Run iterations k0 + 1 .. k0 + cnt from the current state, writing each one's x, slack
+// flows and rho to the tape.
+cudaError_t taped_run(num_problem* h, int64_t k0, int64_t cnt) {
+    AdjTape* t = h->adj;
+    cudaStream_t st = h->stream;
+    cudaError_t e = pmp::ctl_arm(h->ctl, k0 + cnt, 0.0, st);
+    if (e != cudaSuccess) return e;
+    if (h->sched_kind == NUM_SCHEDULE_ROWS && h->prec != NUM_PLAIN_FP64) {
+        // the row kernels write the tape themselves
+        h->tape_x = t->tape_x;
+        h->tape_ps = t->tape_ps;
+        h->tape_rho = t->tape_rho;
+        h->tape_k0 = k0;
+        h->tape_len = (int)cnt;
+        e = run_iterations(h, (int)cnt);
+        h->tape_x = h->tape_ps = nullptr;
+        h->tape_rho = nullptr;
+        h->tape_k0 = 0;
+        h->tape_len = 0;
+        pmp::note_launches(cnt * h->kpi);
+        return e;
+    }
+    const size_t ts = h->prec == NUM_FUSED_FP32 ? 4 : 8;
+    const size_t N = (size_t)h->n, M = (size_t)h->m;
+    for (int64_t i = 0; i < cnt && e == cudaSuccess; ++i) {
+        e = pmp::record_rho(h->ctl, t->tape_rho + i, st);
+        if (e == cudaSuccess) e = run_iterations(h, 1);
+        pmp::note_launches(h->kpi);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync((char*)t->tape_x + ts * N * (size_t)i, h->x, ts * N,
+                                cudaMemcpyDeviceToDevice, st);
+        const void* ps = h->ps;
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync((char*)t->tape_ps + ts * M * (size_t)i, ps, ts * M,
+                                cudaMemcpyDeviceToDevice, st);
+    }
+    return e;
+}
+
+int forward_impl(num_problem* h, int64_t K, int64_t Kc) {
+    cudaStream_t st = h->stream;
+    int rc = tape_alloc(h, K, Kc);
+    if (rc != NUM_OK) return rc;
+    AdjTape* t = h->adj;
+    cudaError_t e = cudaSuccess;
+#define FK(call, what)                  \
+    do {                                \
+        e = (call);                     \
+        if (e != cudaSuccess) {         \
+            adjoint_tape_free(h);       \
+            return cuda_fail(e, what);  \
+        }                               \
+    } while (0)
+    FK(order_after_legacy(h), "ordering");
+    FK(zero_state(h), "zeroing the state");
+    for (int64_t s = 0; s < t->nseg; ++s) {
+        const int64_t cnt = std::min<int64_t>(Kc, K - s * Kc);
+        FK(copy_state(h, t->ckpt + t->sb * (size_t)s, true), "checkpoint");
+        if (s < t->nseg - 1) {
+            FK(pmp::ctl_arm(h->ctl, s * Kc + cnt, 0.0, st), "arming");
+            FK(run_iterations(h, (int)cnt), "forward iterations");
+            pmp::note_launches(cnt * h->kpi);
+        } else {
+            FK(taped_run(h, s * Kc, cnt), "forward iterations of the last segment");
+        }
+    }
+    // the objective of the final state (num_get reports it), then the final state itself
+    FK(h->prec == NUM_FUSED_FP32
+           ? pmp::export_solution<float>(make_view<float>(h), nullptr, nullptr, h->part_exp,
+                                         h->exp_blocks, st)
+           : pmp::export_solution<double>(make_view<double>(h), nullptr, nullptr, h->part_exp,
+                                          h->exp_blocks, st),
+       "objective");
+    FK(copy_state(h, t->ckpt + t->sb * (size_t)t->nseg, true), "final state");
+    FK(cudaMemcpyAsync(h->ctl_host, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st), "ctl");
+    FK(cudaStreamSynchronize(st), "adjoint forward");
+#undef FK
+    t->tape_seg = t->nseg - 1;
+    t->gen = h->param_gen;
+    return check_debug_flag(h);
+}
+
+template <typename T>
+int backward_impl(num_problem* h, const double* xbar, double ubar, double* c_grad,
+                  double* w_grad) {
+    using T2 = typename pmp::Pair<T>::type;
+    AdjTape* t = h->adj;
+    cudaStream_t st = h->stream;
+    const size_t N = (size_t)h->n, M = (size_t)h->m;
     pmp::AdjView<T> a;
     std::memset(&a, 0, sizeof(a));
     a.alpha = h->prm.alpha;
-    a.xb = (T*)A(sizeof(T) * N);
-    a.Zb = (T*)A(sizeof(T) * N);
-    a.ab = (T2*)A(sizeof(T2) * N);
-    a.wb = (T*)A(sizeof(T) * N);
-    a.yb = (T*)A(sizeof(T) * M);
-    a.zsb = (T*)A(sizeof(T) * M);
-    a.Rxb = (T*)A(sizeof(T) * M);
-    a.cb = (T*)A(sizeof(T) * M);
-    if (h->chunks && h->nchunks > 0) a.abc = (T2*)A(sizeof(T2) * (size_t)h->nchunks);
-    T* tape_x = (T*)A(sizeof(T) * N * (size_t)Kc);
-    T* tape_ps = (T*)A(sizeof(T) * M * (size_t)Kc);
-    double* tape_rho = (double*)A(sizeof(double) * (size_t)Kc);
-    char* ckpt = (char*)A(sb * (size_t)(nseg + 1));
-    double* xbar_dev = xbar ? (double*)A(8 * N) : nullptr;
-    auto release = [&]() {
-        cudaStreamSynchronize(st);
-        for (void* q : owned) dev_free(h, q);
-    };
-    if (!ok) {
-        release();
-        return fail(NUM_ERR_OOM, "device allocation failed (tape and checkpoints)");
-    }
+    a.xb = (T*)t->xb;
+    a.Zb = (T*)t->Zb;
+    a.ab = (T2*)t->ab;
+    a.wb = (T*)t->wb;
+    a.yb = (T*)t->yb;
+    a.zsb = (T*)t->zsb;
+    a.Rxb = (T*)t->Rxb;
+    a.cb = (T*)t->cb;
+    a.abc = (T2*)t->abc;
     cudaError_t e = cudaSuccess;
-#define AK(call, what)                 \
+#define BK(call, what)                 \
     do {                               \
         e = (call);                    \
         if (e != cudaSuccess) {        \
-            release();                 \
+            t->tape_seg = -1;          \
             return cuda_fail(e, what); \
         }                              \
     } while (0)
-    AK(order_after_legacy(h), "ordering");
-    if (xbar) AK(cudaMemcpyAsync(xbar_dev, xbar, 8 * N, cudaMemcpyHostToDevice, st), "copy xbar");
-    // run `cnt` iterations one at a time, keeping rho, x and the slack flow of each
-    auto tape_segment = [&](int64_t cnt) -> cudaError_t {
-        for (int64_t i = 0; i < cnt; ++i) {
-            cudaError_t r = pmp::record_rho(h->ctl, tape_rho + i, st);
-            if (r == cudaSuccess) r = run_iterations(h, 1);
-            pmp::note_launches(h->kpi);
-            if (r == cudaSuccess)
-                r = cudaMemcpyAsync(tape_x + N * (size_t)i, h->x, sizeof(T) * N,
-                                    cudaMemcpyDeviceToDevice, st);
-            if (r == cudaSuccess)
-                r = cudaMemcpyAsync(tape_ps + M * (size_t)i, h->ps, sizeof(T) * M,
-                                    cudaMemcpyDeviceToDevice, st);
-            if (r != cudaSuccess) return r;
-        }
-        return cudaSuccess;
-    };
-    // forward K iterations from the zero state, keeping the state at every segment start;
-    // the last segment is taped on the way, so the backward sweep starts without a recompute
-    AK(zero_state(h), "zeroing the state");
-    for (int64_t s = 0; s < nseg; ++s) {
-        const int64_t cnt = std::min<int64_t>(Kc, K - s * Kc);
-        AK(copy_state(h, ckpt + sb * (size_t)s, true), "checkpoint");
-        AK(pmp::ctl_arm(h->ctl, s * Kc + cnt, 0.0, st), "arming");
-        if (s < nseg - 1) {
-            AK(run_iterations(h, (int)cnt), "forward iterations");
-            pmp::note_launches(cnt * h->kpi);
-        } else {
-            AK(tape_segment(cnt), "forward iterations of the last segment");
-        }
-    }
-    if (objective_out) {
-        AK(h->prec == NUM_FUSED_FP32
-               ? pmp::export_solution<float>(make_view<float>(h), nullptr, nullptr, h->part_exp,
-                                             h->exp_blocks, st)
-               : pmp::export_solution<double>(make_view<double>(h), nullptr, nullptr,
-                                              h->part_exp, h->exp_blocks, st),
-           "objective");
-    }
-    // the forward result (with its objective) is restored at the end
-    AK(copy_state(h, ckpt + sb * (size_t)nseg, true), "final state");
+    BK(order_after_legacy(h), "ordering");
+    // the cotangents start from the final state
+    BK(copy_state(h, t->ckpt + t->sb * (size_t)t->nseg, false), "restore the final state");
     a.v = make_view<T>(h);
-    AK(pmp::adjoint_init<T>(a, xbar_dev, objective, st), "adjoint init");
-    // backward, one segment at a time: recompute its iterates (deterministic; the last
-    // segment's are taped already), then sweep
-    for (int64_t s = nseg - 1; s >= 0; --s) {
-        const int64_t cnt = std::min<int64_t>(Kc, K - s * Kc);
-        if (s < nseg - 1) {
-            AK(copy_state(h, ckpt + sb * (size_t)s, false), "restore checkpoint");
-            AK(pmp::ctl_arm(h->ctl, s * Kc + cnt, 0.0, st), "arming");
-            AK(tape_segment(cnt), "recomputing a segment");
+    BK(pmp::adjoint_init<T>(a, xbar, ubar, st), "adjoint init");
+    const T* tx = (const T*)t->tape_x;
+    const T* tp = (const T*)t->tape_ps;
+    for (int64_t s = t->nseg - 1; s >= 0; --s) {
+        const int64_t cnt = std::min<int64_t>(t->Kc, t->K - s * t->Kc);
+        if (t->tape_seg != s) {  // recompute the segment's iterations into the tape
+            t->tape_seg = -1;
+            BK(copy_state(h, t->ckpt + t->sb * (size_t)s, false), "restore checkpoint");
+            BK(taped_run(h, s * t->Kc, cnt), "recomputing a segment");
+            t->tape_seg = s;
         }
         for (int64_t i = cnt - 1; i >= 0; --i)
-            AK(pmp::adjoint_step<T>(a, tape_x + N * (size_t)i, tape_ps + M * (size_t)i,
-                                    tape_rho + i, st),
+            BK(pmp::adjoint_step<T>(a, tx + N * (size_t)i, tp + M * (size_t)i, t->tape_rho + i,
+                                    st),
                "adjoint iteration");
     }
-    // dJ/dw (n values, caller order) through the n-sized staging buffer, dJ/dc (m values)
-    // through the m-sized one
-    if (w_grad) {
-        AK(pmp::adjoint_export<T>(a, /*c_grad=*/nullptr, /*w_grad=*/h->x64, st), "export dJ/dw");
-        AK(cudaMemcpyAsync(w_grad, h->x64, 8 * N, cudaMemcpyDeviceToHost, st), "dJ/dw");
-    }
-    if (c_grad) {
-        AK(pmp::adjoint_export<T>(a, /*c_grad=*/h->y64, /*w_grad=*/nullptr, st), "export dJ/dc");
-        AK(cudaMemcpyAsync(c_grad, h->y64, 8 * M, cudaMemcpyDeviceToHost, st), "dJ/dc");
-    }
+    BK(pmp::adjoint_export<T>(a, c_grad, w_grad, st), "exporting the gradients");
     // leave the handle at the forward result
-    AK(copy_state(h, ckpt + sb * (size_t)nseg, false), "restore the final state");
-    AK(cudaMemcpyAsync(h->ctl_host, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st), "ctl");
-    AK(cudaStreamSynchronize(st), "adjoint");
-#undef AK
-    if (objective_out) *objective_out = h->ctl_host->objective;
-    const int dbg_rc = check_debug_flag(h);
-    if (dbg_rc != NUM_OK) {
-        release();
-        return dbg_rc;
-    }
-    release();
+    BK(copy_state(h, t->ckpt + t->sb * (size_t)t->nseg, false), "restore the final state");
+    BK(cudaMemcpyAsync(h->ctl_host, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st), "ctl");
+    BK(cudaStreamSynchronize(st), "adjoint");
+#undef BK
+    return check_debug_flag(h);
+}
+
+int backward(num_problem* h, const double* xbar, double ubar, double* c_grad, double* w_grad) {
+    if (!h->adj) return fail(NUM_ERR_STATE, "no adjoint forward to differentiate (call num_adjoint_forward)");
+    if (h->adj->gen != h->param_gen || h->adj->prec != h->prec)
+        return fail(NUM_ERR_STATE, "the capacities or weights changed since num_adjoint_forward");
+    return h->prec == NUM_FUSED_FP32 ? backward_impl<float>(h, xbar, ubar, c_grad, w_grad)
+                                     : backward_impl<double>(h, xbar, ubar, c_grad, w_grad);
+}
+
+int checkpoint_interval(int64_t iters, int32_t checkpoint_every, int64_t* Kc) {
+    if (iters < 1) return fail(NUM_ERR_INVALID, "iters must be >= 1");
+    if (checkpoint_every < 0) return fail(NUM_ERR_INVALID, "checkpoint_every must be >= 0");
+    *Kc = checkpoint_every == 0 ? iters : std::min<int64_t>(checkpoint_every, iters);
     return NUM_OK;
 }
 
@@ -197,20 +301,78 @@ int adjoint_impl(num_problem* h, int64_t K, int64_t Kc, const double* xbar, int 
 
 extern "C" {
 
+int num_adjoint_forward(num_problem* h, int64_t iters, int32_t checkpoint_every) {
+    TraceRange trace("num_adjoint_forward");
+    g_last_error.clear();
+    if (!h) return fail(NUM_ERR_INVALID, "handle is NULL");
+    int64_t Kc = 0;
+    const int rc = checkpoint_interval(iters, checkpoint_every, &Kc);
+    if (rc != NUM_OK) return rc;
+    return forward_impl(h, iters, Kc);
+}
+
+int num_adjoint_backward(num_problem* h, const double* xbar, double ubar, double* c_grad,
+                         double* w_grad) {
+    TraceRange trace("num_adjoint_backward");
+    g_last_error.clear();
+    if (!h) return fail(NUM_ERR_INVALID, "handle is NULL");
+    if (!xbar && ubar == 0.0) return fail(NUM_ERR_INVALID, "nothing to differentiate");
+    if (!std::isfinite(ubar)) return fail(NUM_ERR_INVALID, "ubar is not finite");
+    return backward(h, xbar, ubar, c_grad, w_grad);
+}
+
+int num_adjoint_release(num_problem* h) {
+    g_last_error.clear();
+    if (!h) return fail(NUM_ERR_INVALID, "handle is NULL");
+    adjoint_tape_free(h);
+    return NUM_OK;
+}
+
 int num_adjoint(num_problem* h, int64_t iters, int32_t checkpoint_every, const double* xbar,
                 int32_t objective, double* c_grad, double* w_grad, double* objective_out) {
     TraceRange trace("num_adjoint");
     g_last_error.clear();
     if (!h) return fail(NUM_ERR_INVALID, "handle is NULL");
-    if (iters < 1) return fail(NUM_ERR_INVALID, "iters must be >= 1");
     if (objective != 0 && objective != 1) return fail(NUM_ERR_INVALID, "objective must be 0 or 1");
     if (!xbar && !objective) return fail(NUM_ERR_INVALID, "nothing to differentiate");
-    if (checkpoint_every < 0) return fail(NUM_ERR_INVALID, "checkpoint_every must be >= 0");
-    const int64_t Kc = checkpoint_every == 0 ? iters : std::min<int64_t>(checkpoint_every, iters);
-    return h->prec == NUM_FUSED_FP32
-               ? adjoint_impl<float>(h, iters, Kc, xbar, objective, c_grad, w_grad, objective_out)
-               : adjoint_impl<double>(h, iters, Kc, xbar, objective, c_grad, w_grad,
-                                      objective_out);
+    int64_t Kc = 0;
+    int rc = checkpoint_interval(iters, checkpoint_every, &Kc);
+    if (rc != NUM_OK) return rc;
+    rc = forward_impl(h, iters, Kc);
+    if (rc != NUM_OK) return rc;
+    const double objective_value = h->ctl_host->objective;
+    // host arrays: the cotangent through a device copy, the gradients through the n- and
+    // m-sized staging buffers (exported one at a time)
+    cudaStream_t st = h->stream;
+    double* xbar_dev = nullptr;
+    if (xbar) {
+        xbar_dev = (double*)dev_alloc(h, 8 * (size_t)h->n);
+        if (!xbar_dev) {
+            adjoint_tape_free(h);
+            return fail(NUM_ERR_OOM, "device allocation failed");
+        }
+    }
+    cudaError_t e = cudaSuccess;
+    if (xbar_dev) {
+        e = cudaMemcpyAsync(xbar_dev, xbar, 8 * (size_t)h->n, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    }
+    if (e == cudaSuccess) {
+        // dJ/dw to x64 and dJ/dc to y64 in one sweep: x64 / y64 are not used by the sweep
+        rc = backward(h, xbar_dev, objective ? 1.0 : 0.0, c_grad ? h->y64 : nullptr,
+                      w_grad ? h->x64 : nullptr);
+        if (rc == NUM_OK && w_grad)
+            e = cudaMemcpyAsync(w_grad, h->x64, 8 * (size_t)h->n, cudaMemcpyDeviceToHost, st);
+        if (rc == NUM_OK && c_grad && e == cudaSuccess)
+            e = cudaMemcpyAsync(c_grad, h->y64, 8 * (size_t)h->m, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    }
+    if (xbar_dev) dev_free(h, xbar_dev);
+    adjoint_tape_free(h);
+    if (e != cudaSuccess) return cuda_fail(e, "adjoint gradients");
+    if (rc != NUM_OK) return rc;
+    if (objective_out) *objective_out = objective_value;
+    return NUM_OK;
 }
 
 }  // extern "C"

@@ -89,6 +89,7 @@ void destroy_handle(num_problem* h) {
     if (h->stream) cudaStreamSynchronize(h->stream);
     if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
     if (h->graph) cudaGraphDestroy(h->graph);
+    adjoint_tape_free(h);
     while (!h->blocks.empty()) dev_free(h, h->blocks.back().first);
     if (h->ctl_host) cudaFreeHost(h->ctl_host);
     for (cudaEvent_t ev : h->evs) cudaEventDestroy(ev);
@@ -865,6 +866,7 @@ int num_set_capacity(num_problem* h, const double* c) {
                                               nullptr, nullptr, (double*)h->c, nullptr, nullptr,
                                               nullptr, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    h->param_gen += 1;
     return finish_cuda(e, "setting the capacities");
 }
 
@@ -937,7 +939,59 @@ int num_set_weights(num_problem* h, const double* w) {
         e = h->prec == NUM_FUSED_FP32 ? pmp::set_weights<float>(make_view<float>(h), h->x64, st)
                                       : pmp::set_weights<double>(make_view<double>(h), h->x64, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    h->param_gen += 1;
     return finish_cuda(e, "setting the weights");
+}
+
+// The device-array forms of the two setters: the values are checked on the device (finite
+// and > 0) before they replace the handle's.
+static int set_values_device(num_problem* h, const double* a, bool capacity) {
+    const int count = (int)(capacity ? h->m : h->n);
+    cudaStream_t st = h->stream;
+    if (!h->err_d) {
+        h->err_d = (int*)dev_alloc(h, sizeof(int));
+        if (!h->err_d) return fail(NUM_ERR_OOM, "device allocation failed");
+    }
+    int bad = 0;
+    cudaError_t e = order_after_legacy(h);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->err_d, 0, sizeof(int), st);
+    if (e == cudaSuccess) e = pmp::validate_positive(count, a, h->err_d, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, h->err_d, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "checking the values");
+    if (bad)
+        return fail(NUM_ERR_INVALID, capacity ? "a capacity is not finite and > 0"
+                                              : "a weight is not finite and > 0");
+    double* stage = capacity ? h->y64 : h->x64;
+    e = cudaMemcpyAsync(stage, a, 8 * (size_t)count, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) {
+        if (capacity)
+            e = h->prec == NUM_FUSED_FP32
+                    ? pmp::convert_params<float>(0, count, stage, nullptr, nullptr, nullptr,
+                                                 nullptr, nullptr, (float*)h->c, nullptr,
+                                                 nullptr, nullptr, st)
+                    : pmp::convert_params<double>(0, count, stage, nullptr, nullptr, nullptr,
+                                                  nullptr, nullptr, (double*)h->c, nullptr,
+                                                  nullptr, nullptr, st);
+        else
+            e = h->prec == NUM_FUSED_FP32 ? pmp::set_weights<float>(make_view<float>(h), stage, st)
+                                          : pmp::set_weights<double>(make_view<double>(h), stage, st);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    h->param_gen += 1;
+    return finish_cuda(e, capacity ? "setting the capacities" : "setting the weights");
+}
+
+int num_set_capacity_device(num_problem* h, const double* c) {
+    g_last_error.clear();
+    if (!h || !c) return fail(NUM_ERR_INVALID, "NULL argument");
+    return set_values_device(h, c, true);
+}
+
+int num_set_weights_device(num_problem* h, const double* w) {
+    g_last_error.clear();
+    if (!h || !w) return fail(NUM_ERR_INVALID, "NULL argument");
+    return set_values_device(h, w, false);
 }
 
 }  // extern "C"

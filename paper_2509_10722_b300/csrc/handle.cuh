@@ -71,6 +71,16 @@ struct num_problem {
     double kernel_ms[pmp::kPlainKernelsPerIter] = {};
     long long kernel_runs[pmp::kPlainKernelsPerIter] = {};
     int kpi = 0;  // kernels per iteration
+    // adjoint: what num_adjoint_forward keeps for num_adjoint_backward (adjoint_api.cu)
+    struct AdjTape* adj = nullptr;
+    long long param_gen = 0;  // changes whenever c or w change
+    int* err_d = nullptr;     // device flag of the setters that take device arrays
+    // set only while a taped forward run is enqueued (see View::tape_x)
+    void* tape_x = nullptr;
+    void* tape_ps = nullptr;
+    double* tape_rho = nullptr;
+    long long tape_k0 = 0;
+    int tape_len = 0;
 };
 
 namespace pmp {
@@ -98,6 +108,7 @@ constexpr int kExportBlocksMax = 1024;
 void* dev_alloc(num_problem* h, size_t bytes);  // through the handle's allocator; NULL on failure
 void dev_free(num_problem* h, void* p);
 void destroy_handle(num_problem* h);
+void adjoint_tape_free(num_problem* h);  // the adjoint tape's host record (adjoint_api.cu)
 cudaError_t order_after_legacy(num_problem* h);  // order the handle's stream after the legacy one
 cudaError_t run_iterations(num_problem* h, int count);
 // Iterations of each replay of check_every iterations that carry kernel events: all of
@@ -168,6 +179,11 @@ View<T> make_view(const num_problem* h) {
     v.RxN = (T*)h->RxN;
     v.pbar = (T*)h->pbar;
     v.y = (T*)h->y;
+    v.tape_x = (T*)h->tape_x;
+    v.tape_ps = (T*)h->tape_ps;
+    v.tape_rho = h->tape_rho;
+    v.tape_k0 = h->tape_k0;
+    v.tape_len = h->tape_len;
     return v;
 }
 

@@ -118,6 +118,15 @@ __global__ void k_validate_capacities(int m, const double* __restrict__ c, int* 
     if (bits) atomicOr(err, bits);
 }
 
+__global__ void k_validate_positive(int count, const double* __restrict__ a, int* err) {
+    int bad = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
+        const double v = a[i];
+        if (!(v > 0.0) || !isfinite(v)) bad = 1;
+    }
+    if (bad) atomicOr(err, 1);
+}
+
 __global__ void k_init_box(unsigned long long* box) {
     box[0] = ~0ull;
     box[1] = 0ull;
@@ -530,6 +539,12 @@ cudaError_t validate_routes(int n, int m, long long nnz, const int64_t* route_pt
     note_launches(1);
     k_validate_link_ids<<<blocks_for(nnz, kThreads, 8192), kThreads, 0, st>>>(m, nnz, route_links,
                                                                               err_bits);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t validate_positive(int count, const double* a, int* err, cudaStream_t st) {
+    k_validate_positive<<<blocks_for(count, kThreads, 4096), kThreads, 0, st>>>(count, a, err);
     note_launches(1);
     return cudaGetLastError();
 }

@@ -125,6 +125,14 @@ struct View {
     unsigned int* dbg;  // debug builds: set when a gathered index was out of range
     const int* long_routes;  // row kernels: streams with more than kLongRoute links
     int nlong;
+    // adjoint tape (row kernels; NULL tape_x: not taping): iteration k0 + i + 1 writes its
+    // x to tape_x[i n ..], its slack flows to tape_ps[i m ..] and the rho it used to
+    // tape_rho[i], for 0 <= i < tape_len
+    T* tape_x;
+    T* tape_ps;
+    double* tape_rho;
+    long long tape_k0;
+    int tape_len;
 };
 
 // ---- launchers (fused.cu) -------------------------------------------------------------------
@@ -253,7 +261,8 @@ struct AdjView {
     typename Pair<T>::type* abc;  // [v.nchunks] chunk sums of (Abar, Bbar) of long links
 };
 template <typename T>
-cudaError_t adjoint_init(const AdjView<T>& a, const double* xbar, int objective, cudaStream_t st);
+// x_bar = xbar (caller order, may be NULL) + ubar U'(x); w_bar = ubar dU/dw; others zero.
+cudaError_t adjoint_init(const AdjView<T>& a, const double* xbar, double ubar, cudaStream_t st);
 template <typename T>
 cudaError_t adjoint_step(const AdjView<T>& a, const T* x_k, const T* ps_k, const double* rho,
                          cudaStream_t st);
@@ -328,6 +337,8 @@ size_t scan_tmp_len(size_t len);
 // max hi.
 cudaError_t validate_routes(int n, int m, long long nnz, const int64_t* route_ptr,
                             const int* route_links, int* err_bits, cudaStream_t st);
+// *err |= 1 if some a[i], i < count, is not finite and > 0 (device array).
+cudaError_t validate_positive(int count, const double* a, int* err, cudaStream_t st);
 cudaError_t validate_values(int n, int m, const double* c, const uint8_t* utype,
                             const double* w, const double* lo, const double* hi, int* err_bits,
                             unsigned long long* box_minmax, cudaStream_t st);

@@ -86,9 +86,9 @@ __device__ __forceinline__ typename Pair<T>::type warp_route_sum(
 // ---- stream kernel -------------------------------------------------------------------------------
 
 template <typename T>
-__device__ __forceinline__ void stream_epilogue(const View<T>& v, int j, typename Pair<T>::type sum,
-                                                T L, T xo, T Zo, T wt, T lo, T hi, T alpha,
-                                                T inv_rho, Acc<T>& acc) {
+__device__ __forceinline__ T stream_epilogue(const View<T>& v, int j, typename Pair<T>::type sum,
+                                             T L, T xo, T Zo, T wt, T lo, T hi, T alpha,
+                                             T inv_rho, Acc<T>& acc) {
     const T Zn = alpha * L * xo + (T(1) - alpha) * Zo - alpha * sum.x;
     const T S = Zn - sum.y * inv_rho;
     const T xn = stream_prox<T>(S, L, wt, inv_rho, lo, hi, v.ut && v.ut[j] == 2);
@@ -97,6 +97,7 @@ __device__ __forceinline__ void stream_epilogue(const View<T>& v, int j, typenam
     // |sigma| (x - x_prev)^2: formed in T, added in FP64
     const T dx = xn - xo;
     acc.add((double)(L * dx * dx));
+    return xn;
 }
 
 template <typename T>
@@ -118,9 +119,9 @@ __device__ __forceinline__ LinkState<T> load_link(const View<T>& v, int l) {
 
 // Link epilogue (slack prox, average, z and price updates) and its residual terms.
 template <typename T>
-__device__ __forceinline__ void link_epilogue(const View<T>& v, int l, const LinkState<T>& st,
-                                              T Rxn, int deg, T alpha, T rho, T inv_rho,
-                                              Acc<T>& r2, Acc<T>& s2) {
+__device__ __forceinline__ T link_epilogue(const View<T>& v, int l, const LinkState<T>& st,
+                                           T Rxn, int deg, T alpha, T rho, T inv_rho,
+                                           Acc<T>& r2, Acc<T>& s2) {
     using T2 = typename Pair<T>::type;
     const T pbo = st.py.x, y = st.py.y;
     T psn = st.zso - y * inv_rho;
@@ -144,6 +145,7 @@ __device__ __forceinline__ void link_epilogue(const View<T>& v, int l, const Lin
     const T dpb = pbn - pbo, dRx = Rxn - st.Rxo, dd = (psn - pbn) - (st.pso - pbo);
     r2.add((double)((degf + T(1)) * pbn * pbn));
     s2.add((double)(degf * dpb * dpb - T(2) * dpb * dRx + dd * dd));
+    return psn;
 }
 
 // Sum of x over entries [e0, e1) of the link-major index array, by one group of G lanes,

@@ -36,12 +36,16 @@ constexpr int kGroup = 8;  // lanes per link (4 links per warp); 4 to 32 measure
 
 // kSplit: the instance has streams with long routes (v.nlong > 0); without them the kernel
 // is compiled without the warp phase, and the common loop without its length test.
-template <typename T, bool kSplit>
+// kTape: the adjoint tape is being written (the forward runs of num_adjoint_forward and
+// the backward sweep's recomputation); it receives every stream's new rate.
+template <typename T, bool kSplit, bool kTape>
 __global__ void __launch_bounds__(kTh) k_stream_rows(View<T> v) {
     using V = typename Pair<T>::type;
     __shared__ double red[kWarps];
     const Ctl* ctl = v.ctl;
     if (ctl->stop) return;
+    const long long tk = kTape ? ctl->k - v.tape_k0 : -1;  // tape slot of this iteration
+    T* const tape = kTape && tk >= 0 && tk < v.tape_len ? v.tape_x + (size_t)tk * v.n : nullptr;
     const T alpha = (T)ctl->alpha;
     const T inv_rho = (T)(1.0 / ctl->rho);
     const int n = v.n;
@@ -56,7 +60,8 @@ __global__ void __launch_bounds__(kTh) k_stream_rows(View<T> v) {
         const T lo = v.box_uniform ? v.lo_u : __ldg(v.lo + j);
         const T hi = v.box_uniform ? v.hi_u : __ldg(v.hi + j);
         const V sum = route_sum<T>(row_idx, pby, p, pn, v.m, v.dbg);
-        stream_epilogue(v, j, sum, (T)(pn - p), xo, Zo, wt, lo, hi, alpha, inv_rho, acc);
+        const T xn = stream_epilogue(v, j, sum, (T)(pn - p), xo, Zo, wt, lo, hi, alpha, inv_rho, acc);
+        if (kTape && tape) tape[j] = xn;
     }
     // streams with more than kLongRoute links: one warp each
     const int lane = threadIdx.x & 31;
@@ -69,7 +74,9 @@ __global__ void __launch_bounds__(kTh) k_stream_rows(View<T> v) {
             const T xo = v.x[j], Zo = v.Z[j], wt = __ldg(v.wt + j);
             const T lo = v.box_uniform ? v.lo_u : __ldg(v.lo + j);
             const T hi = v.box_uniform ? v.hi_u : __ldg(v.hi + j);
-            stream_epilogue(v, j, sum, (T)(pn - p), xo, Zo, wt, lo, hi, alpha, inv_rho, acc);
+            const T xn = stream_epilogue(v, j, sum, (T)(pn - p), xo, Zo, wt, lo, hi, alpha,
+                                         inv_rho, acc);
+            if (kTape && tape) tape[j] = xn;
         }
     }
     const double s = block_sum(acc.value(), red);
@@ -79,12 +86,17 @@ __global__ void __launch_bounds__(kTh) k_stream_rows(View<T> v) {
 
 // kSpread: the epilogues of a group's links run on all its lanes (many links per group)
 // rather than on its leader (few).  Two pairs of gathers are in flight per lane.
-template <typename T, bool kSpread>
+// kTape: as in the stream kernel; the tape receives every link's slack flow and the rho
+// of the iteration.
+template <typename T, bool kSpread, bool kTape>
 __global__ void __launch_bounds__(kTh) k_link_rows(View<T> v) {
     __shared__ double red[3 * kWarps];
     __shared__ int last;
     Ctl* ctl = v.ctl;
     if (ctl->stop) return;
+    const long long tk = kTape ? ctl->k - v.tape_k0 : -1;  // tape slot of this iteration
+    const bool taping = kTape && tk >= 0 && tk < v.tape_len;
+    T* const tape = taping ? v.tape_ps + (size_t)tk * v.m : nullptr;
     const T alpha = (T)ctl->alpha, rho = (T)ctl->rho, inv_rho = (T)(1.0 / ctl->rho);
     auto g = cg::tiled_partition<kGroup>(cg::this_thread_block());
     const bool leader = g.thread_rank() == 0;
@@ -120,7 +132,8 @@ __global__ void __launch_bounds__(kTh) k_link_rows(View<T> v) {
             }
             if (lk < m && q1 - q0 <= kLongRow) {
                 const LinkState<T> st = load_link(v, (int)lk);
-                link_epilogue(v, (int)lk, st, mine, q1 - q0, alpha, rho, inv_rho, r2, s2);
+                const T psn = link_epilogue(v, (int)lk, st, mine, q1 - q0, alpha, rho, inv_rho, r2, s2);
+                if (kTape && tape) tape[lk] = psn;
             }
         }
     } else {
@@ -144,7 +157,10 @@ __global__ void __launch_bounds__(kTh) k_link_rows(View<T> v) {
                 LinkState<T> st;
                 if (leader) st = load_link(v, l);
                 const T s = group_gather_sum<kGroup, 2>(g, col_idx, x, p0, p1, v.n, v.dbg);
-                if (leader) link_epilogue(v, l, st, s, p1 - p0, alpha, rho, inv_rho, r2, s2);
+                if (leader) {
+                    const T psn = link_epilogue(v, l, st, s, p1 - p0, alpha, rho, inv_rho, r2, s2);
+                    if (kTape && tape) tape[l] = psn;
+                }
             }
             l = ln;
             p0 = q0;
@@ -175,7 +191,8 @@ __global__ void __launch_bounds__(kTh) k_link_rows(View<T> v) {
             if (lane == 0) {
                 v.arrive_l[ch.w] = 0;
                 const LinkState<T> st = load_link(v, ch.x);
-                link_epilogue(v, ch.x, st, t, p1 - p0, alpha, rho, inv_rho, r2, s2);
+                const T psn = link_epilogue(v, ch.x, st, t, p1 - p0, alpha, rho, inv_rho, r2, s2);
+                if (kTape && tape) tape[ch.x] = psn;
             }
         }
     }
@@ -194,6 +211,7 @@ __global__ void __launch_bounds__(kTh) k_link_rows(View<T> v) {
         grid_residual_sums(v.part_l, gridDim.x, v.part_s, v.grid_s, red, a, b, c);
         if (threadIdx.x == 0) {
             ctl->ticket = 0;
+            if (kTape && taping) v.tape_rho[tk] = ctl->rho;  // the rho this iteration used
             finalize_iteration(ctl, a, c + b, v.hist, v.sched);
         }
     }
@@ -202,12 +220,14 @@ __global__ void __launch_bounds__(kTh) k_link_rows(View<T> v) {
 template <typename T>
 cudaError_t rows_occupancy(int* occ_s, int* occ_spread, int* occ_leader) {
     // the variant with the warp phase uses at least as many registers
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ_s, k_stream_rows<T, true>,
-                                                                  kTh, 0);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        occ_s, k_stream_rows<T, true, false>, kTh, 0);
     if (e != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ_spread, k_link_rows<T, true>, kTh, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ_spread, k_link_rows<T, true, false>,
+                                                      kTh, 0);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ_leader, k_link_rows<T, false>, kTh, 0);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ_leader, k_link_rows<T, false, false>,
+                                                         kTh, 0);
 }
 
 // With about 4 links to sum per group slot of a resident grid (c5: 1e5 links), one group
@@ -241,18 +261,26 @@ cudaError_t rows_grids(int precision, int n, int m, int nchunks, int* grid_s, in
     return cudaSuccess;
 }
 
-template <typename T>
-cudaError_t rows_iteration(const View<T>& v, cudaStream_t st, cudaEvent_t* evs) {
+template <typename T, bool kTape>
+void rows_launch(const View<T>& v, cudaStream_t st, cudaEvent_t* evs) {
     if (v.nlong > 0)
-        k_stream_rows<T, true><<<v.grid_s, kTh, 0, st>>>(v);
+        k_stream_rows<T, true, kTape><<<v.grid_s, kTh, 0, st>>>(v);
     else
-        k_stream_rows<T, false><<<v.grid_s, kTh, 0, st>>>(v);
+        k_stream_rows<T, false, kTape><<<v.grid_s, kTh, 0, st>>>(v);
     if (evs) record_kernel_event(evs[0], st);
     if (v.link_spread)
-        k_link_rows<T, true><<<v.grid_l, kTh, 0, st>>>(v);
+        k_link_rows<T, true, kTape><<<v.grid_l, kTh, 0, st>>>(v);
     else
-        k_link_rows<T, false><<<v.grid_l, kTh, 0, st>>>(v);
+        k_link_rows<T, false, kTape><<<v.grid_l, kTh, 0, st>>>(v);
     if (evs) record_kernel_event(evs[1], st);
+}
+
+template <typename T>
+cudaError_t rows_iteration(const View<T>& v, cudaStream_t st, cudaEvent_t* evs) {
+    if (v.tape_x)
+        rows_launch<T, true>(v, st, evs);
+    else
+        rows_launch<T, false>(v, st, evs);
     return cudaGetLastError();
 }
 template cudaError_t rows_iteration<float>(const View<float>&, cudaStream_t, cudaEvent_t*);

@@ -92,7 +92,8 @@ def test_fp32_adjoint_near_reference(small):
     dec = oracle_run(small, iters)["decisions"]
     gc, gw, _ = _gpu_adjoint(small, iters, 0, sched=dec)
     rc, rw, _ = adjoint_ref.gradients(small, iters, dec)
-    assert rel(gc, rc) <= 1e-3 and rel(gw, rw) <= 1e-3
+    # FP32 iterates and cotangents against the FP64 reference gradient
+    assert rel(gc, rc) <= 1e-4 and rel(gw, rw) <= 1e-4
 
 
 @pytest.mark.parametrize("precision", [0, 1])
@@ -141,28 +142,118 @@ def test_adjoint_equals_gpu_finite_differences(small):
 
 def test_c5_slice_500_iterations(slice_c5):
     """The differentiation recipe: 500 unrolled iterations, checkpoints every 50, FP64
-    against the CPU reference gradient; FP32 on the same rho schedule close to it."""
+    against the CPU reference gradient; FP32 on the same rho schedule within 1e-4."""
     iters = 500
     dec = oracle_run(slice_c5, iters)["decisions"]
     rc, rw, _ = adjoint_ref.gradients(slice_c5, iters, dec)
     gc, gw, _ = _gpu_adjoint(slice_c5, iters, 1, kc=50)
     assert rel(gc, rc) <= 1e-8 and rel(gw, rw) <= 1e-8
     fc, fw, _ = _gpu_adjoint(slice_c5, iters, 0, kc=50, sched=dec)
-    assert rel(fc, rc) <= 1e-2 and rel(fw, rw) <= 1e-2
+    assert rel(fc, rc) <= 1e-4 and rel(fw, rw) <= 1e-4
 
 
 def test_autograd_function(small):
+    """total_utility and solve_x through torch autograd equal num_adjoint (host entry), and
+    the torch path runs the forward map once: its launches are the forward, the recomputed
+    segments and the backward sweep, with no second forward from zero."""
     import torch
     from paper_2509_10722_b300 import autograd, capi
-    iters = 120
+    iters, kc = 120, 50
     c = torch.tensor(small["c"], requires_grad=True)
     w = torch.tensor(small["w"], requires_grad=True)
     with capi.Problem(small, precision=1) as p:
-        J = autograd.total_utility(p, small["utype"], c, w, iters)
+        l0 = capi.num_kernel_launches()
+        J = autograd.total_utility(p, c, w, iters, kc)
         J.backward()
-        gc, gw, J2 = p.adjoint(iters, 50)
+        launched = capi.num_kernel_launches() - l0
+        gc, gw, J2 = p.adjoint(iters, kc)
     assert abs(float(J.detach()) - J2) <= 1e-12 * abs(J2)
     assert rel(c.grad.numpy(), gc) <= 1e-12 and rel(w.grad.numpy(), gw) <= 1e-12
+    # forward 2 x 120, recompute of the first two segments 2 x 100, backward 2 x 120, plus
+    # a few setup kernels; a second forward from zero would add another 240
+    assert launched <= 2 * iters + 2 * (iters - kc + 30) + 2 * iters + 40, launched
+    # solve_x: a vector-Jacobian product against the host entry with the same cotangent
+    xbar = np.random.default_rng(7).standard_normal(small["n"])
+    c2 = torch.tensor(small["c"], requires_grad=True)
+    w2 = torch.tensor(small["w"], requires_grad=True)
+    with capi.Problem(small, precision=1) as p:
+        x = autograd.solve_x(p, c2, w2, iters, kc)
+        (x * torch.tensor(xbar)).sum().backward()
+        hc, hw, _ = p.adjoint(iters, kc, xbar=xbar, objective=False)
+    assert rel(c2.grad.numpy(), hc) <= 1e-12 and rel(w2.grad.numpy(), hw) <= 1e-12
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_device_entries_equal_host_entry(small, precision):
+    """num_adjoint_forward + num_adjoint_backward (device arrays) give the host entry's
+    gradients bit for bit, twice in a row from one forward; a utility cotangent ubar
+    scales them; changed capacities or a missing forward are refused."""
+    import torch
+    from paper_2509_10722_b300 import capi
+    iters, kc = 130, 50
+    xbar = np.random.default_rng(9).standard_normal(small["n"])
+    with capi.Problem(small, precision=precision) as p:
+        hc, hw, _ = p.adjoint(iters, kc, xbar=xbar, objective=True)
+        with pytest.raises(capi.NumError) as e0:
+            p.adjoint_backward(ubar=1.0, c_grad=torch.empty(p.m, dtype=torch.float64,
+                                                            device="cuda"))
+        assert e0.value.code == capi.NUM_ERR_STATE
+        p.adjoint_forward(iters, kc)
+        xb = torch.tensor(xbar, device="cuda")
+        outs = []
+        for ubar in (1.0, 1.0, 2.5):
+            cg = torch.empty(p.m, dtype=torch.float64, device="cuda")
+            wg = torch.empty(p.n, dtype=torch.float64, device="cuda")
+            p.adjoint_backward(xbar=xb if ubar == 1.0 else None, ubar=ubar, c_grad=cg,
+                               w_grad=wg)
+            outs.append((cg.cpu().numpy(), wg.cpu().numpy()))
+        assert np.array_equal(outs[0][0], hc) and np.array_equal(outs[0][1], hw)
+        assert np.array_equal(outs[1][0], hc) and np.array_equal(outs[1][1], hw)
+        # the utility part alone, scaled by 2.5, against the host entry's
+        uc, uw, _ = p.adjoint(iters, kc, objective=True)
+        tol = 1e-12 if precision == 1 else 1e-6
+        assert rel(outs[2][0], 2.5 * uc) <= tol and rel(outs[2][1], 2.5 * uw) <= tol
+        p.adjoint_forward(iters, kc)
+        p.set_capacity_device(torch.tensor(small["c"] * 1.01, device="cuda"))
+        with pytest.raises(capi.NumError) as e1:
+            p.adjoint_backward(ubar=1.0, w_grad=torch.empty(p.n, dtype=torch.float64,
+                                                            device="cuda"))
+        assert e1.value.code == capi.NUM_ERR_STATE
+        p.adjoint_release()
+
+
+def test_device_setters(small):
+    """Device-array setters equal the host ones (same iterates after a solve) and refuse
+    non-positive or non-finite values without changing anything."""
+    import torch
+    from paper_2509_10722_b300 import capi
+    c = small["c"] * np.linspace(0.5, 1.5, small["m"])
+    w = small["w"] * np.linspace(1.5, 0.5, small["n"])
+    out = []
+    for dev in (False, True):
+        with capi.Problem(small, precision=1) as p:
+            if dev:
+                p.set_capacity_device(torch.tensor(c, device="cuda"))
+                p.set_weights_device(torch.tensor(w, device="cuda"))
+            else:
+                p.set_capacity(c)
+                p.set_weights(w)
+            p.solve(200, 0.0)
+            out.append(p.get()[0])
+            for bad in (0.0, -1.0, np.nan, np.inf):
+                cb = torch.tensor(c, device="cuda")
+                cb[3] = bad
+                with pytest.raises(capi.NumError) as e:
+                    p.set_capacity_device(cb)
+                assert e.value.code == capi.NUM_ERR_INVALID
+                wb = torch.tensor(w, device="cuda")
+                wb[5] = bad
+                with pytest.raises(capi.NumError) as e:
+                    p.set_weights_device(wb)
+                assert e.value.code == capi.NUM_ERR_INVALID
+            p.solve(10, 0.0)
+            out.append(p.get()[0])
+    assert np.array_equal(out[0], out[2]) and np.array_equal(out[1], out[3])
 
 
 def test_c5_full_size_fp32_gradients_track_fp64():
