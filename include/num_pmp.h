@@ -66,10 +66,6 @@ extern "C" {
 #define NUM_PLAIN_FP64 2 /* unfused baseline: one kernel per step (SpMV, elementwise prox,
                             SpMV-transpose, reductions), all FP64 */
 
-/* ---- kernel schedule of the fused paths ---------------------------------------------------- */
-#define NUM_SCHEDULE_ROWS 1  /* row-parallel kernels (the default) */
-#define NUM_SCHEDULE_TILES 2 /* merge-path tiles */
-
 /* Optional device allocator.  alloc returns device memory of `bytes` bytes usable on
  * `stream` (NULL on failure, which num_create reports as NUM_ERR_OOM); release frees it. */
 typedef struct {
@@ -90,15 +86,9 @@ typedef struct {
  *               tolerances need an FP64 path
  *   check_every iterations per CUDA-graph replay between two host reads of the stop flag
  *               (default 50); iterations after the stop inside a replay do nothing
- *   tile_items  items (nonzeros + rows) per tile of the merge-path kernels; 0 = automatic,
- *               otherwise a power of two in [256, 8192] (small values exercise row splitting)
  *   history     length of the on-device ring buffer of (||r||, ||s||, rho) per iteration
  *               (default 4096; 0 = none)
  *   use_graph   1 (default): replay captured CUDA graphs; 0: plain launches
- *   schedule    0 (default) or NUM_SCHEDULE_ROWS: row-parallel fused kernels (a thread
- *               per stream, 8 lanes per link; a link of more than 256 streams is summed
- *               by whole warps, in chunks of 2048 entries);
- *               NUM_SCHEDULE_TILES: merge-path tiles of tile_items items (any skew)
  *   reorder     1 (default): place streams in the order of the first link of their route
  *               (stable), so that streams sharing that link are adjacent and the gathers
  *               of both kernels share L2 sectors; results are reported in the caller's
@@ -118,10 +108,8 @@ typedef struct {
     int32_t rho_period;
     int32_t precision;
     int32_t check_every;
-    int32_t tile_items;
     int32_t history;
     int32_t use_graph;
-    int32_t schedule;
     int32_t reorder;
     int32_t profile;
     const num_allocator* allocator;

@@ -34,8 +34,6 @@ NUM_FUSED_FP32 = 0
 NUM_FUSED_FP64 = 1
 NUM_PLAIN_FP64 = 2
 
-NUM_SCHEDULE_ROWS = 1
-NUM_SCHEDULE_TILES = 2
 
 INFO = dict(primal=0, dual=1, eps_tol=2, rho=3, objective=4, iters=5, status=6, J=7)
 NUM_INFO_LEN = 8
@@ -53,9 +51,9 @@ class num_params(ctypes.Structure):
     _fields_ = [("rho0", ctypes.c_double), ("alpha", ctypes.c_double), ("mu", ctypes.c_double),
                 ("gamma", ctypes.c_double), ("eps_abs", ctypes.c_double),
                 ("rho_period", ctypes.c_int32), ("precision", ctypes.c_int32),
-                ("check_every", ctypes.c_int32), ("tile_items", ctypes.c_int32),
+                ("check_every", ctypes.c_int32),
                 ("history", ctypes.c_int32), ("use_graph", ctypes.c_int32),
-                ("schedule", ctypes.c_int32), ("reorder", ctypes.c_int32),
+                ("reorder", ctypes.c_int32),
                 ("profile", ctypes.c_int32),
                 ("allocator", ctypes.POINTER(num_allocator))]
 

@@ -1,4 +1,4 @@
-// Reverse-mode derivative of K unrolled PMP iterations (the reduced recurrence of fused.cu,
+// Reverse-mode derivative of K unrolled PMP iterations (the reduced recurrence of rows.cu,
 // Sec. III-D..G) with respect to the capacities c and the weights w, for a cotangent on
 // the final rates x_K.  The rho of every iteration is held fixed (the forward run's own
 // decisions), which makes the K-step map piecewise smooth.
@@ -22,7 +22,7 @@
 // dx/dS = x / sqrt(D), dx/dw = 1 / (rho sqrt(D)); unclipped linear stream, dx/dS = 1/L,
 // dx/dw = 1 / (rho L); a stream at a bound of its box, 0.  Only x_k and ps_k of every
 // iteration are needed; they are recomputed segment by segment from checkpoints.
-// Links of more than kLongRow streams (row schedule) are summed by whole warps in chunks,
+// Links of more than kLongRow streams are summed by whole warps in chunks,
 // and streams with more than kLongRoute links by one warp each, as in the forward kernels.
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>

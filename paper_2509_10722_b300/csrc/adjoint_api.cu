@@ -10,8 +10,8 @@
 //                         iterations; cotangents and gradients are caller DEVICE arrays;
 //   num_adjoint           both, with HOST arrays (the tape is released at the end);
 //   num_adjoint_release   frees what the forward kept.
-// Under the row kernels the tape is written by the forward kernels themselves; otherwise
-// (tile schedule, plain FP64 path) one iteration at a time is copied out.
+// In the fused paths the tape is written by the forward kernels themselves; in the plain
+// FP64 path one iteration at a time is copied out.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -150,8 +150,8 @@ cudaError_t taped_run(num_problem* h, int64_t k0, int64_t cnt) {
     cudaStream_t st = h->stream;
     cudaError_t e = pmp::ctl_arm(h->ctl, k0 + cnt, 0.0, st);
     if (e != cudaSuccess) return e;
-    if (h->sched_kind == NUM_SCHEDULE_ROWS && h->prec != NUM_PLAIN_FP64) {
-        // the row kernels write the tape themselves
+    if (h->prec != NUM_PLAIN_FP64) {
+        // the fused row kernels write the tape themselves
         h->tape_x = t->tape_x;
         h->tape_ps = t->tape_ps;
         h->tape_rho = t->tape_rho;

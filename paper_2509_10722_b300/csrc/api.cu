@@ -120,13 +120,10 @@ cudaError_t run_iterations(num_problem* h, int count) {
         cudaEvent_t* ev =
             prof && i < profiled_iterations(h) ? h->evs.data() + 1 + (size_t)i * h->kpi : nullptr;
         cudaError_t e;
-        const bool rows = h->sched_kind == NUM_SCHEDULE_ROWS;
         if (h->prec == NUM_FUSED_FP32)
-            e = rows ? pmp::rows_iteration<float>(make_view<float>(h), h->stream, ev)
-                     : pmp::fused_iteration<float>(make_view<float>(h), h->stream, ev);
+            e = pmp::rows_iteration<float>(make_view<float>(h), h->stream, ev);
         else if (h->prec == NUM_FUSED_FP64)
-            e = rows ? pmp::rows_iteration<double>(make_view<double>(h), h->stream, ev)
-                     : pmp::fused_iteration<double>(make_view<double>(h), h->stream, ev);
+            e = pmp::rows_iteration<double>(make_view<double>(h), h->stream, ev);
         else
             e = pmp::plain_iteration(make_view<double>(h), h->plain_nb, h->stream, ev);
         if (e != cudaSuccess) return e;
@@ -168,7 +165,6 @@ cudaError_t zero_state(num_problem* h) {
     z(h->ps, ts * h->m);
     z(h->pbar, ts * h->m);
     z(h->y, ts * h->m);
-    z(h->arrive_s, sizeof(int) * (size_t)h->ntiles_s);
     z(h->arrive_l, sizeof(int) * (size_t)h->narrive_l);
     if (h->hist && h->prm.history > 0) z(h->hist, sizeof(double) * 3 * (size_t)h->prm.history);
     if (e != cudaSuccess) return e;
@@ -179,7 +175,6 @@ cudaError_t zero_state(num_problem* h) {
     return e;
 }
 
-bool is_pow2_tile(int t) { return t >= 256 && t <= 8192 && (t & (t - 1)) == 0; }
 
 int check_params(const num_params& p) {
     if (!(p.rho0 > 0.0) || !std::isfinite(p.rho0))
@@ -192,12 +187,8 @@ int check_params(const num_params& p) {
     if (p.rho_period < 0) return fail(NUM_ERR_INVALID, "rho_period must be >= 0");
     if (p.precision < 0 || p.precision > 2) return fail(NUM_ERR_INVALID, "unknown precision");
     if (p.check_every < 1) return fail(NUM_ERR_INVALID, "check_every must be >= 1");
-    if (p.tile_items != 0 && !is_pow2_tile(p.tile_items))
-        return fail(NUM_ERR_INVALID, "tile_items must be 0 or a power of two in [256, 8192]");
     if (p.history < 0) return fail(NUM_ERR_INVALID, "history must be >= 0");
     if (p.profile < 0 || p.profile > 2) return fail(NUM_ERR_INVALID, "profile must be 0, 1 or 2");
-    if (p.schedule < 0 || p.schedule > NUM_SCHEDULE_TILES)
-        return fail(NUM_ERR_INVALID, "unknown schedule");
     if (p.reorder != 0 && p.reorder != 1) return fail(NUM_ERR_INVALID, "reorder must be 0 or 1");
     if (p.allocator && (!p.allocator->alloc || !p.allocator->release))
         return fail(NUM_ERR_INVALID, "allocator needs alloc and release");
@@ -265,8 +256,6 @@ int create_impl(num_problem** out, int64_t n, int64_t m, const int64_t* route_pt
     h->n = n;
     h->m = m;
     h->nnz = nnz;
-    h->Js = (int)(nnz + n);
-    h->Jl = (int)(nnz + m);
     h->prm = prm;
     h->prec = prm.precision;
     h->user_stream = (cudaStream_t)cuda_stream;
@@ -280,14 +269,8 @@ int create_impl(num_problem** out, int64_t n, int64_t m, const int64_t* route_pt
     const bool plain = h->prec == NUM_PLAIN_FP64;
     const size_t ts = fp32 ? 4 : 8;
     const size_t N = (size_t)n, M = (size_t)m, NNZ = (size_t)nnz;
-    h->tile_s = prm.tile_items ? prm.tile_items : pmp::fused_tile_items_stream(fp32 ? 0 : 1);
-    h->tile_l = prm.tile_items ? prm.tile_items : pmp::fused_tile_items_link(fp32 ? 0 : 1);
-    h->ntiles_s = (int)((h->Js + (int64_t)h->tile_s - 1) / h->tile_s);
-    h->ntiles_l = (int)((h->Jl + (int64_t)h->tile_l - 1) / h->tile_l);
     h->plain_nb = pmp::plain_partial_blocks((int)n, (int)m);
-    h->sched_kind = prm.schedule == NUM_SCHEDULE_TILES ? NUM_SCHEDULE_TILES : NUM_SCHEDULE_ROWS;
-    const bool tiles = !plain && h->sched_kind == NUM_SCHEDULE_TILES;
-    const bool rowk = !plain && h->sched_kind == NUM_SCHEDULE_ROWS;
+    const bool rowk = !plain;
     h->exp_blocks = pmp::export_partial_blocks((int)n);
 
     // ---- device memory: the handle's arrays, then the transient build buffers ----
@@ -322,15 +305,6 @@ int create_impl(num_problem** out, int64_t n, int64_t m, const int64_t* route_pt
         h->RxN = A(ts * M);
     } else {
         h->pby = A(2 * ts * M);
-    }
-    if (tiles) {
-        h->tiles_s = (int2*)A(sizeof(int2) * (size_t)h->ntiles_s);
-        h->tiles_l = (int2*)A(sizeof(int2) * (size_t)h->ntiles_l);
-        h->carry_s = A(2 * ts * 2 * (size_t)h->ntiles_s);
-        h->carry_l = A(ts * 2 * (size_t)h->ntiles_l);
-        h->arrive_s = (int*)A(sizeof(int) * (size_t)h->ntiles_s);
-        h->arrive_l = (int*)A(sizeof(int) * (size_t)h->ntiles_l);
-        h->narrive_l = h->ntiles_l;
     }
     const size_t npart = (size_t)(kMaxGrid > h->plain_nb ? kMaxGrid : h->plain_nb);
     h->part_s = (double*)A(sizeof(double) * npart);
@@ -525,15 +499,6 @@ int create_impl(num_problem** out, int64_t n, int64_t m, const int64_t* route_pt
                                        (double*)h->c, (double*)h->wt, (double*)h->lo,
                                        (double*)h->hi, st, h->ut),
            "converting parameters");
-    if (tiles) {
-        CK(pmp::build_tiles(h->col_ptr, (int)n, h->Js, h->tile_s, h->ntiles_s, h->tiles_s, st),
-           "stream tiles");
-        CK(pmp::build_tiles(h->row_ptr, (int)m, h->Jl, h->tile_l, h->ntiles_l, h->tiles_l, st),
-           "link tiles");
-        CK(pmp::fused_grids(fp32 ? 0 : 1, h->tile_s, h->tile_l, h->ntiles_s, h->ntiles_l,
-                            &h->grid_s, &h->grid_l),
-           "sizing the fused grids");
-    }
     if (rowk) {
         CK(pmp::count_chunks(h->row_ptr, (int)m, d_ccount, d_coff, d_ctmp, &h->nchunks, st),
            "counting long-link chunks");
@@ -611,10 +576,8 @@ void num_default_params(num_params* p) {
     p->rho_period = 50;
     p->precision = NUM_FUSED_FP32;
     p->check_every = 50;
-    p->tile_items = 0;
     p->history = 4096;
     p->use_graph = 1;
-    p->schedule = 0;
     p->reorder = 1;
     p->profile = 0;
     p->allocator = nullptr;

@@ -512,7 +512,7 @@ int batch_create_impl(num_batch** out, int32_t count, const int64_t* stream_off,
         prm = *p;
     else
         num_default_params(&prm);
-    if (prm.precision == NUM_PLAIN_FP64 || prm.schedule == NUM_SCHEDULE_TILES)
+    if (prm.precision == NUM_PLAIN_FP64)
         return fail(NUM_ERR_INVALID, "batches run the fused row kernels (FP32 or FP64)");
     const int64_t n = stream_off[count], m = link_off[count];
     if (n > INT32_MAX - 1 || m > INT32_MAX - 1)

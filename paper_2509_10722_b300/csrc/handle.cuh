@@ -18,7 +18,6 @@
 
 struct num_problem {
     int64_t n = 0, m = 0, nnz = 0;
-    int Js = 0, Jl = 0;
     num_params prm{};
     num_allocator alloc{};
     bool custom_alloc = false;
@@ -31,10 +30,8 @@ struct num_problem {
     std::vector<std::pair<void*, size_t>> blocks;
 
     int *col_ptr = nullptr, *row_idx = nullptr, *row_ptr = nullptr, *col_idx = nullptr;
-    int2 *tiles_s = nullptr, *tiles_l = nullptr;
-    int ntiles_s = 0, ntiles_l = 0, tile_s = 0, tile_l = 0, grid_s = 0, grid_l = 0;
+    int grid_s = 0, grid_l = 0;
     int link_spread = 0;
-    int sched_kind = NUM_SCHEDULE_ROWS;  // fused paths: row kernels or merge-path tiles
     int* perm = nullptr;                 // caller's index of the stream at each position
     uint8_t* ut = nullptr;               // utility types, only if some stream has U = -w / x
     int4* chunks = nullptr;              // row kernels: chunks of the long links
@@ -44,8 +41,8 @@ struct num_problem {
     int narrive_l = 0;                   // entries of arrive_l
     void *wt = nullptr, *lo = nullptr, *hi = nullptr, *c = nullptr;
     void *x = nullptr, *Z = nullptr, *pby = nullptr, *zs = nullptr, *Rx = nullptr, *ps = nullptr;
-    void *carry_s = nullptr, *carry_l = nullptr;
-    int *arrive_s = nullptr, *arrive_l = nullptr;
+    void* carry_l = nullptr;   // chunk sums of the long links
+    int* arrive_l = nullptr;   // chunks done per long link
     double *part_s = nullptr, *part_l = nullptr;
     int plain_nb = 0;
     void *A = nullptr, *B = nullptr, *tS = nullptr, *tR = nullptr, *tL = nullptr, *RxN = nullptr,
@@ -127,18 +124,10 @@ View<T> make_view(const num_problem* h) {
     v.n = (int)h->n;
     v.m = (int)h->m;
     v.nnz = (int)h->nnz;
-    v.Js = h->Js;
-    v.Jl = h->Jl;
     v.col_ptr = h->col_ptr;
     v.row_idx = h->row_idx;
     v.row_ptr = h->row_ptr;
     v.col_idx = h->col_idx;
-    v.tiles_s = h->tiles_s;
-    v.tiles_l = h->tiles_l;
-    v.ntiles_s = h->ntiles_s;
-    v.ntiles_l = h->ntiles_l;
-    v.tile_s = h->tile_s;
-    v.tile_l = h->tile_l;
     v.wt = (const T*)h->wt;
     v.lo = (const T*)h->lo;
     v.hi = (const T*)h->hi;
@@ -152,9 +141,7 @@ View<T> make_view(const num_problem* h) {
     v.zs = (T*)h->zs;
     v.Rx = (T*)h->Rx;
     v.ps = (T*)h->ps;
-    v.carry_s = (typename View<T>::T2*)h->carry_s;
     v.carry_l = (T*)h->carry_l;
-    v.arrive_s = h->arrive_s;
     v.arrive_l = h->arrive_l;
     v.part_s = h->part_s;
     v.part_l = h->part_l;

@@ -292,29 +292,6 @@ __global__ void k_find_duplicates(const int* __restrict__ keys, const int* __res
     if (dup) atomicOr(err, VB_DUPLICATE);
 }
 
-// row containing item j of the item space where row r holds items
-// [ptr[r] + r, ptr[r+1] + r] (its entries, then one row-end item)
-__device__ __forceinline__ int row_of_item(const int* ptr, int nrows, int j) {
-    int lo = 0, hi = nrows - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (ptr[mid] + mid <= j)
-            lo = mid;
-        else
-            hi = mid - 1;
-    }
-    return lo;
-}
-
-__global__ void k_tiles(const int* __restrict__ ptr, int nrows, int J, int tile, int ntiles,
-                        int2* tiles) {
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ntiles; t += gridDim.x * blockDim.x) {
-        const long long j0 = (long long)t * tile;
-        const long long j1 = j0 + tile < J ? j0 + tile : J;
-        tiles[t] = make_int2(row_of_item(ptr, nrows, (int)j0), row_of_item(ptr, nrows, (int)(j1 - 1)));
-    }
-}
-
 // ---- stream relabeling: streams ordered by the first link of their route ---------------------
 __global__ void k_first_link(int n, const int64_t* __restrict__ route_ptr,
                              const int* __restrict__ route_links, int* keys, int* vals) {
@@ -642,13 +619,6 @@ cudaError_t relabel_streams(int n, int m, const int64_t* route_ptr, const int* r
     return cudaGetLastError();
 }
 
-cudaError_t build_tiles(const int* ptr, int nrows, int J, int tile, int ntiles, int2* tiles,
-                        cudaStream_t st) {
-    k_tiles<<<blocks_for(ntiles, kThreads, 65535), kThreads, 0, st>>>(ptr, nrows, J, tile, ntiles,
-                                                                      tiles);
-    note_launches(1);
-    return cudaGetLastError();
-}
 
 cudaError_t count_chunks(const int* row_ptr, int m, int* counts, int* offs, int* tmp,
                          int* nchunks, cudaStream_t st) {

@@ -76,14 +76,10 @@ template <typename T>
 struct View {
     using T2 = typename Pair<T>::type;
     int n, m, nnz;
-    int Js, Jl;                 // item counts of the two tiled spaces: nnz + n, nnz + m
     const int* col_ptr;         // CSC [n+1]
     const int* row_idx;         // CSC [nnz] link of each route entry
     const int* row_ptr;         // CSR [m+1]
     const int* col_idx;         // CSR [nnz] stream of each link entry
-    const int2* tiles_s;        // stream-kernel tiles: (first row, last row)
-    const int2* tiles_l;        // link-kernel tiles
-    int ntiles_s, ntiles_l, tile_s, tile_l;
     const T* wt;                // signed weights
     const T* lo;                // per-stream box (unused when box_uniform)
     const T* hi;
@@ -96,10 +92,8 @@ struct View {
     T* zs;
     T* Rx;
     T* ps;
-    T2* carry_s;                // split-row partial sums, 2 per tile
-    T* carry_l;
-    int* arrive_s;              // split-row arrival counters, 1 per tile
-    int* arrive_l;
+    T* carry_l;                 // row kernels: chunk sums of the long links
+    int* arrive_l;              // row kernels: chunks done per long link
     double* part_s;             // per-block residual partials of the stream kernel [grid_s]
     double* part_l;             // ... of the link kernel [2 * grid_l]
     int grid_s, grid_l;
@@ -135,20 +129,11 @@ struct View {
     int tape_len;
 };
 
-// ---- launchers (fused.cu) -------------------------------------------------------------------
-// Tile sizes used by the fused kernels for each precision and kernel.
-int fused_tile_items_stream(int precision);
-int fused_tile_items_link(int precision);
-size_t fused_smem_stream(int precision, int tile);
-size_t fused_smem_link(int precision, int tile);
-// Pick persistent grid sizes (<= ntiles) from the occupancy of each kernel.
-cudaError_t fused_grids(int precision, int tile_s, int tile_l, int ntiles_s, int ntiles_l,
-                        int* grid_s, int* grid_l);
-// One iteration on stream st.  If evs is not NULL, evs[q] is recorded on st right after
-// the q-th kernel of the iteration (for per-kernel timing), as an external event so that
-// it is a real event-record node when the launch is captured into a graph.
-template <typename T>
-cudaError_t fused_iteration(const View<T>& v, cudaStream_t st, cudaEvent_t* evs);
+// ---- launchers ---------------------------------------------------------------------------------
+// One iteration on stream st (rows.cu: the fused FP32 / FP64 kernels; plain.cu: the FP64
+// baseline).  If evs is not NULL, evs[q] is recorded on st right after the q-th kernel of
+// the iteration (for per-kernel timing), as an external event so that it is a real
+// event-record node when the launch is captured into a graph.
 cudaError_t plain_iteration(const View<double>& v, int plain_blocks, cudaStream_t st,
                             cudaEvent_t* evs);
 constexpr int kFusedKernelsPerIter = 2;
@@ -353,10 +338,6 @@ cudaError_t relabel_streams(int n, int m, const int64_t* route_ptr, const int* r
 cudaError_t build_operator(int n, int m, int nnz, const int64_t* route_ptr,
                            const int* route_links, int* col_ptr, int* row_idx, int* row_ptr,
                            int* col_idx, const Scratch& s, int* err_bits, cudaStream_t st);
-// (first row, last row) of every tile of `tile` items over the item space of a pointer
-// array with one extra item per row (J = ptr[nrows] + nrows).
-cudaError_t build_tiles(const int* ptr, int nrows, int J, int tile, int ntiles, int2* tiles,
-                        cudaStream_t st);
 // Convert parameters to the iteration precision (stream arrays in relabeled order).
 template <typename T>
 cudaError_t convert_params(int n, int m, const double* c, const uint8_t* utype,

@@ -1,7 +1,27 @@
-// Row-parallel variant of the two fused kernels of one PMP iteration (same arithmetic as
-// the tile engine in fused.cu; see the derivation there).  On this GPU the iteration is
-// bound by random gathers from L2 (one 32-byte sector per gathered value), so the design
-// goal is to keep as many gathers in flight as possible with no block-wide barriers:
+// The two fused kernels of one PMP iteration (Sec. III-D..G) on one GPU.
+//
+// Per-terminal ADMM collapses to per-stream / per-link state (u is the same on every
+// terminal of a link, z sums to zero over a link, and the log / linear prox of Sec. III-E
+// depend on their argument only through its sum).  With Z_j = sum of z over stream j's
+// terminals, y_l = rho u_l (the unscaled price, so the rescale of Eq. dual-rescale is a
+// no-op), and iteration k using rho_k:
+//
+//   stream kernel (routes, CSC):  A_j = sum_{l in j} pbar_l,  B_j = sum_{l in j} y_l
+//       Z_j  <- alpha |j| x_j + (1 - alpha) Z_j - alpha A_j          (z update, Sec. III-G)
+//       x_j  <- clip( prox_j( Z_j - B_j / rho ) )                     (prox, Sec. III-E)
+//       partial  sum_j |j| (x_j - x_j_prev)^2                         (dual residual)
+//   link kernel (CSR):            Rx_l = sum_{j in l} x_j
+//       ps_l   <- max(zs_l - y_l / rho, -c_l)                         (slack prox)
+//       pbar_l <- (Rx_l + ps_l) / (deg_l + 1)                         (link average)
+//       zs_l   <- alpha (ps_l - pbar_l) + (1 - alpha) zs_l
+//       y_l    <- y_l + alpha rho pbar_l                              (price update)
+//       partials  sum_l (deg_l + 1) pbar_l^2                          (||r||^2)
+//                 sum_l [deg_l dpbar^2 - 2 dpbar dRx + (dps - dpbar)^2]  (rest of ||s||^2/rho^2)
+//   last block of the link kernel: FP64 sums, norms, stopping test, rho update.
+//
+// On this GPU the iteration is bound by random gathers from L2 (one 32-byte sector per
+// gathered value), so the design goal is to keep as many gathers in flight as possible
+// with no block-wide barriers:
 //
 //   stream kernel: one thread per stream; the stream's state is loaded first, then its
 //     route entries four at a time (four independent gathers of (pbar, y) in flight);
@@ -12,9 +32,10 @@
 //     streams are cut into fixed chunks of kChunk (2048) entries, each chunk summed by one
 //     warp (four gathers in flight per lane) into its own slot, and the warp that brings
 //     the row's arrival count to the number of chunks sums the slots in a fixed order and
-//     runs the epilogue (no waiting, deterministic);
+//     runs the epilogue (no waiting, deterministic): the long links' work is cut into
+//     equal pieces, which is what balances the Zipf-skewed link degrees;
 //   the last block of the link kernel finishes the iteration (FP64 residual sums, stopping
-//   test, rho), as in the tile engine.
+//   test, rho).
 // Residual terms are summed in FP64 (per thread, per block, over the grid) in both
 // precisions.
 #include <cooperative_groups.h>

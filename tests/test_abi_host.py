@@ -89,7 +89,7 @@ def test_size_limit_rejected_before_allocation(capi):
 
 @pytest.mark.parametrize("field,value", [("alpha", 2.5), ("rho0", -1.0), ("mu", 0.5),
                                          ("gamma", 0.9), ("precision", 7), ("check_every", 0),
-                                         ("tile_items", 300), ("history", -1),
+                                         ("history", -1),
                                          ("rho_period", -5), ("profile", 3),
                                          ("profile", -1)])
 def test_bad_params(capi, field, value):

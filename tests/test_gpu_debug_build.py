@@ -24,13 +24,13 @@ c1 = W.workload("c1")
 zipf = W.random_instance(20000, 500, 2, 12, seed=5, link_dist="zipf", frac_log=0.6,
                          frac_alpha2=0.2, c_scale=0.1, box=(0.0, 10.0))
 for name, inst in (("c1", c1), ("zipf", zipf)):
-    for prec, sched in ((0, 1), (1, 1), (0, 2), (2, 1)):
-        with capi.Problem(inst, precision=prec, schedule=sched) as p:
+    for prec in (0, 1, 2):
+        with capi.Problem(inst, precision=prec) as p:
             st, it = p.solve(300, 0.0)
             assert st in (0, 1), st
             x, lam, _ = p.get()
-        out[f"{name}_{prec}_{sched}_x"] = x
-        out[f"{name}_{prec}_{sched}_lam"] = lam
+        out[f"{name}_{prec}_x"] = x
+        out[f"{name}_{prec}_lam"] = lam
 with capi.Batch([c1, zipf], precision=0) as b:
     rc, it, stt = b.solve(300, 0.0)
     xs, ps, _ = b.get()

@@ -4,9 +4,8 @@ than 32 links), link distribution (uniform or Zipf), utility mix (log, linear, a
 box (uniform, per stream, or fixed rates), rho0, alpha, the rho update period and the
 iteration count.
 
-- Single instances: one kernel path per example (FP64 rows, FP64 tiles with a random tile
-  size, plain FP64, FP32 rows on the oracle's rho decisions), compared after the same
-  number of iterations.
+- Single instances: one kernel path per example (FP64 fused, plain FP64, FP32 fused on
+  the oracle's rho decisions), compared after the same number of iterations.
 - Batches: 1 to 8 such instances in one batch with a random work partition, in FP64 (with
   a stopping tolerance half of the time: every instance must stop at the oracle's
   iteration) or in FP32 on the oracle's decisions.
@@ -103,28 +102,24 @@ def cases(draw):
     inst = draw(instances())
     params = solver_params(draw)
     iters = draw(st.integers(1, 260))
-    path = draw(st.sampled_from(["fp64_rows", "fp64_tiles", "plain", "fp32_rows"]))
-    tile = draw(st.sampled_from([256, 512, 2048]))
-    return inst, params, iters, path, tile
+    path = draw(st.sampled_from(["fp64_rows", "plain", "fp32_rows"]))
+    return inst, params, iters, path
 
 
 @settings(max_examples=150, **FUZZ)
 @given(cases())
 def test_random_instances_match_oracle(case):
-    inst, params, iters, path, tile = case
+    inst, params, iters, path = case
     ref = oracle_run(inst, iters, **params)
     kw = gpu_params(params)
     if path == "fp64_rows":
-        g = run_gpu(inst, iters, "fp64", schedule=1, **kw)
-        tol = 1e-9
-    elif path == "fp64_tiles":
-        g = run_gpu(inst, iters, "fp64", schedule=2, tile_items=tile, **kw)
+        g = run_gpu(inst, iters, "fp64", **kw)
         tol = 1e-9
     elif path == "plain":
         g = run_gpu(inst, iters, "plain", **kw)
         tol = 1e-9
     else:
-        g = run_gpu(inst, iters, "fp32", schedule=1, schedule_decisions=ref["decisions"], **kw)
+        g = run_gpu(inst, iters, "fp32", schedule_decisions=ref["decisions"], **kw)
         tol = 1e-4
     assert g["iters"] == iters
     assert rel(g["x"], ref["x"]) <= tol, (path, rel(g["x"], ref["x"]))
@@ -269,10 +264,10 @@ def test_random_many_link_instances_match_oracle(case):
     inst, iters, path = case
     ref = oracle_run(inst, iters)
     if path == "fp64_rows":
-        g = run_gpu(inst, iters, "fp64", schedule=1)
+        g = run_gpu(inst, iters, "fp64")
         tol = 1e-9
     else:
-        g = run_gpu(inst, iters, "fp32", schedule=1, schedule_decisions=ref["decisions"])
+        g = run_gpu(inst, iters, "fp32", schedule_decisions=ref["decisions"])
         tol = 1e-4
     assert rel(g["x"], ref["x"]) <= tol, (path, rel(g["x"], ref["x"]))
     err = price_err(g["lam"], ref["lam"], inst)

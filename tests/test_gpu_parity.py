@@ -33,12 +33,11 @@ def _check_hist(gh, oh, rtol):
     assert np.allclose(gh[:, :2], oh[:, :2], rtol=rtol, atol=rtol * 1e-3 * scale)
 
 
-@pytest.mark.parametrize("precision,schedule,reorder", [("fp64", 1, 1), ("fp64", 2, 1),
-                                                        ("plain", 0, 1), ("fp64", 1, 0)])
+@pytest.mark.parametrize("precision,reorder", [("fp64", 1), ("plain", 1), ("fp64", 0)])
 @pytest.mark.parametrize("iters", [1, 7, 50, 51, 300, 2000])
-def test_c1_fp64_paths_match_oracle(c1, c1_oracle, precision, schedule, reorder, iters):
+def test_c1_fp64_paths_match_oracle(c1, c1_oracle, precision, reorder, iters):
     ref = c1_oracle[iters]
-    g = run_gpu(c1, iters, precision, schedule=schedule, reorder=reorder)
+    g = run_gpu(c1, iters, precision, reorder=reorder)
     assert g["iters"] == iters
     e = compare(g, ref, FP64_TOL)
     assert e["x"] <= FP64_TOL and e["lam"] <= FP64_TOL, e
@@ -84,20 +83,20 @@ def test_stopping_iteration_matches_oracle(c1, precision):
     assert g["info"]["primal"] < g["info"]["eps_tol"] and g["info"]["dual"] < g["info"]["eps_tol"]
 
 
-# ---- ragged shapes, tile splitting, skew, degenerate rows ------------------------------------
+# ---- ragged shapes, skew, degenerate rows -------------------------------------------------------
 
 def _cases():
     yield "one_stream_one_link", W.random_instance(1, 1, 1, 1, seed=1), {}
     yield "tiny", W.random_instance(37, 11, 1, 6, seed=2), {}
     yield "links_without_streams", W.random_instance(40, 400, 1, 3, seed=3), {}
-    yield "split_rows_small_tiles", W.random_instance(5000, 300, 1, 8, seed=4), dict(tile_items=256)
-    yield "zipf_hot_rows_many_tiles", W.random_instance(
+    yield "dense_links", W.random_instance(5000, 300, 1, 8, seed=4), {}
+    yield "zipf_hot_links", W.random_instance(
         20000, 500, 2, 12, seed=5, link_dist="zipf", frac_log=1.0, c_scale=0.1,
-        w_dist="lognormal", box=(0.0, 10.0)), dict(tile_items=256)
-    yield "zipf_default_tiles", W.random_instance(
+        w_dist="lognormal", box=(0.0, 10.0)), {}
+    yield "zipf_chunked_links", W.random_instance(
         60000, 2000, 2, 12, seed=6, link_dist="zipf", frac_log=1.0, c_scale=0.1,
         w_dist="lognormal", box=(0.0, 10.0)), {}
-    yield "long_routes", W.random_instance(300, 200, 60, 150, seed=7), dict(tile_items=512)
+    yield "long_routes", W.random_instance(300, 200, 60, 150, seed=7), {}
 
     def mix_long(seed):
         """Short routes (1..6 links) with 2% of the streams on 33..400 links: the row stream
@@ -113,7 +112,7 @@ def _cases():
         rl = np.concatenate([rng.choice(m, size=int(k), replace=False) for k in lens])
         return dict(short, route_ptr=rp, route_links=rl.astype(np.int32))
     yield "mixed_long_routes", mix_long(13), {}
-    yield "ragged_tail", W.random_instance(4097, 1025, 1, 10, seed=8), dict(tile_items=1024)
+    yield "ragged_tail", W.random_instance(4097, 1025, 1, 10, seed=8), {}
     yield "all_linear", W.random_instance(2000, 300, 1, 6, seed=9, frac_log=0.0), {}
     yield "alpha2_mixed", W.random_instance(3000, 400, 1, 6, seed=12, frac_log=0.4,
                                             frac_alpha2=0.4), {}
@@ -137,29 +136,22 @@ def _cases():
 CASES = list(_cases())
 
 
-SCHED = {"rows": 1, "tiles": 2}
-
-
 @pytest.mark.parametrize("name,inst,params", CASES, ids=[c[0] for c in CASES])
-@pytest.mark.parametrize("precision,schedule,reorder", [("fp64", "rows", 1), ("fp64", "tiles", 1),
-                                                        ("plain", "rows", 1),
-                                                        ("fp64", "rows", 0)])
-def test_shapes_fp64_match_oracle(name, inst, params, precision, schedule, reorder):
+@pytest.mark.parametrize("precision,reorder", [("fp64", 1), ("plain", 1), ("fp64", 0)])
+def test_shapes_fp64_match_oracle(name, inst, params, precision, reorder):
     iters = 200
     ref = oracle_run(inst, iters)
-    g = run_gpu(inst, iters, precision, schedule=SCHED[schedule], reorder=reorder, **params)
+    g = run_gpu(inst, iters, precision, reorder=reorder, **params)
     e = compare(g, ref, FP64_TOL)
     assert e["x"] <= FP64_TOL and e["lam"] <= FP64_TOL, e
     assert e["x_el"] <= 1e-9 and e["lam_el"] <= 1e-9, e
 
 
 @pytest.mark.parametrize("name,inst,params", CASES, ids=[c[0] for c in CASES])
-@pytest.mark.parametrize("schedule", ["rows", "tiles"])
-def test_shapes_fp32_match_oracle(name, inst, params, schedule):
+def test_shapes_fp32_match_oracle(name, inst, params):
     iters = 200
     ref = oracle_run(inst, iters)
-    g = run_gpu(inst, iters, "fp32", schedule_decisions=ref["decisions"],
-                schedule=SCHED[schedule], **params)
+    g = run_gpu(inst, iters, "fp32", schedule_decisions=ref["decisions"], **params)
     e = compare(g, ref, FP32_TOL)
     assert e["x"] <= FP32_TOL and e["lam"] <= FP32_TOL, e
 
@@ -176,12 +168,11 @@ def test_operator_is_bit_exact(name, inst, params, reorder):
 
 # ---- determinism, graph vs launches, device inputs ----------------------------------------------
 
-@pytest.mark.parametrize("schedule", [1, 2])
-def test_runs_are_bit_identical(c1, schedule):
-    a = run_gpu(c1, 500, "fp32", schedule=schedule)
-    b = run_gpu(c1, 500, "fp32", schedule=schedule)
-    c = run_gpu(c1, 500, "fp32", use_graph=0, schedule=schedule)
-    d = run_gpu(c1, 500, "fp32", check_every=7, schedule=schedule)
+def test_runs_are_bit_identical(c1):
+    a = run_gpu(c1, 500, "fp32")
+    b = run_gpu(c1, 500, "fp32")
+    c = run_gpu(c1, 500, "fp32", use_graph=0)
+    d = run_gpu(c1, 500, "fp32", check_every=7)
     for other in (b, c, d):
         assert np.array_equal(a["x"], other["x"]) and np.array_equal(a["lam"], other["lam"])
 
@@ -313,14 +304,14 @@ def test_sampled_profile_batch(c1):
     assert list(runs) == [10, 10] and np.all(ms > 0)
 
 
-@pytest.mark.parametrize("precision,schedule,nk", [(0, 1, 2), (1, 2, 2), (2, 1, 8)])
-def test_profile_without_graphs(c1, precision, schedule, nk):
+@pytest.mark.parametrize("precision,nk", [(0, 2), (1, 2), (2, 8)])
+def test_profile_without_graphs(c1, precision, nk):
     """Per-kernel times with plain launches (use_graph = 0): the events are recorded on the
     stream directly rather than as graph nodes, and the iterates equal the graph path's."""
     from paper_2509_10722_b300 import capi
     out = []
     for g in (0, 1):
-        with capi.Problem(c1, precision=precision, schedule=schedule, profile=1,
+        with capi.Problem(c1, precision=precision, profile=1,
                           use_graph=g, check_every=10) as p:
             status, done = p.solve(40, 0.0)
             ms, runs = p.kernel_times()
