@@ -357,6 +357,33 @@ def timed(solver, torch, steps):
 
 # ---- arms --------------------------------------------------------------------------------------------
 
+GOLDEN_C2 = os.path.join(ROOT, "tests", "golden", "c2_oracle_record")
+
+
+def error_vs_oracle(x, lam, objective, iters):
+    """A c2 result against the FP64 oracle's own run of the same instance to the same
+    tolerance (the record in tests/golden, written by tests/golden/make_c2_record.py with
+    the oracle alone): the seeded samples of rates and prices, the objective and the
+    stopping iteration.  None if the record is absent."""
+    if not (os.path.exists(GOLDEN_C2 + ".json") and os.path.exists(GOLDEN_C2 + ".npz")):
+        return None
+    rec = json.load(open(GOLDEN_C2 + ".json"))
+    z = np.load(GOLDEN_C2 + ".npz")
+    out = {}
+    for name, got, idx, ref in (("x", x, z["x_idx"], z["x"]), ("prices", lam, z["lam_idx"], z["lam"])):
+        d = np.asarray(got, dtype=np.float64)[idx] - ref
+        scale = np.maximum(np.abs(ref), 1e-3 * np.max(np.abs(ref)))
+        out[f"{name}_rel"] = float(np.linalg.norm(d) / np.linalg.norm(ref))
+        out[f"{name}_el_max"] = float(np.max(np.abs(d) / scale))
+    out["objective_rel"] = abs(objective - rec["objective"]) / abs(rec["objective"])
+    out["iters"] = int(iters)
+    out["oracle_iters"] = int(rec["iters"])
+    out["sample"] = (f"{len(z['x_idx'])} stream rates and {len(z['lam_idx'])} prices at seeded "
+                     f"positions; elementwise errors floored at 1e-3 of the largest value")
+    out["record"] = "tests/golden/c2_oracle_record.json"
+    return out
+
+
 def workload_config(args, n, m, nnz):
     """The workload of a line, the same in both arms (what is run, not how)."""
     return {"workload": f"{args.workload}: {WORKLOAD_TEXT[args.workload]}",
@@ -478,6 +505,8 @@ def run_ours(args, dist):
     info = infos[-1][2]
     x32 = fp32.x.double().cpu().numpy()
     p32 = fp32.p.double().cpu().numpy()
+    ev_oracle = (error_vs_oracle(x32, p32, info["objective"], it_per_solve[-1])
+                 if args.workload == "c2" and args.scale is None and dist.rank == 0 else None)
 
     # per-kernel device times measured by events inside the timed solves
     kms, kruns = fp32.kernel_ms, fp32.kernel_runs
@@ -527,6 +556,7 @@ def run_ours(args, dist):
                 "solve (num_solve to the stopping test)": float(fp32.phase_ms[1] / args.steps),
                 "get (FP64 export, objective)": float(fp32.phase_ms[2] / args.steps)},
             "iters_to_tol": it_per_solve[-1], "converged": all(s == 0 for s in statuses),
+            "error_vs_oracle": ev_oracle,
             "final_residuals": {"primal": info["primal"], "dual": info["dual"],
                                 "eps_tol": info["eps_tol"]},
             "objective": info["objective"],

@@ -332,6 +332,13 @@ NUM_API int num_objective_noalloc(int64_t n, const double* x, const uint8_t* uty
 NUM_API int num_measure_gather_rate(int64_t count, int64_t vec_len, int32_t vec_bytes,
                                     int32_t repeats, double* gathers_per_s);
 
+/* As num_measure_gather_rate, with plain stores of 4- or 8-byte values to the random
+ * positions instead of reads: the rate at which a kernel could push each value to a
+ * permuted copy (to be read back contiguously) instead of gathering it.  Written to the
+ * HOST double *stores_per_s.  The paper has no counterpart; it is a measurement service. */
+NUM_API int num_measure_scatter_rate(int64_t count, int64_t vec_len, int32_t vec_bytes,
+                                     int32_t repeats, double* stores_per_s);
+
 /* Free every resource of the handle.  NULL is ignored. */
 NUM_API void num_destroy(num_problem* h);
 

@@ -115,6 +115,7 @@ def _load():
         "num_kernel_launches": (ctypes.c_int64, []),
         "num_objective_noalloc": (ctypes.c_int, [i64, P, P, P, P, P]),
         "num_measure_gather_rate": (ctypes.c_int, [i64, i64, i32, i32, ctypes.POINTER(d)]),
+        "num_measure_scatter_rate": (ctypes.c_int, [i64, i64, i32, i32, ctypes.POINTER(d)]),
         "num_batch_create": (ctypes.c_int, [ctypes.POINTER(P), i32, P, P, P, P, P, P, P, P, P,
                                             pp, P]),
         "num_batch_create_instances": (ctypes.c_int, [ctypes.POINTER(P), i32,
@@ -149,7 +150,8 @@ EXPORTED = ("num_default_params", "num_create", "num_create_device", "num_set_rh
             "num_set_capacity_device", "num_set_weights_device",
             "num_get_state", "num_set_state",
             "num_iteration_bytes", "num_get_kernel_times", "num_kernel_launches",
-            "num_objective_noalloc", "num_measure_gather_rate", "num_destroy", "num_strerror",
+            "num_objective_noalloc", "num_measure_gather_rate", "num_measure_scatter_rate",
+            "num_destroy", "num_strerror",
             "num_last_error",
             "num_batch_create", "num_batch_create_instances", "num_batch_set_rho_schedules",
             "num_batch_solve",
@@ -409,6 +411,14 @@ def num_measure_gather_rate(count, vec_len, vec_bytes, repeats=5):
     out = ctypes.c_double(0.0)
     _check(_lib.num_measure_gather_rate(int(count), int(vec_len), int(vec_bytes), int(repeats),
                                         ctypes.byref(out)))
+    return out.value
+
+
+def num_measure_scatter_rate(count, vec_len, vec_bytes, repeats=5):
+    """Uniformly random 4- or 8-byte stores per second to a vector of vec_len elements."""
+    out = ctypes.c_double(0.0)
+    _check(_lib.num_measure_scatter_rate(int(count), int(vec_len), int(vec_bytes),
+                                         int(repeats), ctypes.byref(out)))
     return out.value
 
 

@@ -6,7 +6,9 @@
 // vector that lives in L2, one 32-byte sector each, and their rate, not HBM bandwidth,
 // bounds the iteration.  This file measures that rate on the GPU at hand: `count` uniformly
 // random 4- or 8-byte reads from a vector of `vec_len` elements, four reads in flight per
-// thread at full occupancy, timed with CUDA events.  The paper has no counterpart; it is a
+// thread at full occupancy, timed with CUDA events.  The same with plain stores to random
+// positions (num_measure_scatter_rate) measures the alternative of pushing each value to
+// a permuted copy and reading that contiguously.  The paper has no counterpart; it is a
 // measurement service for reporting the kernels against the ceiling that bounds them.
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -63,6 +65,23 @@ k_gather(const int* __restrict__ idx, long long count, const V* __restrict__ v, 
     if (s == -1.f) *sink = s;
 }
 
+// each thread writes four independent values per round to uniformly random positions
+template <typename V>
+__global__ void __launch_bounds__(kThreads)
+k_scatter(const int* __restrict__ idx, long long count, V* __restrict__ v) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    for (; i + 3 * stride < count; i += 4 * stride) {
+        const int j0 = __ldg(idx + i), j1 = __ldg(idx + i + stride);
+        const int j2 = __ldg(idx + i + 2 * stride), j3 = __ldg(idx + i + 3 * stride);
+        v[j0] = V{};
+        v[j1] = V{};
+        v[j2] = V{};
+        v[j3] = V{};
+    }
+    for (; i < count; i += stride) v[__ldg(idx + i)] = V{};
+}
+
 struct Buffers {
     int* idx = nullptr;
     void* vec = nullptr;
@@ -89,7 +108,7 @@ int fail(cudaError_t e, const char* what) {
 }
 
 template <typename V>
-int measure(long long count, long long len, int repeats, double* rate) {
+int measure(long long count, long long len, int repeats, double* rate, bool stores) {
     Buffers b;
     cudaError_t e;
     int dev = 0, sms = 0;
@@ -111,10 +130,15 @@ int measure(long long count, long long len, int repeats, double* rate) {
     k_fill<V><<<fill_grid, kThreads, 0, b.st>>>((V*)b.vec, len);
     // full occupancy: 2048 resident threads per SM
     const int grid = sms * (2048 / kThreads);
-    k_gather<V><<<grid, kThreads, 0, b.st>>>(b.idx, count, (const V*)b.vec, b.sink);  // warm-up
+    auto pass = [&]() {
+        if (stores)
+            k_scatter<V><<<grid, kThreads, 0, b.st>>>(b.idx, count, (V*)b.vec);
+        else
+            k_gather<V><<<grid, kThreads, 0, b.st>>>(b.idx, count, (const V*)b.vec, b.sink);
+    };
+    pass();  // warm-up
     cudaEventRecord(b.e0, b.st);
-    for (int r = 0; r < repeats; ++r)
-        k_gather<V><<<grid, kThreads, 0, b.st>>>(b.idx, count, (const V*)b.vec, b.sink);
+    for (int r = 0; r < repeats; ++r) pass();
     cudaEventRecord(b.e1, b.st);
     pmp::note_launches(3 + repeats);
     if ((e = cudaGetLastError()) != cudaSuccess) return fail(e, "launching the gather kernels");
@@ -129,9 +153,11 @@ int measure(long long count, long long len, int repeats, double* rate) {
 
 }  // namespace
 
-extern "C" int num_measure_gather_rate(int64_t count, int64_t vec_len, int32_t vec_bytes,
-                                       int32_t repeats, double* gathers_per_s) {
-    if (!gathers_per_s) return pmp::report_error(NUM_ERR_INVALID, "gathers_per_s is NULL");
+namespace {
+
+int measure_rate(int64_t count, int64_t vec_len, int32_t vec_bytes, int32_t repeats,
+                 double* rate, bool stores) {
+    if (!rate) return pmp::report_error(NUM_ERR_INVALID, "the result pointer is NULL");
     if (count < 1 || count > 2000000000LL)
         return pmp::report_error(NUM_ERR_INVALID, "count must be in [1, 2e9]");
     if (vec_len < 1 || vec_len > 2147483647LL)
@@ -140,8 +166,20 @@ extern "C" int num_measure_gather_rate(int64_t count, int64_t vec_len, int32_t v
         return pmp::report_error(NUM_ERR_INVALID, "vec_bytes must be 4 or 8");
     if (repeats < 1 || repeats > 1000)
         return pmp::report_error(NUM_ERR_INVALID, "repeats must be in [1, 1000]");
-    const int rc = vec_bytes == 4 ? measure<float>(count, vec_len, repeats, gathers_per_s)
-                                  : measure<float2>(count, vec_len, repeats, gathers_per_s);
+    const int rc = vec_bytes == 4 ? measure<float>(count, vec_len, repeats, rate, stores)
+                                  : measure<float2>(count, vec_len, repeats, rate, stores);
     if (rc == NUM_OK) pmp::clear_error();
     return rc;
+}
+
+}  // namespace
+
+extern "C" int num_measure_gather_rate(int64_t count, int64_t vec_len, int32_t vec_bytes,
+                                       int32_t repeats, double* gathers_per_s) {
+    return measure_rate(count, vec_len, vec_bytes, repeats, gathers_per_s, false);
+}
+
+extern "C" int num_measure_scatter_rate(int64_t count, int64_t vec_len, int32_t vec_bytes,
+                                        int32_t repeats, double* stores_per_s) {
+    return measure_rate(count, vec_len, vec_bytes, repeats, stores_per_s, true);
 }
