@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--eps", type=float, default=1e-4)
     ap.add_argument("--max-iters", type=int, default=50_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-reorder", action="store_true",
+                    help="keep the caller's stream order (measures the first-link ordering)")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-iters", type=int, default=3)
@@ -293,14 +295,15 @@ def pinned_copy(inst, torch):
 class Solver:
     """One whole solve per call, on a fixed torch stream, inputs resident on the device."""
 
-    def __init__(self, capi, torch, dev_inst, n, m, precision, eps, max_iters, stream):
+    def __init__(self, capi, torch, dev_inst, n, m, precision, eps, max_iters, stream,
+                 reorder=1):
         self.capi, self.torch = capi, torch
         self.d = dev_inst
         self.n, self.m = n, m
         self.eps, self.max_iters = eps, max_iters
         self.stream = stream
         self.alloc = capi.torch_allocator()
-        self.params = capi.num_default_params(precision=precision, profile=2,
+        self.params = capi.num_default_params(precision=precision, profile=2, reorder=reorder,
                                               allocator=ctypes.pointer(self.alloc))
         self.x = torch.empty(n, dtype=torch.float64, device="cuda")
         self.p = torch.empty(m, dtype=torch.float64, device="cuda")
@@ -482,7 +485,8 @@ def run_ours(args, dist):
     n, m, nnz = inst["n"], inst["m"], int(inst["route_ptr"][-1])
     dev = to_device(inst, torch)
     stream = torch.cuda.Stream()
-    fp32 = Solver(capi, torch, dev, n, m, PRECISION["fp32"], args.eps, args.max_iters, stream)
+    fp32 = Solver(capi, torch, dev, n, m, PRECISION["fp32"], args.eps, args.max_iters, stream,
+                  reorder=0 if args.no_reorder else 1)
     for _ in range(args.warmup):
         fp32.step()
     fp32.reset_kernel_times()
