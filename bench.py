@@ -721,7 +721,7 @@ def run_batched(args):
     n_tot = int(sum(t["n"] for t in insts))
     m_tot = int(sum(t["m"] for t in insts))
     nnz_tot = int(sum(int(t["route_ptr"][-1]) for t in insts))
-    st1, st2 = trials[:5], trials[5:]
+    st1, st2 = trials[:6], trials[6:]
     # Both kernels against their ceilings.  The sampled launches spread over the whole run,
     # tail included, where few instances still run; so the work of an average launch is
     # each instance's work weighted by its iterations, over the launches of the run.

@@ -391,16 +391,19 @@ NUM_API int num_batch_create_instances(num_batch** out, int32_t count, const num
  * decision of instance i at its q-th update point (-1, 0, +1; host array, copied). */
 NUM_API int num_batch_set_rho_schedules(num_batch* b, const int8_t* decisions, int64_t len);
 
-/* Work partition of a batch's two kernels.  Every instance's streams are cut into work
- * items of stream_item consecutive streams and its links into items of link_item
- * consecutive links; a block takes one item at a time; in the link kernel link_lanes
- * lanes sum R x of one link.  The default is {2048, 256, 8}.  The partition does not
- * change the arithmetic of a stream or a link, except that link_lanes fixes the order of
- * the additions of (R x)_l; the residual norms are summed per item, so their last bits
- * follow the partition as well. */
+/* Work partition of a batch's two kernels.  stream_item = 0 (balanced): the stacked
+ * streams are cut into one range of equal length per resident block of the stream
+ * kernel, and each range again where an instance ends; otherwise every instance's
+ * streams are cut into work items of stream_item consecutive streams, which the blocks
+ * take in turn.  link_item likewise for the links, where a balanced range holds an equal
+ * share of route entries (plus a fixed weight per link for its epilogue).  In the link
+ * kernel link_lanes lanes sum R x of one link.  The default is {0, 0, 8}.  The partition
+ * does not change the arithmetic of a stream or a link, except that link_lanes fixes the
+ * order of the additions of (R x)_l; the residual norms are summed per item, so their
+ * last bits follow the partition as well. */
 typedef struct {
-    int32_t stream_item; /* power of two in [256, 65536] */
-    int32_t link_item;   /* power of two in [32, 8192] */
+    int32_t stream_item; /* 0, or a power of two in [256, 65536] */
+    int32_t link_item;   /* 0, or a power of two in [32, 8192] */
     int32_t link_lanes;  /* 4, 8, 16 or 32 */
 } num_batch_schedule;
 
@@ -412,9 +415,9 @@ NUM_API int num_batch_get_schedule(const num_batch* b, num_batch_schedule* out);
 NUM_API int num_batch_set_schedule(num_batch* b, const num_batch_schedule* s);
 
 /* Autotuner of the partition: times candidate partitions on this batch and keeps the
- * fastest.  Stage 1 tries stream_item in {512, 1024, 2048, 4096, 8192} with the link side
- * unchanged and keeps the one with the least stream-kernel time; stage 2 tries link_item
- * in {64, 128, 256, 512, 1024} times link_lanes in {4, 8, 16, 32} and keeps the least
+ * fastest.  Stage 1 tries stream_item in {0, 512, 1024, 2048, 4096, 8192} with the link
+ * side unchanged and keeps the one with the least stream-kernel time; stage 2 tries
+ * link_item in {0, 64, 128, 256, 512, 1024} times link_lanes in {4, 8, 16, 32} and keeps the least
  * link-kernel time (ties: the earlier candidate).  Each candidate runs 2 untimed and
  * trial_iters (1 .. 500) timed iterations of every instance without a stopping test;
  * kernel times are CUDA events around each kernel.  Afterwards the chosen partition is in
@@ -423,7 +426,7 @@ NUM_API int num_batch_set_schedule(num_batch* b, const num_batch_schedule* s);
  * NULL) receives the partition.  trial_ms (HOST, 4 * max_trials doubles, may be NULL with
  * max_trials = 0) receives, per candidate in the order tried, (stream_item, link_item,
  * link_lanes, milliseconds of the kernel that stage compares); *ntrials (may be NULL) the
- * number of candidates tried (25).  Synchronizes the stream.  The choice follows measured
+ * number of candidates tried (30).  Synchronizes the stream.  The choice follows measured
  * times, so two calls can choose differently, and with a different link_lanes the
  * results differ in the last bits (see num_batch_schedule); pass the chosen partition to
  * num_batch_set_schedule to reproduce a run. */

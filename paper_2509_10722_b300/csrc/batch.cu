@@ -14,10 +14,11 @@
 //     order by the whole block, norms, stopping test, rho; an instance that stops takes
 //     itself off the count of running instances (the host stops replaying at zero).
 //     Instances are finished as their items complete, in parallel with the rest.
-// The work partition (streams per stream item, links per link item, lanes per link) is a
-// runtime schedule, chosen by the caller or by the autotuner in api.cu; the arithmetic of
-// a stream or a link does not depend on it except through the lanes per link, which fix
-// the order of the additions of R x.
+// The work partition (fixed-size items taken by the blocks in turn, or balanced: one
+// contiguous range of streams / of link entries per block, cut at instance boundaries;
+// lanes per link) is a runtime schedule, chosen by the caller or by the autotuner in
+// batch_api.cu; the arithmetic of a stream or a link does not depend on it except through
+// the lanes per link, which fix the order of the additions of R x.
 // No block waits on another; sums are in a fixed order, so runs are deterministic.
 #include <algorithm>
 
@@ -45,7 +46,13 @@ __global__ void __launch_bounds__(kTh) k_stream_batch(BatchView<T> b) {
     __shared__ double red[kWarps];
     if (b.glob->running == 0) return;
     const View<T>& v = b.v;
-    for (int it = blockIdx.x; it < b.nsitems; it += gridDim.x) {
+    int it0 = blockIdx.x, it1 = b.nsitems, step = gridDim.x;  // items in turn, or
+    if (b.sblk) {                                            // this block's range
+        it0 = __ldg(b.sblk + blockIdx.x);
+        it1 = __ldg(b.sblk + blockIdx.x + 1);
+        step = 1;
+    }
+    for (int it = it0; it < it1; it += step) {
         const int4 item = __ldg(b.sitems + it);
         const Ctl* c = b.ctls + item.x;
         if (c->stop) continue;  // block-uniform
@@ -137,7 +144,13 @@ __global__ void __launch_bounds__(kTh) k_link_batch(BatchView<T> b) {
     const bool leader = g.thread_rank() == 0;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     constexpr int kGroups = kTh / G;
-    for (int it = blockIdx.x; it < b.nlitems; it += gridDim.x) {
+    int it0 = blockIdx.x, it1 = b.nlitems, step = gridDim.x;  // items in turn, or
+    if (b.lblk) {                                            // this block's range
+        it0 = __ldg(b.lblk + blockIdx.x);
+        it1 = __ldg(b.lblk + blockIdx.x + 1);
+        step = 1;
+    }
+    for (int it = it0; it < it1; it += step) {
         const int4 item = __ldg(b.litems + it);
         const Ctl* c = b.ctls + item.x;
         if (c->stop) continue;  // block-uniform
@@ -370,6 +383,21 @@ int blocks_for(long long count) {
 }
 
 }  // namespace
+
+cudaError_t batch_resident(int precision, int lanes, int* blocks_s, int* blocks_l) {
+    int dev = 0, sms = 0, os = 0, ol = 0, oe = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    e = precision == 0 ? batch_occupancy<float>(lanes, &os, &ol, &oe)
+                       : batch_occupancy<double>(lanes, &os, &ol, &oe);
+    if (e != cudaSuccess) return e;
+    if (os < 1 || ol < 1) return cudaErrorInvalidConfiguration;
+    *blocks_s = os * sms;
+    *blocks_l = ol * sms;
+    return cudaSuccess;
+}
 
 cudaError_t batch_grids(int precision, int lanes, int nsitems, int nlitems, int nchunks,
                         int* grid_s, int* grid_l, int* grid_e) {

@@ -62,23 +62,31 @@ struct num_batch {
     double* part_t = nullptr;          // [3 cap_teams] per-block residual partials
     int cap_teams = 0;
     int grid_p = 0;                    // blocks of the current team plan
+    // balanced partitions (stream_item / link_item = 0): each block's item range
+    int* sblk = nullptr;               // [kMaxBalancedBlocks + 1]
+    int* lblk = nullptr;
+    bool sbal = false, lbal = false;
+    std::vector<int> link_deg;         // entries of each link (host copy, for the weights)
 };
 
 namespace {
 
 // Work partition of a batch: defaults, limits and the autotuner's candidates.
-constexpr num_batch_schedule kBatchDefault = {2048, 256, 8};
+constexpr num_batch_schedule kBatchDefault = {0, 0, 8};  // balanced ranges, 8 lanes
+constexpr int kMaxBalancedBlocks = 4096;  // above any resident grid of the batch kernels
+constexpr int kBalancedMinWork = 256;     // streams (or link entries) per block at least
+constexpr int kLinkEpilogueWeight = 4;    // a link's epilogue, in route entries
 constexpr int kStreamItemMin = 256, kStreamItemMax = 65536;
 constexpr int kLinkItemMin = 32, kLinkItemMax = 8192;
-constexpr int kTuneStreamItems[] = {512, 1024, 2048, 4096, 8192};
-constexpr int kTuneLinkItems[] = {64, 128, 256, 512, 1024};
+constexpr int kTuneStreamItems[] = {0, 512, 1024, 2048, 4096, 8192};  // 0: balanced
+constexpr int kTuneLinkItems[] = {0, 64, 128, 256, 512, 1024};
 constexpr int kTuneLanes[] = {4, 8, 16, 32};
 
 bool pow2_in(int v, int lo, int hi) { return v >= lo && v <= hi && (v & (v - 1)) == 0; }
 
 bool valid_schedule(const num_batch_schedule& c) {
-    return pow2_in(c.stream_item, kStreamItemMin, kStreamItemMax) &&
-           pow2_in(c.link_item, kLinkItemMin, kLinkItemMax) &&
+    return (c.stream_item == 0 || pow2_in(c.stream_item, kStreamItemMin, kStreamItemMax)) &&
+           (c.link_item == 0 || pow2_in(c.link_item, kLinkItemMin, kLinkItemMax)) &&
            (c.link_lanes == 4 || c.link_lanes == 8 || c.link_lanes == 16 || c.link_lanes == 32);
 }
 
@@ -95,6 +103,8 @@ pmp::BatchView<T> make_batch_view(const num_batch* b) {
     v.nlitems = b->nlitems;
     v.sitem_off = b->sitem_off;
     v.litem_off = b->litem_off;
+    v.sblk = b->sbal ? b->sblk : nullptr;
+    v.lblk = b->lbal ? b->lblk : nullptr;
     v.count = b->count;
     v.part_s = b->part_s;
     v.part_l = b->part_l;
@@ -166,29 +176,117 @@ int batch_reset_all(num_batch* b) {
     return NUM_OK;
 }
 
+// Cut the rows [0, off[count]) into `blocks` consecutive ranges of equal weight and each
+// range again at instance boundaries (off): items (instance, first row, end row) in row
+// order, blk[b] = first item of block b.  pre (prefix sums of the row weights, pre[r] =
+// weight of the rows before r) may be NULL for unit weights.
+void balanced_items(const std::vector<int64_t>& off, const std::vector<double>* pre,
+                    int blocks, std::vector<int4>& items, std::vector<int>& blk) {
+    const int count = (int)off.size() - 1;
+    const int64_t rows = off[count];
+    const double W = pre ? (*pre)[rows] : (double)rows;
+    items.clear();
+    blk.assign((size_t)blocks + 1, 0);
+    int64_t r = 0;
+    int inst = 0;
+    for (int q = 0; q < blocks; ++q) {
+        blk[q] = (int)items.size();
+        // the first row whose prefix weight reaches the block's share
+        const double target = W * (double)(q + 1) / (double)blocks;
+        int64_t end;
+        if (q == blocks - 1)
+            end = rows;
+        else if (pre)
+            end = (int64_t)(std::lower_bound(pre->begin() + r, pre->begin() + rows + 1, target) -
+                            pre->begin());
+        else
+            end = (int64_t)std::ceil(target);
+        end = std::min<int64_t>(std::max<int64_t>(end, r), rows);
+        while (r < end) {
+            while (off[inst + 1] <= r) ++inst;
+            const int64_t cut = std::min<int64_t>(end, off[inst + 1]);
+            items.push_back(make_int4(inst, (int)r, (int)cut, 0));
+            r = cut;
+        }
+    }
+    blk[blocks] = (int)items.size();
+}
+
 // Build the work items of schedule `cfg` (instance, first row, end row) and size the grids;
 // a captured graph of the old partition is dropped.  Streams keep their instance's range
 // after the first-link ordering because an instance's links are a contiguous id range.
+// stream_item / link_item = 0: balanced, one range of equal work per block (streams; link
+// entries plus an epilogue weight per link, chunked links counting their epilogue only).
 int batch_apply_schedule(num_batch* b, const num_batch_schedule& cfg) {
     num_problem* h = b->p;
     cudaStream_t st = h->stream;
+    const int prec = h->prec == NUM_FUSED_FP32 ? 0 : 1;
     std::vector<int4> si, li;
-    std::vector<int> so(b->count + 1), lo_(b->count + 1);
-    for (int i = 0; i < b->count; ++i) {
-        so[i] = (int)si.size();
-        for (int64_t r = b->soff[i]; r < b->soff[i + 1]; r += cfg.stream_item)
-            si.push_back(make_int4(i, (int)r, (int)std::min<int64_t>(r + cfg.stream_item,
-                                                                     b->soff[i + 1]), 0));
-        lo_[i] = (int)li.size();
-        for (int64_t r = b->loff[i]; r < b->loff[i + 1]; r += cfg.link_item)
-            li.push_back(make_int4(i, (int)r, (int)std::min<int64_t>(r + cfg.link_item,
-                                                                     b->loff[i + 1]), 0));
+    std::vector<int> so(b->count + 1), lo_(b->count + 1), sblk, lblk;
+    int res_s = 0, res_l = 0;
+    cudaError_t e = pmp::batch_resident(prec, cfg.link_lanes, &res_s, &res_l);
+    if (e != cudaSuccess) return cuda_fail(e, "occupancy of the batch kernels");
+    res_s = std::min(res_s, kMaxBalancedBlocks);
+    res_l = std::min(res_l, kMaxBalancedBlocks);
+    int grid_s_bal = 0, grid_l_bal = 0;
+    if (cfg.stream_item == 0) {
+        const int64_t N = b->soff[b->count];
+        grid_s_bal = (int)std::max<int64_t>(
+            1, std::min<int64_t>(res_s, (N + kBalancedMinWork - 1) / kBalancedMinWork));
+        balanced_items(b->soff, nullptr, grid_s_bal, si, sblk);
+    } else {
+        for (int i = 0; i < b->count; ++i)
+            for (int64_t r = b->soff[i]; r < b->soff[i + 1]; r += cfg.stream_item)
+                si.push_back(make_int4(i, (int)r, (int)std::min<int64_t>(r + cfg.stream_item,
+                                                                         b->soff[i + 1]), 0));
     }
+    if (cfg.link_item == 0) {
+        const int64_t M = b->loff[b->count];
+        if (b->link_deg.empty()) {  // entries of every link, once
+            std::vector<int> rp((size_t)M + 1);
+            e = cudaMemcpyAsync(rp.data(), h->row_ptr, sizeof(int) * rp.size(),
+                                cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) return cuda_fail(e, "reading the link degrees");
+            b->link_deg.resize((size_t)M);
+            for (int64_t l = 0; l < M; ++l) b->link_deg[l] = rp[l + 1] - rp[l];
+        }
+        std::vector<double> pre((size_t)M + 1, 0.0);
+        const bool chunked = h->nchunks > 0;
+        for (int64_t l = 0; l < M; ++l) {
+            const int d = b->link_deg[l];
+            pre[l + 1] = pre[l] + (chunked && d > pmp::kLongRow ? 0.0 : (double)d) +
+                         (double)kLinkEpilogueWeight;
+        }
+        grid_l_bal = (int)std::max<int64_t>(
+            1, std::min<int64_t>(res_l, (int64_t)(pre[M] / kBalancedMinWork) + 1));
+        // blocks beyond the ranges still sum the chunks of the long links
+        const int grid_chunks = (int)std::min<int64_t>(res_l, (h->nchunks + 7) / 8);
+        balanced_items(b->loff, &pre, grid_l_bal, li, lblk);
+        if (grid_chunks > grid_l_bal) {
+            lblk.resize((size_t)grid_chunks + 1, lblk.back());
+            grid_l_bal = grid_chunks;
+        }
+    } else {
+        for (int i = 0; i < b->count; ++i)
+            for (int64_t r = b->loff[i]; r < b->loff[i + 1]; r += cfg.link_item)
+                li.push_back(make_int4(i, (int)r, (int)std::min<int64_t>(r + cfg.link_item,
+                                                                         b->loff[i + 1]), 0));
+    }
+    // the first item of each instance (items are in row order, instances contiguous)
+    std::fill(so.begin(), so.end(), -1);
+    std::fill(lo_.begin(), lo_.end(), -1);
+    for (int q = (int)si.size() - 1; q >= 0; --q) so[si[q].x] = q;
+    for (int q = (int)li.size() - 1; q >= 0; --q) lo_[li[q].x] = q;
     so[b->count] = (int)si.size();
     lo_[b->count] = (int)li.size();
+    for (int i = b->count - 1; i >= 0; --i) {
+        if (so[i] < 0) so[i] = so[i + 1];
+        if (lo_[i] < 0) lo_[i] = lo_[i + 1];
+    }
     if ((int)si.size() > b->cap_sitems || (int)li.size() > b->cap_litems)
         return fail(NUM_ERR_STATE, "work items exceed their capacity");
-    cudaError_t e = cudaStreamSynchronize(st);  // no kernel may still read the old items
+    e = cudaStreamSynchronize(st);  // no kernel may still read the old items
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(b->sitems, si.data(), sizeof(int4) * si.size(), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess)
@@ -199,13 +297,21 @@ int batch_apply_schedule(num_batch* b, const num_batch_schedule& cfg) {
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(b->litem_off, lo_.data(), sizeof(int) * (b->count + 1),
                             cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && !sblk.empty())
+        e = cudaMemcpyAsync(b->sblk, sblk.data(), sizeof(int) * sblk.size(), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && !lblk.empty())
+        e = cudaMemcpyAsync(b->lblk, lblk.data(), sizeof(int) * lblk.size(), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // the host vectors go out of scope
     if (e != cudaSuccess) return cuda_fail(e, "copying the work items");
     b->nsitems = (int)si.size();
     b->nlitems = (int)li.size();
-    e = pmp::batch_grids(h->prec == NUM_FUSED_FP32 ? 0 : 1, cfg.link_lanes, b->nsitems,
-                         b->nlitems, h->nchunks, &b->grid_s, &b->grid_l, &b->grid_e);
+    e = pmp::batch_grids(prec, cfg.link_lanes, b->nsitems, b->nlitems, h->nchunks, &b->grid_s,
+                         &b->grid_l, &b->grid_e);
     if (e != cudaSuccess) return cuda_fail(e, "sizing the batch grids");
+    b->sbal = cfg.stream_item == 0;
+    b->lbal = cfg.link_item == 0;
+    if (b->sbal) b->grid_s = grid_s_bal;
+    if (b->lbal) b->grid_l = grid_l_bal;
     b->cfg = cfg;
     if (b->graph_exec) cudaGraphExecDestroy(b->graph_exec);
     if (b->graph) cudaGraphDestroy(b->graph);
@@ -543,6 +649,9 @@ int batch_create_impl(num_batch** out, int32_t count, const int64_t* stream_off,
         batch_destroy(b);
         return fail(NUM_ERR_INVALID, "too many work items");
     }
+    // balanced partitions make at most one item per block plus one per instance
+    cap_s = std::max<int64_t>(cap_s, (int64_t)kMaxBalancedBlocks + count);
+    cap_l = std::max<int64_t>(cap_l, (int64_t)kMaxBalancedBlocks + count);
     b->cap_sitems = (int)cap_s;
     b->cap_litems = (int)cap_l;
     const int H = prm.history > 0 ? prm.history : 1;
@@ -561,9 +670,11 @@ int batch_create_impl(num_batch** out, int32_t count, const int64_t* stream_off,
     b->soff_d = (int*)dev_alloc(h, sizeof(int) * (count + 1));
     b->loff_d = (int*)dev_alloc(h, sizeof(int) * (count + 1));
     b->bar = (unsigned int*)dev_alloc(h, sizeof(unsigned int) * 2 * (size_t)count);
+    b->sblk = (int*)dev_alloc(h, sizeof(int) * (kMaxBalancedBlocks + 1));
+    b->lblk = (int*)dev_alloc(h, sizeof(int) * (kMaxBalancedBlocks + 1));
     if (!b->ctls || !b->glob || !b->sitems || !b->litems || !b->sitem_off || !b->litem_off ||
         !b->part_s || !b->part_l || !b->part_e || !b->hist || !b->eps_scale || !b->arrive ||
-        !b->soff_d || !b->loff_d || !b->bar) {
+        !b->soff_d || !b->loff_d || !b->bar || !b->sblk || !b->lblk) {
         batch_destroy(b);
         return fail(NUM_ERR_OOM, "device allocation failed");
     }

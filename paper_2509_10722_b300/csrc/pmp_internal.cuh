@@ -156,6 +156,10 @@ struct BatchView {
     const int4* sitems;
     const int4* litems;
     int nsitems, nlitems;
+    // balanced partitions: block b takes items [sblk[b], sblk[b+1]) (and lblk for the link
+    // kernel); NULL: block b takes items b, b + gridDim.x, ...
+    const int* sblk;
+    const int* lblk;
     const int* sitem_off;
     const int* litem_off;
     int count;
@@ -204,6 +208,9 @@ inline cudaError_t record_kernel_event(cudaEvent_t ev, cudaStream_t st) {
 
 cudaError_t batch_grids(int precision, int lanes, int nsitems, int nlitems, int nchunks,
                         int* grid_s, int* grid_l, int* grid_e);
+// Resident blocks of the two batch kernels (occupancy x SMs), the grids of a balanced
+// partition.
+cudaError_t batch_resident(int precision, int lanes, int* blocks_s, int* blocks_l);
 // Persistent form: the most blocks of the persistent kernel that can be resident at once
 // (the bound of a cooperative launch), and one cooperative launch of it.
 cudaError_t batch_persistent_capacity(int precision, int lanes, bool split, int* blocks);

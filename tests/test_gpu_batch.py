@@ -174,7 +174,8 @@ def test_every_partition_matches_oracle(batch, part):
 
 def test_item_sizes_do_not_change_the_iterates(batch):
     """With the lanes per link fixed and the rho decisions replayed, the FP32 iterates are
-    bit-identical for every item size: the partition only regroups the residual sums."""
+    bit-identical for every item size and for the balanced ranges: the partition only
+    regroups the residual sums."""
     from paper_2509_10722_b300 import capi
     iters = 200
     sched = np.zeros((len(batch), iters // 50), dtype=np.int8)
@@ -182,7 +183,8 @@ def test_item_sizes_do_not_change_the_iterates(batch):
         d = oracle_run(inst, iters)["decisions"]
         sched[i, :d.size] = d
     out = []
-    for part in [(2048, 256, 8), (256, 32, 8), (65536, 8192, 8)]:
+    for part in [(0, 0, 8), (2048, 256, 8), (256, 32, 8), (65536, 8192, 8), (0, 512, 8),
+                 (1024, 0, 8)]:
         with capi.Batch(batch, precision=0, history=64) as b:
             b.set_schedule(*part)
             b.set_rho_schedules(sched)
@@ -198,12 +200,12 @@ def test_autotune_chooses_a_partition_and_resets(batch):
     iters = 150
     with capi.Batch(batch, precision=0, history=64) as b:
         chosen, trials = b.autotune(trial_iters=5)
-        assert trials.shape == (25, 4) and np.all(trials[:, 3] > 0)
+        assert trials.shape == (30, 4) and np.all(trials[:, 3] > 0)
         assert b.schedule() == chosen
-        # stage 1 varied stream_item only, stage 2 link_item and lanes
-        assert sorted(set(trials[:5, 0])) == [512, 1024, 2048, 4096, 8192]
-        assert len(set(map(tuple, trials[5:, 1:3]))) == 20
-        assert chosen[0] == trials[:5][np.argmin(trials[:5, 3]), 0]
+        # stage 1 varied stream_item only (0: balanced ranges), stage 2 link_item and lanes
+        assert sorted(set(trials[:6, 0])) == [0, 512, 1024, 2048, 4096, 8192]
+        assert len(set(map(tuple, trials[6:, 1:3]))) == 24
+        assert chosen[0] == trials[:6][np.argmin(trials[:6, 3]), 0]
         rc, it, _ = b.solve(iters, 0.0)
         assert list(it) == [iters] * len(batch)  # reset: counts start from zero
         xs, ps, infos = b.get()
@@ -226,7 +228,7 @@ def test_bad_partitions_are_rejected(bad):
         with pytest.raises(capi.NumError) as e:
             b.set_schedule(*bad)
         assert e.value.code == capi.NUM_ERR_INVALID
-        assert b.schedule() == (2048, 256, 8)
+        assert b.schedule() == (0, 0, 8)
 
 
 # ---- creation from separate instances (num_batch_create_instances) -------------------------

@@ -136,7 +136,9 @@ def batch_cases(draw):
     iters = draw(st.integers(1, 200))
     precision = draw(st.sampled_from([0, 1]))
     eps = draw(st.sampled_from([0.0, 1e-3])) if precision == 1 else 0.0
-    part = (2 ** draw(st.integers(8, 13)), 2 ** draw(st.integers(5, 10)),
+    # 0: balanced ranges (one per block, cut at instance boundaries)
+    part = (draw(st.sampled_from([0] + [2 ** k for k in range(8, 14)])),
+            draw(st.sampled_from([0] + [2 ** k for k in range(5, 11)])),
             draw(st.sampled_from([4, 8, 16, 32])))
     return insts, params, iters, precision, eps, part
 
