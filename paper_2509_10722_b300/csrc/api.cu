@@ -504,15 +504,19 @@ int create_impl(num_problem** out, int64_t n, int64_t m, const int64_t* route_pt
            "counting long-link chunks");
         const size_t nc = (size_t)(h->nchunks > 0 ? h->nchunks : 1);
         h->chunks = (int4*)dev_alloc(h, sizeof(int4) * nc);
+        h->chunk_queue = (int*)dev_alloc(h, sizeof(int) * nc);
         h->carry_l = dev_alloc(h, ts * nc);
         h->arrive_l = (int*)dev_alloc(h, sizeof(int) * nc);
         h->narrive_l = (int)nc;
-        if (!h->chunks || !h->carry_l || !h->arrive_l) {
+        if (!h->chunks || !h->chunk_queue || !h->carry_l || !h->arrive_l) {
             drop();
             return fail(NUM_ERR_OOM, "device allocation failed");
         }
-        if (h->nchunks > 0)
+        if (h->nchunks > 0) {
             CK(pmp::fill_chunks(h->row_ptr, (int)m, d_coff, h->chunks, st), "long-link chunks");
+            CK(pmp::order_chunks(h->chunks, h->nchunks, s, h->chunk_queue, st),
+               "ordering the chunk queue");
+        }
         CK(pmp::count_long_routes(h->col_ptr, (int)n, d_ccount, d_coff, d_ctmp, &h->nlong, st),
            "counting long routes");
         h->long_routes = (int*)dev_alloc(h, sizeof(int) * (size_t)(h->nlong > 0 ? h->nlong : 1));

@@ -35,6 +35,7 @@ struct num_problem {
     int* perm = nullptr;                 // caller's index of the stream at each position
     uint8_t* ut = nullptr;               // utility types, only if some stream has U = -w / x
     int4* chunks = nullptr;              // row kernels: chunks of the long links
+    int* chunk_queue = nullptr;          // row kernels: the chunks, longest first
     int* long_routes = nullptr;          // row kernels: streams with long routes
     int nlong = 0;
     int nchunks = 0;
@@ -149,6 +150,7 @@ View<T> make_view(const num_problem* h) {
     v.grid_l = h->grid_l;
     v.link_spread = h->link_spread;
     v.chunks = h->chunks;
+    v.chunk_queue = h->chunk_queue;
     v.nchunks = h->nchunks;
     v.perm = h->perm;
     v.ut = h->ut;

@@ -359,6 +359,15 @@ __global__ void k_chunk_fill(const int* __restrict__ row_ptr, int m, const int* 
     }
 }
 
+// Sort keys of the chunk queue: kChunk - length (0 for a full chunk), value the chunk index.
+__global__ void k_chunk_keys(const int4* __restrict__ chunks, int nchunks, int* keys, int* vals) {
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nchunks; q += gridDim.x * blockDim.x) {
+        const int4 ch = chunks[q];
+        keys[q] = kChunk - (ch.z - ch.y);
+        vals[q] = q;
+    }
+}
+
 template <typename T>
 __global__ void k_convert(int n, int m, const double* __restrict__ c,
                           const uint8_t* __restrict__ utype, const double* __restrict__ w,
@@ -657,6 +666,17 @@ cudaError_t fill_chunks(const int* row_ptr, int m, const int* offs, int4* chunks
     k_chunk_fill<<<blocks_for(m, kThreads, 65535), kThreads, 0, st>>>(row_ptr, m, offs, chunks);
     note_launches(1);
     return cudaGetLastError();
+}
+
+cudaError_t order_chunks(const int4* chunks, int nchunks, const Scratch& s, int* queue,
+                         cudaStream_t st) {
+    k_chunk_keys<<<blocks_for(nchunks, kThreads, 65535), kThreads, 0, st>>>(chunks, nchunks,
+                                                                           s.keys_a, s.vals_a);
+    note_launches(1);
+    int *ki = nullptr, *vi = nullptr;
+    cudaError_t e = radix_sort_pairs(nchunks, kChunk, s, &ki, &vi, st);
+    if (e != cudaSuccess) return e;
+    return cudaMemcpyAsync(queue, vi, sizeof(int) * (size_t)nchunks, cudaMemcpyDeviceToDevice, st);
 }
 
 template <typename T>

@@ -36,6 +36,7 @@ struct Ctl {
     int hist_len;      // entries of the residual ring buffer
     unsigned int ticket;  // last-block-done counter of the link kernel
     unsigned int ticket2; // last-block-done counter of the reductions
+    unsigned int chunk_next;  // the link kernel's queue of long-link chunks: next to take
 };
 
 enum Stop { RUNNING = 0, CONVERGED = 1, LIMIT = 2, NONFINITE = 3 };
@@ -101,6 +102,8 @@ struct View {
                                 // group's links spread over its lanes) or 0 (few: one group
                                 // per link, its leader runs the epilogue)
     const int4* chunks;         // row kernels: (link, first entry, end entry, first chunk)
+    const int* chunk_queue;     // row link kernel: chunk indices in the order its queue hands
+                                // them out (the longest first)
     int nchunks;
     const int* perm;            // caller's index of the stream at each position (or NULL)
     const uint8_t* ut;          // utility type per stream, only when some stream has type 2
@@ -319,6 +322,10 @@ struct Scratch {  // transient buffers of the operator build, caller-allocated
 
 size_t radix_hist_len(int nnz);
 size_t scan_tmp_len(size_t len);
+// Order of the long-link chunk queue: queue[nchunks] receives the chunk indices by
+// decreasing chunk length, equal lengths in chunk order (a stable radix sort in s).
+cudaError_t order_chunks(const int4* chunks, int nchunks, const Scratch& s, int* queue,
+                         cudaStream_t st);
 
 // Validate the inputs in two parts, so that the routes can be checked and the operator
 // built while the other arrays are still being copied: the routes (route_ptr increasing

@@ -33,7 +33,8 @@
 //     warp (four gathers in flight per lane) into its own slot, and the warp that brings
 //     the row's arrival count to the number of chunks sums the slots in a fixed order and
 //     runs the epilogue (no waiting, deterministic): the long links' work is cut into
-//     equal pieces, which is what balances the Zipf-skewed link degrees;
+//     equal pieces, which the warps take from a grid-wide queue, longest first, once
+//     their own links are done; that is what balances the Zipf-skewed link degrees;
 //   the last block of the link kernel finishes the iteration (FP64 residual sums, stopping
 //   test, rho).
 // Residual terms are summed in FP64 (per thread, per block, over the grid) in both
@@ -189,32 +190,45 @@ __global__ void __launch_bounds__(kTh) k_link_rows(View<T> v) {
         }
     }
     // chunks of the longer links: one warp each (four gathers in flight per lane), so that
-    // a chunk is a short chain of round trips and the chunks balance across warps
+    // a chunk is a short chain of round trips.  The warps take them from a queue shared by
+    // the grid, longest first, and each warp takes its next chunk before it sums the
+    // current one: a warp that is done with its links takes more chunks, so that the
+    // Zipf-skewed work evens out over the SMs, and the chunks taken last are the shortest.
+    // Which warp sums a chunk does not change the result: every chunk has its own slot, and
+    // the slots of a link are summed in a fixed order.
     const int lane = threadIdx.x & 31;
-    for (int q = blockIdx.x * kWarps + (int)(threadIdx.x >> 5); q < v.nchunks;
-         q += gridDim.x * kWarps) {
-        const int4 ch = __ldg(v.chunks + q);  // (row, first entry, end entry, first chunk)
-        const T s = warp_gather_sum(col_idx, x, ch.y, ch.z, lane, v.n, v.dbg);
-        int fin = 0;
-        if (lane == 0) {
-            v.carry_l[q] = s;
-            __threadfence();
-            const int p0 = __ldg(row_ptr + ch.x), p1 = __ldg(row_ptr + ch.x + 1);
-            const int nch = (p1 - p0 + kChunk - 1) / kChunk;
-            fin = atomicAdd(v.arrive_l + ch.w, 1) == nch - 1;
-        }
-        fin = __shfl_sync(0xffffffffu, fin, 0);
-        if (fin) {  // every chunk of the row is in: sum the slots in a fixed order
-            __threadfence();
-            const int p0 = __ldg(row_ptr + ch.x), p1 = __ldg(row_ptr + ch.x + 1);
-            const int nch = (p1 - p0 + kChunk - 1) / kChunk;
-            const T t = warp_sum_slots(v.carry_l + ch.w, nch, lane);
+    if (v.nchunks > 0) {
+        int t = 0;  // queue position
+        if (lane == 0) t = (int)atomicAdd(&ctl->chunk_next, 1u);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        while (t < v.nchunks) {
+            int tn = 0;
+            if (lane == 0) tn = (int)atomicAdd(&ctl->chunk_next, 1u);
+            const int q = __ldg(v.chunk_queue + t);
+            const int4 ch = __ldg(v.chunks + q);  // (row, first entry, end entry, first chunk)
+            const T s = warp_gather_sum(col_idx, x, ch.y, ch.z, lane, v.n, v.dbg);
+            int fin = 0;
             if (lane == 0) {
-                v.arrive_l[ch.w] = 0;
-                const LinkState<T> st = load_link(v, ch.x);
-                const T psn = link_epilogue(v, ch.x, st, t, p1 - p0, alpha, rho, inv_rho, r2, s2);
-                if (kTape && tape) tape[ch.x] = psn;
+                v.carry_l[q] = s;
+                __threadfence();
+                const int p0 = __ldg(row_ptr + ch.x), p1 = __ldg(row_ptr + ch.x + 1);
+                const int nch = (p1 - p0 + kChunk - 1) / kChunk;
+                fin = atomicAdd(v.arrive_l + ch.w, 1) == nch - 1;
             }
+            fin = __shfl_sync(0xffffffffu, fin, 0);
+            if (fin) {  // every chunk of the row is in: sum the slots in a fixed order
+                __threadfence();
+                const int p0 = __ldg(row_ptr + ch.x), p1 = __ldg(row_ptr + ch.x + 1);
+                const int nch = (p1 - p0 + kChunk - 1) / kChunk;
+                const T tot = warp_sum_slots(v.carry_l + ch.w, nch, lane);
+                if (lane == 0) {
+                    v.arrive_l[ch.w] = 0;
+                    const LinkState<T> st = load_link(v, ch.x);
+                    const T psn = link_epilogue(v, ch.x, st, tot, p1 - p0, alpha, rho, inv_rho, r2, s2);
+                    if (kTape && tape) tape[ch.x] = psn;
+                }
+            }
+            t = __shfl_sync(0xffffffffu, tn, 0);
         }
     }
     double rs[2] = {r2.value(), s2.value()};
@@ -232,6 +246,7 @@ __global__ void __launch_bounds__(kTh) k_link_rows(View<T> v) {
         grid_residual_sums(v.part_l, gridDim.x, v.part_s, v.grid_s, red, a, b, c);
         if (threadIdx.x == 0) {
             ctl->ticket = 0;
+            ctl->chunk_next = 0;  // every warp of the grid has left the chunk queue
             if (kTape && taping) v.tape_rho[tk] = ctl->rho;  // the rho this iteration used
             finalize_iteration(ctl, a, c + b, v.hist, v.sched);
         }

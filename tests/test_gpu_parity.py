@@ -178,10 +178,14 @@ def test_runs_are_bit_identical(c1):
 
 
 def test_skewed_runs_are_bit_identical():
-    inst = CASES[5][1]  # Zipf links, several split into chunks
+    """Zipf links, several split into chunks: which warp takes which chunk from the link
+    kernel's queue varies from run to run, the bits must not."""
+    inst = CASES[5][1]
     a = run_gpu(inst, 100, "fp32")
     b = run_gpu(inst, 100, "fp32")
-    assert np.array_equal(a["x"], b["x"]) and np.array_equal(a["lam"], b["lam"])
+    c = run_gpu(inst, 100, "fp32", use_graph=0)
+    for other in (b, c):
+        assert np.array_equal(a["x"], other["x"]) and np.array_equal(a["lam"], other["lam"])
 
 
 def test_device_inputs_equal_host_inputs(c1):
