@@ -40,18 +40,35 @@ namespace {
 constexpr int kTh = 256;
 constexpr int kGroup = 8;
 
+// The inputs of a link's transpose step that do not depend on the gathers.
+template <typename T>
+struct AdjLinkState {
+    T yb, zsb, ps, c;
+};
+
+template <typename T>
+__device__ __forceinline__ AdjLinkState<T> adj_load_link(const AdjView<T>& a, int l,
+                                                         const T* __restrict__ ps_k) {
+    AdjLinkState<T> st;
+    st.yb = a.yb[l];
+    st.zsb = a.zsb[l];
+    st.ps = ps_k[l];
+    st.c = a.v.c[l];
+    return st;
+}
+
 // Transpose of the link step of one link, given sa = (R Abar)_l and sb = (R Bbar)_l.
 template <typename T>
-__device__ __forceinline__ void adj_link_epilogue(const AdjView<T>& a, int l, T sa, T sb, int deg,
-                                                  T alpha, T rho, const T* __restrict__ ps_k) {
-    const View<T>& v = a.v;
-    const T yb = a.yb[l] + sb;
-    const T zsb = a.zsb[l];
+__device__ __forceinline__ void adj_link_epilogue(const AdjView<T>& a, int l,
+                                                  const AdjLinkState<T>& st, T sa, T sb, int deg,
+                                                  T alpha, T rho) {
+    const T yb = st.yb + sb;
+    const T zsb = st.zsb;
     const T deg1 = (T)(deg + 1);
     const T t = sa + alpha * rho * yb - alpha * zsb;
     const T psb = t / deg1 + alpha * zsb;
     a.Rxb[l] = t / deg1;
-    const bool open = ps_k[l] > -v.c[l];  // slack prox not at its bound
+    const bool open = st.ps > -st.c;  // slack prox not at its bound
     a.zsb[l] = (T(1) - alpha) * zsb + (open ? psb : T(0));
     a.yb[l] = yb - (open ? psb / rho : T(0));
     if (!open) a.cb[l] -= psb;
@@ -66,36 +83,57 @@ __global__ void __launch_bounds__(kTh) k_adj_link(AdjView<T> a, const T* __restr
     const View<T>& v = a.v;
     const T alpha = (T)a.alpha, rho = (T)*rho_ptr;
     constexpr int kGroups = kTh / kGroup;
-    for (int l = blockIdx.x * kGroups + (int)(threadIdx.x / kGroup); l < v.m;
-         l += gridDim.x * kGroups) {
-        const int p0 = __ldg(v.row_ptr + l), p1 = __ldg(v.row_ptr + l + 1);
-        if (a.abc && p1 - p0 > kLongRow) continue;  // done by its chunks
-        // R Abar, R Bbar: lane k adds entries p0 + k, p0 + k + kGroup, ... in that order,
-        // four gathers in flight
-        T sa = T(0), sb = T(0);
-        for (int e = p0 + g.thread_rank(); e < p1; e += 4 * kGroup) {
-            int ix[4];
-#pragma unroll
-            for (int k = 0; k < 4; ++k)
-                ix[k] = (k == 0 || e + k * kGroup < p1)
-                            ? checked_index(__ldg(v.col_idx + e + k * kGroup), v.n, v.dbg)
-                            : -1;
-            T2 u[4];
-#pragma unroll
-            for (int k = 0; k < 4; ++k) u[k] = ix[k] >= 0 ? __ldg(a.ab + ix[k]) : T2{T(0), T(0)};
-#pragma unroll
-            for (int k = 0; k < 4; ++k)
-                if (ix[k] >= 0) {
-                    sa += u[k].x;
-                    sb += u[k].y;
-                }
+    const int m = v.m;
+    // one group per link, links in turn over the grid; the bounds of the group's
+    // next link are loaded before the current link is summed, and the leader loads the
+    // link's own inputs before the gathers
+    int l = blockIdx.x * kGroups + (int)(threadIdx.x / kGroup);
+    int p0 = 0, p1 = 0;
+    if (l < m) {
+        p0 = __ldg(v.row_ptr + l);
+        p1 = __ldg(v.row_ptr + l + 1);
+    }
+    while (l < m) {
+        const int ln = l + gridDim.x * kGroups;
+        int q0 = 0, q1 = 0;
+        if (ln < m) {
+            q0 = __ldg(v.row_ptr + ln);
+            q1 = __ldg(v.row_ptr + ln + 1);
         }
+        if (!a.abc || p1 - p0 <= kLongRow) {  // longer links are done by their chunks
+            AdjLinkState<T> st;
+            if (leader) st = adj_load_link(a, l, ps_k);
+            // R Abar, R Bbar: lane k adds entries p0 + k, p0 + k + kGroup, ... in that
+            // order, four gathers in flight
+            T sa = T(0), sb = T(0);
+            for (int e = p0 + g.thread_rank(); e < p1; e += 4 * kGroup) {
+                int ix[4];
 #pragma unroll
-        for (int o = kGroup / 2; o > 0; o >>= 1) {
-            sa += g.shfl_down(sa, o);
-            sb += g.shfl_down(sb, o);
+                for (int k = 0; k < 4; ++k)
+                    ix[k] = (k == 0 || e + k * kGroup < p1)
+                                ? checked_index(__ldg(v.col_idx + e + k * kGroup), v.n, v.dbg)
+                                : -1;
+                T2 u[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    u[k] = ix[k] >= 0 ? __ldg(a.ab + ix[k]) : T2{T(0), T(0)};
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    if (ix[k] >= 0) {
+                        sa += u[k].x;
+                        sb += u[k].y;
+                    }
+            }
+#pragma unroll
+            for (int o = kGroup / 2; o > 0; o >>= 1) {
+                sa += g.shfl_down(sa, o);
+                sb += g.shfl_down(sb, o);
+            }
+            if (leader) adj_link_epilogue(a, l, st, sa, sb, p1 - p0, alpha, rho);
         }
-        if (leader) adj_link_epilogue(a, l, sa, sb, p1 - p0, alpha, rho, ps_k);
+        l = ln;
+        p0 = q0;
+        p1 = q1;
     }
     if (!a.abc) return;
     // chunks of the longer links: one warp each; the warp that completes a link sums its
@@ -141,24 +179,46 @@ __global__ void __launch_bounds__(kTh) k_adj_link(AdjView<T> a, const T* __restr
         }
         if (lane == 0) {
             v.arrive_l[ch.w] = 0;
-            adj_link_epilogue(a, ch.x, ta, tb, p1 - p0, alpha, rho, ps_k);
+            const AdjLinkState<T> st = adj_load_link(a, ch.x, ps_k);
+            adj_link_epilogue(a, ch.x, st, ta, tb, p1 - p0, alpha, rho);
         }
     }
 }
 
+// The inputs of a stream's transpose step that do not depend on the gathers.
+template <typename T>
+struct AdjStreamState {
+    T xb, x, wt, lo, hi, Zb, wb;
+    bool a2;  // U = -w / x
+};
+
+template <typename T>
+__device__ __forceinline__ AdjStreamState<T> adj_load_stream(const AdjView<T>& a, int j,
+                                                             const T* __restrict__ x_k) {
+    const View<T>& v = a.v;
+    AdjStreamState<T> st;
+    st.xb = a.xb[j];
+    st.x = x_k[j];
+    st.wt = v.wt[j];
+    st.lo = v.box_uniform ? v.lo_u : v.lo[j];
+    st.hi = v.box_uniform ? v.hi_u : v.hi[j];
+    st.Zb = a.Zb[j];
+    st.wb = a.wb[j];
+    st.a2 = v.ut && v.ut[j] == 2;
+    return st;
+}
+
 // Transpose of the stream step of stream j, given r = (R' Rx_bar)_j.
 template <typename T>
-__device__ __forceinline__ void adj_stream_epilogue(const AdjView<T>& a, int j, T r, int len,
-                                                    const T* __restrict__ x_k, T alpha, T rho) {
+__device__ __forceinline__ void adj_stream_epilogue(const AdjView<T>& a, int j,
+                                                    const AdjStreamState<T>& st, T r, int len,
+                                                    T alpha, T rho) {
     using T2 = typename Pair<T>::type;
-    const View<T>& v = a.v;
-    const T xbk = a.xb[j] + r;
-    const T x = x_k[j], L = (T)len, wt = v.wt[j];
-    const T lo = v.box_uniform ? v.lo_u : v.lo[j];
-    const T hi = v.box_uniform ? v.hi_u : v.hi[j];
+    const T xbk = st.xb + r;
+    const T x = st.x, L = (T)len, wt = st.wt;
     T dS = T(0), dw = T(0);
-    if (x > lo && x < hi) {
-        if (v.ut && v.ut[j] == 2) {
+    if (x > st.lo && x < st.hi) {
+        if (st.a2) {
             // rho L x^3 - rho S x^2 - w = 0 with S = L x - w / (rho x^2):
             // f_x = rho L x^2 + 2 w / x, dx/dS = rho x^2 / f_x, dx/dw = 1 / f_x
             const T fx = rho * L * x * x + T(2) * wt / x;
@@ -174,8 +234,8 @@ __device__ __forceinline__ void adj_stream_epilogue(const AdjView<T>& a, int j, 
         }
     }
     const T Sb = xbk * dS;
-    a.wb[j] += xbk * dw;
-    const T t = a.Zb[j] + Sb;
+    a.wb[j] = st.wb + xbk * dw;
+    const T t = st.Zb + Sb;
     a.xb[j] = alpha * L * t;
     a.Zb[j] = (T(1) - alpha) * t;
     T2 ab;
@@ -190,9 +250,12 @@ __global__ void __launch_bounds__(kTh) k_adj_stream(AdjView<T> a, const T* __res
     const View<T>& v = a.v;
     const T alpha = (T)a.alpha, rho = (T)*rho_ptr;
     const bool split = v.nlong > 0;
+    // one thread per stream, streams in turn over the grid; the stream's own inputs are loaded
+    // before its gathers
     for (int j = blockIdx.x * kTh + threadIdx.x; j < v.n; j += gridDim.x * kTh) {
         const int p = __ldg(v.col_ptr + j), pn = __ldg(v.col_ptr + j + 1);
         if (split && pn - p > kLongRoute) continue;  // summed by a warp below
+        const AdjStreamState<T> st = adj_load_stream(a, j, x_k);
         T r = T(0);  // (R' Rx_bar)_j in route order, four gathers in flight
         int e = p;
         for (; e + 4 <= pn; e += 4) {
@@ -208,7 +271,7 @@ __global__ void __launch_bounds__(kTh) k_adj_stream(AdjView<T> a, const T* __res
             r += g3;
         }
         for (; e < pn; ++e) r += __ldg(a.Rxb + checked_index(__ldg(v.row_idx + e), v.m, v.dbg));
-        adj_stream_epilogue(a, j, r, pn - p, x_k, alpha, rho);
+        adj_stream_epilogue(a, j, st, r, pn - p, alpha, rho);
     }
     // streams with more than kLongRoute links: one warp each, as in the forward kernel
     const int lane = threadIdx.x & 31;
@@ -221,7 +284,7 @@ __global__ void __launch_bounds__(kTh) k_adj_stream(AdjView<T> a, const T* __res
             r += a.Rxb[checked_index(__ldg(v.row_idx + e), v.m, v.dbg)];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) r += __shfl_down_sync(0xffffffffu, r, o);
-        if (lane == 0) adj_stream_epilogue(a, j, r, pn - p, x_k, alpha, rho);
+        if (lane == 0) adj_stream_epilogue(a, j, adj_load_stream(a, j, x_k), r, pn - p, alpha, rho);
     }
 }
 
@@ -290,7 +353,39 @@ int grid_for(long long count) {
     return (int)(b < 1 ? 1 : (b > 8192 ? 8192 : b));
 }
 
+// With a few links or streams per thread slot of a resident grid (c5: 1e5 links, 1e6
+// streams), a resident grid that loops was fastest; with tens (ten times c5), one block
+// per 256 items up to 8192 blocks.  The switch sits between the two.
+constexpr long long kFewBlocksPerSlot = 16;
+
+template <typename K>
+cudaError_t pass_grid(K kernel, long long items, long long blocks_needed, int* grid) {
+    int dev = 0, sms = 0, occ = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, kTh, 0);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) return cudaErrorInvalidConfiguration;
+    const long long resident = (long long)occ * sms;
+    if (blocks_needed > kFewBlocksPerSlot * resident) {
+        *grid = grid_for(items);
+        return cudaSuccess;
+    }
+    const long long g = resident < blocks_needed ? resident : blocks_needed;
+    *grid = (int)(g < 1 ? 1 : g);
+    return cudaSuccess;
+}
+
 }  // namespace
+
+template <typename T>
+cudaError_t adjoint_grids(AdjView<T>& a) {
+    constexpr int kGroups = kTh / kGroup;
+    cudaError_t e = pass_grid(k_adj_link<T>, (long long)a.v.m * kGroup,
+                              ((long long)a.v.m + kGroups - 1) / kGroups, &a.grid_l);
+    if (e != cudaSuccess) return e;
+    return pass_grid(k_adj_stream<T>, a.v.n, ((long long)a.v.n + kTh - 1) / kTh, &a.grid_s);
+}
 
 template <typename T>
 cudaError_t adjoint_init(const AdjView<T>& a, const double* xbar, double ubar, cudaStream_t st) {
@@ -302,8 +397,9 @@ cudaError_t adjoint_init(const AdjView<T>& a, const double* xbar, double ubar, c
 template <typename T>
 cudaError_t adjoint_step(const AdjView<T>& a, const T* x_k, const T* ps_k, const double* rho,
                          cudaStream_t st) {
-    k_adj_link<T><<<grid_for((long long)a.v.m * kGroup), kTh, 0, st>>>(a, ps_k, rho);
-    k_adj_stream<T><<<grid_for(a.v.n), kTh, 0, st>>>(a, x_k, rho);
+    k_adj_link<T><<<a.grid_l > 0 ? a.grid_l : grid_for((long long)a.v.m * kGroup), kTh, 0, st>>>(
+        a, ps_k, rho);
+    k_adj_stream<T><<<a.grid_s > 0 ? a.grid_s : grid_for(a.v.n), kTh, 0, st>>>(a, x_k, rho);
     note_launches(2);
     return cudaGetLastError();
 }
@@ -329,6 +425,7 @@ cudaError_t set_weights(const View<T>& v, const double* w, cudaStream_t st) {
 }
 
 #define PMP_ADJ_INST(T)                                                                        \
+    template cudaError_t adjoint_grids<T>(AdjView<T>&);                                        \
     template cudaError_t adjoint_init<T>(const AdjView<T>&, const double*, double, cudaStream_t); \
     template cudaError_t adjoint_step<T>(const AdjView<T>&, const T*, const T*, const double*,  \
                                          cudaStream_t);                                        \

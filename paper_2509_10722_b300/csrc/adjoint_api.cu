@@ -257,6 +257,7 @@ int backward_impl(num_problem* h, const double* xbar, double ubar, double* c_gra
     // the cotangents start from the final state
     BK(copy_state(h, t->ckpt + t->sb * (size_t)t->nseg, false), "restore the final state");
     a.v = make_view<T>(h);
+    BK(pmp::adjoint_grids<T>(a), "sizing the adjoint grids");
     BK(pmp::adjoint_init<T>(a, xbar, ubar, st), "adjoint init");
     const T* tx = (const T*)t->tape_x;
     const T* tp = (const T*)t->tape_ps;

@@ -254,7 +254,13 @@ struct AdjView {
     T* cb;                        // dJ/dc [m]
     T* wb;                        // dJ/dw [n]
     typename Pair<T>::type* abc;  // [v.nchunks] chunk sums of (Abar, Bbar) of long links
+    int grid_l, grid_s;           // grids of the two passes (by adjoint_grids)
 };
+// Grids of the backward link and stream passes (their blocks loop over links and streams):
+// the blocks that fit on the GPU at once when each thread slot has a few items, else one
+// block per 256 items up to 8192.
+template <typename T>
+cudaError_t adjoint_grids(AdjView<T>& a);
 template <typename T>
 // x_bar = xbar (caller order, may be NULL) + ubar U'(x); w_bar = ubar dU/dw; others zero.
 cudaError_t adjoint_init(const AdjView<T>& a, const double* xbar, double ubar, cudaStream_t st);
