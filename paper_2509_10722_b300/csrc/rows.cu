@@ -110,7 +110,10 @@ __global__ void __launch_bounds__(kTh) k_stream_rows(View<T> v) {
 // rather than on its leader (few).  Two pairs of gathers are in flight per lane.
 // kTape: as in the stream kernel; the tape receives every link's slack flow and the rho
 // of the iteration.
-template <typename T, bool kSpread, bool kTape>
+// kChunks: the instance has links of more than kLongRow streams (v.nchunks > 0); without
+// them the kernel is compiled without the chunk phase (which costs the other phases
+// registers: 48 against 40 per thread, 5 resident blocks per SM instead of 6).
+template <typename T, bool kSpread, bool kTape, bool kChunks>
 __global__ void __launch_bounds__(kTh) k_link_rows(View<T> v) {
     __shared__ double red[3 * kWarps];
     __shared__ int last;
@@ -147,12 +150,12 @@ __global__ void __launch_bounds__(kTh) k_link_rows(View<T> v) {
             for (int j = 0; j < kGroup; ++j) {
                 if (base + j >= m) break;  // the same for the whole group
                 const int p0 = g.shfl(q0, j), p1 = g.shfl(q1, j);
-                if (p1 - p0 > kLongRow) continue;  // done by its chunks
+                if (kChunks && p1 - p0 > kLongRow) continue;  // done by its chunks
                 const T s = group_gather_sum<kGroup, 2>(g, col_idx, x, p0, p1, v.n, v.dbg);
                 const T sj = g.shfl(s, 0);
                 if (sl == j) mine = sj;
             }
-            if (lk < m && q1 - q0 <= kLongRow) {
+            if (lk < m && (!kChunks || q1 - q0 <= kLongRow)) {
                 const LinkState<T> st = load_link(v, (int)lk);
                 const T psn = link_epilogue(v, (int)lk, st, mine, q1 - q0, alpha, rho, inv_rho, r2, s2);
                 if (kTape && tape) tape[lk] = psn;
@@ -175,7 +178,7 @@ __global__ void __launch_bounds__(kTh) k_link_rows(View<T> v) {
                 q0 = __ldg(row_ptr + ln);
                 q1 = __ldg(row_ptr + ln + 1);
             }
-            if (p1 - p0 <= kLongRow) {  // longer links are done by their chunks
+            if (!kChunks || p1 - p0 <= kLongRow) {  // longer links are done by their chunks
                 LinkState<T> st;
                 if (leader) st = load_link(v, l);
                 const T s = group_gather_sum<kGroup, 2>(g, col_idx, x, p0, p1, v.n, v.dbg);
@@ -197,7 +200,7 @@ __global__ void __launch_bounds__(kTh) k_link_rows(View<T> v) {
     // Which warp sums a chunk does not change the result: every chunk has its own slot, and
     // the slots of a link are summed in a fixed order.
     const int lane = threadIdx.x & 31;
-    if (v.nchunks > 0) {
+    if (kChunks) {
         int t = 0;  // queue position
         if (lane == 0) t = (int)atomicAdd(&ctl->chunk_next, 1u);
         t = __shfl_sync(0xffffffffu, t, 0);
@@ -253,17 +256,17 @@ __global__ void __launch_bounds__(kTh) k_link_rows(View<T> v) {
     }
 }
 
-template <typename T>
+template <typename T, bool kChunks>
 cudaError_t rows_occupancy(int* occ_s, int* occ_spread, int* occ_leader) {
     // the variant with the warp phase uses at least as many registers
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
         occ_s, k_stream_rows<T, true, false>, kTh, 0);
     if (e != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ_spread, k_link_rows<T, true, false>,
-                                                      kTh, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        occ_spread, k_link_rows<T, true, false, kChunks>, kTh, 0);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ_leader, k_link_rows<T, false, false>,
-                                                         kTh, 0);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        occ_leader, k_link_rows<T, false, false, kChunks>, kTh, 0);
 }
 
 // With about 4 links to sum per group slot of a resident grid (c5: 1e5 links), one group
@@ -280,8 +283,12 @@ cudaError_t rows_grids(int precision, int n, int m, int nchunks, int* grid_s, in
     if (e != cudaSuccess) return e;
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
-    e = precision == 0 ? rows_occupancy<float>(&occ_s, &occ_spread, &occ_leader)
-                       : rows_occupancy<double>(&occ_s, &occ_spread, &occ_leader);
+    if (precision == 0)
+        e = nchunks > 0 ? rows_occupancy<float, true>(&occ_s, &occ_spread, &occ_leader)
+                        : rows_occupancy<float, false>(&occ_s, &occ_spread, &occ_leader);
+    else
+        e = nchunks > 0 ? rows_occupancy<double, true>(&occ_s, &occ_spread, &occ_leader)
+                        : rows_occupancy<double, false>(&occ_s, &occ_spread, &occ_leader);
     if (e != cudaSuccess) return e;
     if (occ_s < 1 || occ_spread < 1 || occ_leader < 1) return cudaErrorInvalidConfiguration;
     const long long need_s = ((long long)n + kTh - 1) / kTh;
@@ -304,10 +311,17 @@ void rows_launch(const View<T>& v, cudaStream_t st, cudaEvent_t* evs) {
     else
         k_stream_rows<T, false, kTape><<<v.grid_s, kTh, 0, st>>>(v);
     if (evs) record_kernel_event(evs[0], st);
-    if (v.link_spread)
-        k_link_rows<T, true, kTape><<<v.grid_l, kTh, 0, st>>>(v);
-    else
-        k_link_rows<T, false, kTape><<<v.grid_l, kTh, 0, st>>>(v);
+    if (v.nchunks > 0) {
+        if (v.link_spread)
+            k_link_rows<T, true, kTape, true><<<v.grid_l, kTh, 0, st>>>(v);
+        else
+            k_link_rows<T, false, kTape, true><<<v.grid_l, kTh, 0, st>>>(v);
+    } else {
+        if (v.link_spread)
+            k_link_rows<T, true, kTape, false><<<v.grid_l, kTh, 0, st>>>(v);
+        else
+            k_link_rows<T, false, kTape, false><<<v.grid_l, kTh, 0, st>>>(v);
+    }
     if (evs) record_kernel_event(evs[1], st);
 }
 
