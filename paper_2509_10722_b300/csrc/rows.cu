@@ -113,8 +113,12 @@ __global__ void __launch_bounds__(kTh) k_stream_rows(View<T> v) {
 // kChunks: the instance has links of more than kLongRow streams (v.nchunks > 0); without
 // them the kernel is compiled without the chunk phase (which costs the other phases
 // registers: 48 against 40 per thread, 5 resident blocks per SM instead of 6).
+// The FP32 spread variants are held to 40 registers (6 resident blocks per SM; a few bytes
+// of spills): left free they take 48 (5 blocks), which was 1.2% slower at c2 and 0.3% faster
+// at the Zipf-skewed c3 shape.
 template <typename T, bool kSpread, bool kTape, bool kChunks>
-__global__ void __launch_bounds__(kTh) k_link_rows(View<T> v) {
+__global__ void __launch_bounds__(kTh, (kSpread && sizeof(T) == 4) ? 6 : 1)
+    k_link_rows(View<T> v) {
     __shared__ double red[3 * kWarps];
     __shared__ int last;
     Ctl* ctl = v.ctl;
@@ -134,30 +138,42 @@ __global__ void __launch_bounds__(kTh) k_link_rows(View<T> v) {
     if (kSpread) {
         // links of up to kLongRow streams, many per group: a group takes kGroup consecutive
         // links at a time and sums them one after the other with all its lanes; lane k then
-        // runs the epilogue of the k-th of them, so that the epilogues use every lane
+        // runs the epilogue of the k-th of them, so that the epilogues use every lane.
+        // Rounds of kGroup links per group are dealt out in turn (groups side by side take
+        // links side by side); the links left after the full rounds are split evenly, fewer
+        // than kGroup per group, so that no group has a round more than another.
         const int sl = g.thread_rank();
-        const long long stride = (long long)gridDim.x * kGroups * kGroup;
-        for (long long base = ((long long)blockIdx.x * kGroups + threadIdx.x / kGroup) * kGroup;
-             base < m; base += stride) {
-            const long long lk = base + sl;  // this lane's link
+        const int ngroups = gridDim.x * kGroups;
+        const int gid = blockIdx.x * kGroups + (int)(threadIdx.x / kGroup);
+        const int per_round = ngroups * kGroup;
+        const int rounds = m / per_round;
+        const int rest0 = rounds * per_round;  // first link left over
+        const int rest = m - rest0;
+        const int last0 = rest0 + (int)((long long)gid * rest / ngroups);
+        const int last1 = rest0 + (int)((long long)(gid + 1) * rest / ngroups);
+        for (int k = 0; k <= rounds; ++k) {
+            // this round's links of the group: [base, end)
+            const int base = k < rounds ? (k * ngroups + gid) * kGroup : last0;
+            const int end = k < rounds ? base + kGroup : last1;
+            const int lk = base + sl;  // this lane's link
             int q0 = 0, q1 = 0;
-            if (lk < m) {
+            if (lk < end) {
                 q0 = __ldg(row_ptr + lk);
                 q1 = __ldg(row_ptr + lk + 1);
             }
             T mine = T(0);
 #pragma unroll 1
             for (int j = 0; j < kGroup; ++j) {
-                if (base + j >= m) break;  // the same for the whole group
+                if (base + j >= end) break;  // the same for the whole group
                 const int p0 = g.shfl(q0, j), p1 = g.shfl(q1, j);
                 if (kChunks && p1 - p0 > kLongRow) continue;  // done by its chunks
                 const T s = group_gather_sum<kGroup, 2>(g, col_idx, x, p0, p1, v.n, v.dbg);
                 const T sj = g.shfl(s, 0);
                 if (sl == j) mine = sj;
             }
-            if (lk < m && (!kChunks || q1 - q0 <= kLongRow)) {
-                const LinkState<T> st = load_link(v, (int)lk);
-                const T psn = link_epilogue(v, (int)lk, st, mine, q1 - q0, alpha, rho, inv_rho, r2, s2);
+            if (lk < end && (!kChunks || q1 - q0 <= kLongRow)) {
+                const LinkState<T> st = load_link(v, lk);
+                const T psn = link_epilogue(v, lk, st, mine, q1 - q0, alpha, rho, inv_rho, r2, s2);
                 if (kTape && tape) tape[lk] = psn;
             }
         }
