@@ -113,11 +113,13 @@ __global__ void __launch_bounds__(kTh) k_stream_rows(View<T> v) {
 // kChunks: the instance has links of more than kLongRow streams (v.nchunks > 0); without
 // them the kernel is compiled without the chunk phase (which costs the other phases
 // registers: 48 against 40 per thread, 5 resident blocks per SM instead of 6).
-// The FP32 spread variants are held to 40 registers (6 resident blocks per SM; a few bytes
-// of spills): left free they take 48 (5 blocks), which was 1.2% slower at c2 and 0.3% faster
-// at the Zipf-skewed c3 shape.
+// The FP32 spread and taping variants are held to 40 registers (6 resident blocks per SM; a
+// few bytes of spills).  Left free, the spread variant takes 48 (5 blocks), which was 1.2%
+// slower at c2 and 0.3% faster at the Zipf-skewed c3 shape, and the taping one-group-per-link
+// variant 56 (4 blocks), which made the adjoint's recomputation 10% slower at c5; the
+// one-group-per-link variant without the tape was 1% faster left at 48.
 template <typename T, bool kSpread, bool kTape, bool kChunks>
-__global__ void __launch_bounds__(kTh, (kSpread && sizeof(T) == 4) ? 6 : 1)
+__global__ void __launch_bounds__(kTh, ((kSpread || kTape) && sizeof(T) == 4) ? 6 : 1)
     k_link_rows(View<T> v) {
     __shared__ double red[3 * kWarps];
     __shared__ int last;
