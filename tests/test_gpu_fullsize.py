@@ -3,9 +3,12 @@
 c2 (n = 1e7, m = 1e6): every element of x and of the prices after the first iterations
 against the oracle run on the whole instance; at convergence, the KKT conditions of the
 problem (properties that hold at any size) and FP32 against the FP64 path.
-c3 (Zipf-skewed links, hot links cut into chunks): the oracle on a 1/50 instance; at full
-size FP32 against FP64 on one rho schedule (c3 does not reach eps_abs = 1e-4 within
-40,000 iterations in either precision, so it has no converged point to check).
+c3 (Zipf-skewed links, hot links cut into chunks): at full size every element of x and of
+the prices after the first iterations against the oracle run on the whole instance, in
+the configuration bench.py times (epilogues spread over the lanes, chunks from the queue);
+the oracle on a 1/50 instance for 60 iterations; at full size FP32 against FP64 on one rho
+schedule (c3 does not reach eps_abs = 1e-4 within 40,000 iterations in either precision,
+so it has no converged point to check).
 """
 import numpy as np
 import pytest
@@ -66,6 +69,26 @@ def test_c2_kkt_at_tight_tolerance(c2):
 
 
 @pytest.fixture(scope="module")
+def c3():
+    return W.workload("c3")
+
+
+@pytest.fixture(scope="module")
+def c3_oracle3(c3):
+    return oracle_run(c3, 3)  # about 50 s and 9 GB of host memory
+
+
+@pytest.mark.parametrize("precision,tol", [("fp32", 1e-4), ("fp64", 1e-10)])
+def test_c3_first_iterations_match_oracle(c3, c3_oracle3, precision, tol):
+    """n = 2e7, m = 2e6, 1.4e8 entries; the hottest link has 1.1e7 streams and every link
+    above 256 streams is summed in 2,048-entry chunks taken from the grid-wide queue."""
+    g = run_gpu(c3, 3, precision, history=8)
+    e = compare(g, c3_oracle3, tol)
+    assert e["x"] <= tol and e["lam"] <= tol, e
+    assert e["x_el"] <= 10 * tol and e["lam_el"] <= 10 * tol, e
+
+
+@pytest.fixture(scope="module")
 def c3_small():
     return W.workload("c3", scale=0.02)  # n = 4e5, m = 4e4; hottest link ~57% of streams
 
@@ -79,11 +102,10 @@ def test_c3_scaled_matches_oracle(c3_small, precision, tol):
     assert e["x"] <= tol and e["lam"] <= tol, e
 
 
-def test_c3_full_size_fp32_tracks_fp64():
+def test_c3_full_size_fp32_tracks_fp64(c3):
     """Full c3 (1.4e8 entries; every link above 256 streams is summed by warps in chunks of
     2,048 entries, the hottest has 1.1e7 streams): FP32 on the FP64 run's rho schedule stays within 1e-4 of
     it after 300 iterations."""
-    c3 = W.workload("c3")
     f64 = run_gpu(c3, 300, "fp64", history=300)
     f32 = run_gpu(c3, 300, "fp32", history=300,
                   schedule_decisions=decisions_from_hist(f64["hist"]))
