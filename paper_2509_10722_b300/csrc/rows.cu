@@ -113,13 +113,23 @@ __global__ void __launch_bounds__(kTh) k_stream_rows(View<T> v) {
 // kChunks: the instance has links of more than kLongRow streams (v.nchunks > 0); without
 // them the kernel is compiled without the chunk phase (which costs the other phases
 // registers: 48 against 40 per thread, 5 resident blocks per SM instead of 6).
-// The FP32 spread and taping variants are held to 40 registers (6 resident blocks per SM; a
-// few bytes of spills).  Left free, the spread variant takes 48 (5 blocks), which was 1.2%
-// slower at c2 and 0.3% faster at the Zipf-skewed c3 shape, and the taping one-group-per-link
-// variant 56 (4 blocks), which made the adjoint's recomputation 10% slower at c5; the
-// one-group-per-link variant without the tape was 1% faster left at 48.
+// Resident blocks per SM each variant asks of the compiler (0: no request), as measured.
+// The FP32 taping variants and the FP32 spread variant with chunks ask for 6 (40 registers,
+// a few bytes of spills): left free, the taping one-group-per-link variant takes 56
+// registers (4 blocks), which made the adjoint's recomputation 10% slower at c5, and the
+// spread variant with chunks 48 (5 blocks).  The FP32 one-group-per-link variant asks for 1,
+// which lets it take 48 registers: 8% faster on a network of 1e5 links than at 40.  The
+// FP32 spread variant without chunks compiles to 40 registers without spills with no
+// request, and FP64 to 62-64.
 template <typename T, bool kSpread, bool kTape, bool kChunks>
-__global__ void __launch_bounds__(kTh, ((kSpread || kTape) && sizeof(T) == 4) ? 6 : 1)
+constexpr int link_min_blocks() {
+    if (sizeof(T) != 4) return 0;
+    if (kTape || (kSpread && kChunks)) return 6;
+    return kSpread ? 0 : 1;
+}
+
+template <typename T, bool kSpread, bool kTape, bool kChunks>
+__global__ void __launch_bounds__(kTh, (link_min_blocks<T, kSpread, kTape, kChunks>()))
     k_link_rows(View<T> v) {
     __shared__ double red[3 * kWarps];
     __shared__ int last;
@@ -142,41 +152,71 @@ __global__ void __launch_bounds__(kTh, ((kSpread || kTape) && sizeof(T) == 4) ? 
         // links at a time and sums them one after the other with all its lanes; lane k then
         // runs the epilogue of the k-th of them, so that the epilogues use every lane.
         // Rounds of kGroup links per group are dealt out in turn (groups side by side take
-        // links side by side); the links left after the full rounds are split evenly, fewer
-        // than kGroup per group, so that no group has a round more than another.
+        // links side by side, whose first-link streams share sectors).
         const int sl = g.thread_rank();
-        const int ngroups = gridDim.x * kGroups;
-        const int gid = blockIdx.x * kGroups + (int)(threadIdx.x / kGroup);
-        const int per_round = ngroups * kGroup;
-        const int rounds = m / per_round;
-        const int rest0 = rounds * per_round;  // first link left over
-        const int rest = m - rest0;
-        const int last0 = rest0 + (int)((long long)gid * rest / ngroups);
-        const int last1 = rest0 + (int)((long long)(gid + 1) * rest / ngroups);
-        for (int k = 0; k <= rounds; ++k) {
-            // this round's links of the group: [base, end)
-            const int base = k < rounds ? (k * ngroups + gid) * kGroup : last0;
-            const int end = k < rounds ? base + kGroup : last1;
-            const int lk = base + sl;  // this lane's link
-            int q0 = 0, q1 = 0;
-            if (lk < end) {
-                q0 = __ldg(row_ptr + lk);
-                q1 = __ldg(row_ptr + lk + 1);
-            }
-            T mine = T(0);
+        if constexpr (kChunks) {
+            // the links left after the full rounds are split evenly, fewer than kGroup per
+            // group, so that no group has a round more than another
+            const int ngroups = gridDim.x * kGroups;
+            const int gid = blockIdx.x * kGroups + (int)(threadIdx.x / kGroup);
+            const int per_round = ngroups * kGroup;
+            const int rounds = m / per_round;
+            const int rest0 = rounds * per_round;  // first link left over
+            const int rest = m - rest0;
+            const int last0 = rest0 + (int)((long long)gid * rest / ngroups);
+            const int last1 = rest0 + (int)((long long)(gid + 1) * rest / ngroups);
+            for (int k = 0; k <= rounds; ++k) {
+                // this round's links of the group: [base, end)
+                const int base = k < rounds ? (k * ngroups + gid) * kGroup : last0;
+                const int end = k < rounds ? base + kGroup : last1;
+                const int lk = base + sl;  // this lane's link
+                int q0 = 0, q1 = 0;
+                if (lk < end) {
+                    q0 = __ldg(row_ptr + lk);
+                    q1 = __ldg(row_ptr + lk + 1);
+                }
+                T mine = T(0);
 #pragma unroll 1
-            for (int j = 0; j < kGroup; ++j) {
-                if (base + j >= end) break;  // the same for the whole group
-                const int p0 = g.shfl(q0, j), p1 = g.shfl(q1, j);
-                if (kChunks && p1 - p0 > kLongRow) continue;  // done by its chunks
-                const T s = group_gather_sum<kGroup, 2>(g, col_idx, x, p0, p1, v.n, v.dbg);
-                const T sj = g.shfl(s, 0);
-                if (sl == j) mine = sj;
+                for (int j = 0; j < kGroup; ++j) {
+                    if (base + j >= end) break;  // the same for the whole group
+                    const int p0 = g.shfl(q0, j), p1 = g.shfl(q1, j);
+                    if (p1 - p0 > kLongRow) continue;  // done by its chunks
+                    const T s = group_gather_sum<kGroup, 2>(g, col_idx, x, p0, p1, v.n, v.dbg);
+                    const T sj = g.shfl(s, 0);
+                    if (sl == j) mine = sj;
+                }
+                if (lk < end && q1 - q0 <= kLongRow) {
+                    const LinkState<T> st = load_link(v, lk);
+                    const T psn = link_epilogue(v, lk, st, mine, q1 - q0, alpha, rho, inv_rho, r2, s2);
+                    if (kTape && tape) tape[lk] = psn;
+                }
             }
-            if (lk < end && (!kChunks || q1 - q0 <= kLongRow)) {
-                const LinkState<T> st = load_link(v, lk);
-                const T psn = link_epilogue(v, lk, st, mine, q1 - q0, alpha, rho, inv_rho, r2, s2);
-                if (kTape && tape) tape[lk] = psn;
+        } else {
+            // the rounds go on to the end: split evenly, the last round took this variant
+            // registers (or spills) that cost more than the split saved on short links
+            const long long stride = (long long)gridDim.x * kGroups * kGroup;
+            for (long long base = ((long long)blockIdx.x * kGroups + threadIdx.x / kGroup) * kGroup;
+                 base < m; base += stride) {
+                const long long lk = base + sl;  // this lane's link
+                int q0 = 0, q1 = 0;
+                if (lk < m) {
+                    q0 = __ldg(row_ptr + lk);
+                    q1 = __ldg(row_ptr + lk + 1);
+                }
+                T mine = T(0);
+#pragma unroll 1
+                for (int j = 0; j < kGroup; ++j) {
+                    if (base + j >= m) break;  // the same for the whole group
+                    const int p0 = g.shfl(q0, j), p1 = g.shfl(q1, j);
+                    const T s = group_gather_sum<kGroup, 2>(g, col_idx, x, p0, p1, v.n, v.dbg);
+                    const T sj = g.shfl(s, 0);
+                    if (sl == j) mine = sj;
+                }
+                if (lk < m) {
+                    const LinkState<T> st = load_link(v, (int)lk);
+                    const T psn = link_epilogue(v, (int)lk, st, mine, q1 - q0, alpha, rho, inv_rho, r2, s2);
+                    if (kTape && tape) tape[lk] = psn;
+                }
             }
         }
     } else {
