@@ -67,7 +67,9 @@ extern "C" {
                             SpMV-transpose, reductions), all FP64 */
 
 /* Optional device allocator.  alloc returns device memory of `bytes` bytes usable on
- * `stream` (NULL on failure, which num_create reports as NUM_ERR_OOM); release frees it. */
+ * `stream` (NULL on failure, which num_create reports as NUM_ERR_OOM); release frees it.
+ * The kernels need 16-byte aligned blocks: a block that is not is handed back at once and
+ * asked again 16 bytes larger (release then receives that block and size). */
 typedef struct {
     void* (*alloc)(void* ctx, size_t bytes, void* stream);
     void (*release)(void* ctx, void* ptr, size_t bytes, void* stream);

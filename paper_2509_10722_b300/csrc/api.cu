@@ -55,29 +55,43 @@ void clear_error() { g_last_error.clear(); }
 namespace pmp {
 namespace host {
 
+// Device memory of the handle.  The kernels read pairs of values (and the chunk table) as
+// 16-byte loads, so every block must start on a 16-byte boundary: cudaMalloc's always do;
+// a block from the caller's allocator that does not is asked 16 bytes larger and used from
+// its first 16-byte boundary.
 void* dev_alloc(num_problem* h, size_t bytes) {
     if (bytes == 0) bytes = 16;
     void* p = nullptr;
     if (h->custom_alloc) {
         p = h->alloc.alloc(h->alloc.ctx, bytes, (void*)h->user_stream);
+        if (p && ((uintptr_t)p & 15u) != 0) {
+            h->alloc.release(h->alloc.ctx, p, bytes, (void*)h->user_stream);
+            bytes += 16;
+            void* raw = h->alloc.alloc(h->alloc.ctx, bytes, (void*)h->user_stream);
+            if (!raw) return nullptr;
+            void* q = (void*)(((uintptr_t)raw + 15u) & ~(uintptr_t)15u);
+            h->blocks.push_back({q, raw, bytes});
+            return q;
+        }
     } else {
         if (cudaMalloc(&p, bytes) != cudaSuccess) {
             cudaGetLastError();
             p = nullptr;
         }
     }
-    if (p) h->blocks.emplace_back(p, bytes);
+    if (p) h->blocks.push_back({p, p, bytes});
     return p;
 }
 
 void dev_free(num_problem* h, void* p) {
     if (!p) return;
     for (size_t i = 0; i < h->blocks.size(); ++i) {
-        if (h->blocks[i].first == p) {
+        if (h->blocks[i].ptr == p) {
+            const auto b = h->blocks[i];
             if (h->custom_alloc)
-                h->alloc.release(h->alloc.ctx, p, h->blocks[i].second, (void*)h->stream);
+                h->alloc.release(h->alloc.ctx, b.raw, b.bytes, (void*)h->stream);
             else
-                cudaFree(p);
+                cudaFree(b.raw);
             h->blocks.erase(h->blocks.begin() + i);
             return;
         }
@@ -90,7 +104,7 @@ void destroy_handle(num_problem* h) {
     if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
     if (h->graph) cudaGraphDestroy(h->graph);
     adjoint_tape_free(h);
-    while (!h->blocks.empty()) dev_free(h, h->blocks.back().first);
+    while (!h->blocks.empty()) dev_free(h, h->blocks.back().ptr);
     if (h->ctl_host) cudaFreeHost(h->ctl_host);
     for (cudaEvent_t ev : h->evs) cudaEventDestroy(ev);
     if (h->legacy_ev) cudaEventDestroy(h->legacy_ev);

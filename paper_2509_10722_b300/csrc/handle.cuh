@@ -27,7 +27,12 @@ struct num_problem {
     cudaEvent_t legacy_ev = nullptr;
     int device = 0;
     int prec = 0;
-    std::vector<std::pair<void*, size_t>> blocks;
+    struct Block {
+        void* ptr;     // what the library uses: 16-byte aligned
+        void* raw;     // what the allocator returned
+        size_t bytes;  // what was asked of the allocator
+    };
+    std::vector<Block> blocks;
 
     int *col_ptr = nullptr, *row_idx = nullptr, *row_ptr = nullptr, *col_idx = nullptr;
     int grid_s = 0, grid_l = 0;

@@ -116,6 +116,38 @@ def test_failing_allocator_reports_oom(capi):
     assert ei.value.code == capi.NUM_ERR_OOM and len(calls) == 1
 
 
+def test_allocator_blocks_are_aligned_to_16_bytes(capi):
+    """The kernels read 16-byte pairs: a block the caller's allocator returns off a 16-byte
+    boundary is handed back at once and asked again 16 bytes larger; every block is
+    released with the address and size the allocator saw."""
+    live = {}
+    calls = []
+    counter = [0]
+    fake = [0x10000]
+
+    def alloc(ctx, nbytes, stream):
+        counter[0] += 1
+        if counter[0] == 9:
+            return None
+        fake[0] += 1 << 20
+        ptr = fake[0] + (8 if counter[0] % 2 else 0)  # every other block misaligned
+        live[ptr] = nbytes
+        calls.append((ptr, nbytes))
+        return ptr
+
+    def release(ctx, ptr, nbytes, stream):
+        assert live.pop(ptr) == nbytes
+
+    a = capi.num_allocator(capi.ALLOC_FN(alloc), capi.RELEASE_FN(release), None)
+    p = capi.num_default_params(allocator=ctypes.pointer(a))
+    with pytest.raises(capi.NumError) as ei:
+        _create(capi, params=p)
+    assert ei.value.code == capi.NUM_ERR_OOM and counter[0] == 9 and not live
+    for i, (ptr, nbytes) in enumerate(calls):
+        if ptr % 16:
+            assert calls[i + 1][1] == nbytes + 16
+
+
 def test_allocator_failing_midway_releases_everything(capi):
     """The k-th allocation fails: every earlier block is handed back, none twice."""
     live = {}
