@@ -26,9 +26,11 @@
 //   stream kernel: one thread per stream; the stream's state is loaded first, then its
 //     route entries four at a time (four independent gathers of (pbar, y) in flight);
 //     streams with more than kLongRoute (32) links are summed by one warp each instead;
-//   link kernel: a group of G lanes per link (G = 32 / rows per warp), the link's own
-//     state loaded by the group leader before the gathers, R x summed by the group in a
-//     fixed order, the link epilogue by the leader; links with more than kLongRow (256)
+//   link kernel: a group of 8 lanes sums R x of a link in a fixed order; with few links
+//     per group (a small instance) each link has its own group, whose leader loads the
+//     link's state before the gathers and runs the epilogue; with many, a group sums 8
+//     consecutive links one after the other and its 8 lanes run their epilogues; links
+//     with more than kLongRow (256)
 //     streams are cut into fixed chunks of kChunk (2048) entries, each chunk summed by one
 //     warp (four gathers in flight per lane) into its own slot, and the warp that brings
 //     the row's arrival count to the number of chunks sums the slots in a fixed order and
