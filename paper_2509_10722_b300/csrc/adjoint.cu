@@ -23,7 +23,8 @@
 // dx/dw = 1 / (rho L); a stream at a bound of its box, 0.  Only x_k and ps_k of every
 // iteration are needed; they are recomputed segment by segment from checkpoints.
 // Links of more than kLongRow streams are summed by whole warps in chunks,
-// and streams with more than kLongRoute links by one warp each, as in the forward kernels.
+// and streams with more than kLongRoute links by one warp each, as in the forward kernels
+// (the chunks dealt out to the warps in turn, not from the forward link kernel's queue).
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 

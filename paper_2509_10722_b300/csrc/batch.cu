@@ -178,7 +178,9 @@ __global__ void __launch_bounds__(kTh) k_link_batch(BatchView<T> b) {
             finish_instance(b, item.x, lane);
         }
     }
-    // chunks of the longer links: one warp each, as in the single-instance row kernel
+    // chunks of the longer links: one warp each, as in the single-instance row kernel, but
+    // dealt out to the warps in turn (there is no grid-wide queue here: no block finishes
+    // the launch, so none could reset it)
     for (int q = blockIdx.x * kWarps + warp; q < b.nchunks; q += gridDim.x * kWarps) {
         const int i = __ldg(b.chunk_inst + q);
         const Ctl* c = b.ctls + i;
