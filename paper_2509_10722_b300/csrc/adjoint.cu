@@ -24,7 +24,7 @@
 // iteration are needed; they are recomputed segment by segment from checkpoints.
 // Links of more than kLongRow streams are summed by whole warps in chunks,
 // and streams with more than kLongRoute links by one warp each, as in the forward kernels
-// (the chunks dealt out to the warps in turn, not from the forward link kernel's queue).
+// (the chunks dealt out to the warps in turn, not from the forward link kernels' queue).
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 

@@ -45,6 +45,8 @@ __global__ void __launch_bounds__(kTh) k_stream_batch(BatchView<T> b) {
     using V = typename Pair<T>::type;
     __shared__ double red[kWarps];
     if (b.glob->running == 0) return;
+    // the link kernel of the previous iteration is done: its chunk queue starts over
+    if (blockIdx.x == 0 && threadIdx.x == 0) b.glob->chunk_next = 0;
     const View<T>& v = b.v;
     int it0 = blockIdx.x, it1 = b.nsitems, step = gridDim.x;  // items in turn, or
     if (b.sblk) {                                            // this block's range
@@ -178,45 +180,56 @@ __global__ void __launch_bounds__(kTh) k_link_batch(BatchView<T> b) {
             finish_instance(b, item.x, lane);
         }
     }
-    // chunks of the longer links: one warp each, as in the single-instance row kernel, but
-    // dealt out to the warps in turn (there is no grid-wide queue here: no block finishes
-    // the launch, so none could reset it)
-    for (int q = blockIdx.x * kWarps + warp; q < b.nchunks; q += gridDim.x * kWarps) {
-        const int i = __ldg(b.chunk_inst + q);
-        const Ctl* c = b.ctls + i;
-        if (c->stop) continue;  // warp-uniform
-        const int4 ch = __ldg(b.chunks + q);
-        const T s = warp_gather_sum(v.col_idx, v.x, ch.y, ch.z, lane, v.n, v.dbg);
-        int done = 0;
-        if (lane == 0) {
-            b.carry[q] = s;
-            __threadfence();
-            const int p0 = __ldg(v.row_ptr + ch.x), p1 = __ldg(v.row_ptr + ch.x + 1);
-            const int nch = (p1 - p0 + kChunk - 1) / kChunk;
-            done = atomicAdd(b.arrive_c + ch.w, 1) == nch - 1;
-        }
-        done = __shfl_sync(0xffffffffu, done, 0);
-        if (!done) continue;
-        __threadfence();
-        const int p0 = __ldg(v.row_ptr + ch.x), p1 = __ldg(v.row_ptr + ch.x + 1);
-        const int nch = (p1 - p0 + kChunk - 1) / kChunk;
-        const T t = warp_sum_slots(b.carry + ch.w, nch, lane);
-        int whole = 0;
-        if (lane == 0) {
-            const T alpha = (T)c->alpha, rho = (T)c->rho, inv_rho = (T)(1.0 / c->rho);
-            Acc<T> r2, s2;
-            b.arrive_c[ch.w] = 0;
-            const LinkState<T> st = load_link(v, ch.x);
-            link_epilogue(v, ch.x, st, t, p1 - p0, alpha, rho, inv_rho, r2, s2);
-            b.part_c[2 * ch.w] = r2.value();
-            b.part_c[2 * ch.w + 1] = s2.value();
-            __threadfence();
-            whole = instance_done(b, i);
-        }
-        whole = __shfl_sync(0xffffffffu, whole, 0);
-        if (whole) {
-            __threadfence();
-            finish_instance(b, i, lane);
+    // chunks of the longer links: one warp each, taken from a queue shared by the grid,
+    // longest first, each warp taking its next chunk before it sums the current one, as in
+    // the single-instance row kernel (the iteration's stream kernel resets the queue)
+    if (b.nchunks > 0) {
+        int t = 0;  // queue position
+        if (lane == 0) t = (int)atomicAdd(&b.glob->chunk_next, 1u);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        while (t < b.nchunks) {
+            int tn = 0;
+            if (lane == 0) tn = (int)atomicAdd(&b.glob->chunk_next, 1u);
+            const int q = __ldg(v.chunk_queue + t);
+            const int i = __ldg(b.chunk_inst + q);
+            const Ctl* c = b.ctls + i;
+            if (!c->stop) {  // warp-uniform
+                const int4 ch = __ldg(b.chunks + q);
+                const T s = warp_gather_sum(v.col_idx, v.x, ch.y, ch.z, lane, v.n, v.dbg);
+                int done = 0;
+                if (lane == 0) {
+                    b.carry[q] = s;
+                    __threadfence();
+                    const int p0 = __ldg(v.row_ptr + ch.x), p1 = __ldg(v.row_ptr + ch.x + 1);
+                    const int nch = (p1 - p0 + kChunk - 1) / kChunk;
+                    done = atomicAdd(b.arrive_c + ch.w, 1) == nch - 1;
+                }
+                done = __shfl_sync(0xffffffffu, done, 0);
+                if (done) {
+                    __threadfence();
+                    const int p0 = __ldg(v.row_ptr + ch.x), p1 = __ldg(v.row_ptr + ch.x + 1);
+                    const int nch = (p1 - p0 + kChunk - 1) / kChunk;
+                    const T tot = warp_sum_slots(b.carry + ch.w, nch, lane);
+                    int whole = 0;
+                    if (lane == 0) {
+                        const T alpha = (T)c->alpha, rho = (T)c->rho, inv_rho = (T)(1.0 / c->rho);
+                        Acc<T> r2, s2;
+                        b.arrive_c[ch.w] = 0;
+                        const LinkState<T> st = load_link(v, ch.x);
+                        link_epilogue(v, ch.x, st, tot, p1 - p0, alpha, rho, inv_rho, r2, s2);
+                        b.part_c[2 * ch.w] = r2.value();
+                        b.part_c[2 * ch.w + 1] = s2.value();
+                        __threadfence();
+                        whole = instance_done(b, i);
+                    }
+                    whole = __shfl_sync(0xffffffffu, whole, 0);
+                    if (whole) {
+                        __threadfence();
+                        finish_instance(b, i, lane);
+                    }
+                }
+            }
+            t = __shfl_sync(0xffffffffu, tn, 0);
         }
     }
 }
@@ -334,6 +347,7 @@ __global__ void k_batch_arm(Ctl* ctls, BatchGlobal* glob, int count, long long m
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         glob->running = max_iters > 0 ? count : 0;  // instances still running
         glob->ticket = 0;
+        glob->chunk_next = 0;
     }
 }
 
@@ -355,6 +369,7 @@ __global__ void k_batch_reset(Ctl* ctls, BatchGlobal* glob, int count, double rh
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         glob->running = 0;
         glob->ticket = 0;
+        glob->chunk_next = 0;
     }
 }
 

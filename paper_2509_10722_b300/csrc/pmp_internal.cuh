@@ -147,6 +147,7 @@ struct BatchGlobal {
     int running;          // number of instances still running
     int timeout;          // persistent kernel: 1 once a bounded wait of some block ran out
     int timeout_block;    // the block whose wait ran out first
+    unsigned int chunk_next;  // batch link kernel: next position in the chunk queue
 };
 
 // Work items are (instance, first row, end row, 0); item ranges of instance i are
