@@ -365,3 +365,21 @@ def test_many_links_fp32_match_oracle(many_links):
     ref = oracle_run(many_links, 150)
     g = run_gpu(many_links, 150, "fp32", schedule_decisions=ref["decisions"])
     assert rel(g["x"], ref["x"]) <= 1e-4 and rel(g["lam"], ref["lam"]) <= 1e-4
+
+
+@pytest.mark.parametrize("m", [500_009, 681_997, 1_048_583])
+def test_spread_rounds_cover_every_link(m):
+    """Half a million to a million links without any long one: the link kernel runs its
+    spread variant without the chunk phase, rounds of 8 links per group dealt out in turn,
+    the last round partial by a different amount at each size.  A link left out of every
+    round would keep its initial price; element by element against the oracle after 3
+    iterations (FP64 1e-10, FP32 1e-4 in norm, ten times that element by element with the
+    floor of 1e-3 of the largest value)."""
+    inst = W.random_instance(m // 4, m, 1, 4, seed=m % 1000, frac_log=0.7, box=(0.0, 20.0))
+    assert np.bincount(inst["route_links"], minlength=m).max() <= 256
+    ref = oracle_run(inst, 3)
+    for precision, tol in (("fp64", 1e-10), ("fp32", 1e-4)):
+        g = run_gpu(inst, 3, precision)
+        e = compare(g, ref, tol)
+        assert e["x"] <= tol and e["lam"] <= tol, (precision, e)
+        assert e["x_el"] <= 10 * tol and e["lam_el"] <= 10 * tol, (precision, e)
