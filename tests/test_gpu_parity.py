@@ -383,3 +383,18 @@ def test_spread_rounds_cover_every_link(m):
         e = compare(g, ref, tol)
         assert e["x"] <= tol and e["lam"] <= tol, (precision, e)
         assert e["x_el"] <= 10 * tol and e["lam_el"] <= 10 * tol, (precision, e)
+
+
+@pytest.mark.parametrize("m,n", [(30_011, 300_007), (120_007, 30_011), (400_009, 700_001)])
+def test_grid_rounds_cover_every_stream_and_link(m, n):
+    """Below the spread threshold the link kernel runs one group per link, links dealt out
+    to a resident grid in turn; the stream kernel deals streams to its threads the same
+    way.  Sizes chosen so that both have a partial last round (up to three rounds of
+    streams, four of links): element by element against the oracle after 3 iterations."""
+    inst = W.random_instance(n, m, 1, 4, seed=(m + n) % 1000, frac_log=0.7, box=(0.0, 20.0))
+    ref = oracle_run(inst, 3)
+    for precision, tol in (("fp64", 1e-10), ("fp32", 1e-4)):
+        g = run_gpu(inst, 3, precision)
+        e = compare(g, ref, tol)
+        assert e["x"] <= tol and e["lam"] <= tol, (precision, e)
+        assert e["x_el"] <= 10 * tol and e["lam_el"] <= 10 * tol, (precision, e)
